@@ -1,0 +1,167 @@
+"""Dense FP64 Sinkhorn and exact kernel-vector products (test infrastructure).
+
+Notation: source points x_i (n of them, weights a = p), target points y_j
+(m of them, weights b = p~), cost d_ij^r with d the Euclidean distance
+(Eq. (dist)).  The paper writes the Gibbs kernel as exp(-lambda d^r); this
+oracle takes eps = 1/lambda, so k_ij = exp(-d_ij^r / eps) and every 1/lambda
+in the paper becomes a factor eps.  The scaling vectors u, v are the paper's
+alpha, alpha~.
+
+Only tests/, smoke() and bench.py's CPU-baseline leg may use this module.
+"""
+import numpy as np
+
+
+def cost_matrix(x, y, r):
+    """d_ij^r with d_ij = ||x_i - y_j||_2 (Eq. (dist), Def. "Wasserstein distance")."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    diff = x[:, None, :] - y[None, :, :]
+    dist = np.sqrt(np.sum(diff * diff, axis=-1))
+    return dist ** r
+
+
+def gibbs_kernel(x, y, eps, r):
+    """k_ij = exp(-d_ij^r / eps): the Gibbs kernel of Alg. 1 (with lambda = 1/eps)."""
+    return np.exp(-cost_matrix(x, y, r) / eps)
+
+
+def kernel_apply(x, y, v, eps, r, chunk=256):
+    """t_i = sum_j v_j exp(-||x_i - y_j||^r / eps), i = 1..n (Eq. (matexp)).
+
+    Matrix-free: rows are formed ``chunk`` at a time, so memory stays
+    O(chunk * m) and the oracle reaches sizes where the dense K does not fit.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    out = np.empty(x.shape[0], dtype=np.float64)
+    for i0 in range(0, x.shape[0], chunk):
+        out[i0:i0 + chunk] = gibbs_kernel(x[i0:i0 + chunk], y, eps, r) @ v
+    return out
+
+
+def kernel_apply_T(x, y, u, eps, r, chunk=256):
+    """t~_j = sum_i u_i exp(-||x_i - y_j||^r / eps), j = 1..m (Eq. (matexpt))."""
+    return kernel_apply(y, x, u, eps, r, chunk)
+
+
+def entropy(p):
+    """H(P) = -sum_i p_i log p_i (Lemma "Quality of the Sinkhorn approximation"), 0 log 0 = 0."""
+    p = np.asarray(p, dtype=np.float64)
+    nz = p > 0
+    return float(-np.sum(p[nz] * np.log(p[nz])))
+
+
+def plan_entropy(pi):
+    """H(pi) = -sum_ij pi_ij log pi_ij (Eq. (negentropy))."""
+    return entropy(np.ravel(pi))
+
+
+def transport_plan(u, v, K):
+    """pi = diag(u) K diag(v) (Eq. (pi*))."""
+    return u[:, None] * K * v[None, :]
+
+
+def dual_objective(u, v, a, b, K, eps):
+    """Dual function Eq. (27) with 1/lambda = eps:
+
+    d(u, v) = eps sum_i a_i (1/2 + log u_i) + eps sum_j b_j (1/2 + log v_j)
+              - eps sum_ij u_i k_ij v_j.
+    With sum a = sum b = 1 this is the value Alg. 1 returns.
+    """
+    return float(eps * np.sum(a * (0.5 + np.log(u)))
+                 + eps * np.sum(b * (0.5 + np.log(v)))
+                 - eps * (u @ K @ v))
+
+
+def sinkhorn_value(u, v, a, b, uKv, eps):
+    """Result line of Alg. 1 / Alg. 3 with 1/lambda = eps:
+
+    s = eps + eps sum_i a_i log u_i + eps sum_j b_j log v_j - eps u^T K v.
+    ``uKv`` is u^T K v (Alg. 3 writes it as sum_j t~_j v_j).
+    """
+    return float(eps * (1.0 + np.sum(a * np.log(u)) + np.sum(b * np.log(v)) - uKv))
+
+
+def marginal_residuals(u, v, a, b, K):
+    """The two terms of Eq. (Error): ||pi 1 - p|| and ||pi^T 1 - p~|| (Euclidean)."""
+    row = u * (K @ v) - a
+    col = v * (K.T @ u) - b
+    return float(np.linalg.norm(row)), float(np.linalg.norm(col))
+
+
+def sinkhorn_dense(x, a, y, b, eps, r, iters, record=False):
+    """Alg. 1 (standard Sinkhorn) with an explicit K, in FP64.
+
+    Starts from u = 1_n, v = 1_m (the Set line of Alg. 1).  One iteration is the
+    odd half-step u_i <- a_i / (K v)_i followed by the even half-step
+    v_j <- b_j / (K^T u)_j (Eq. (S1), reading its second p_j as p~_j = b_j).
+    ``iters`` counts such pairs, so Delta = 2 * iters half-steps are taken.
+
+    Returns a dict with u, v, the result value ``s`` (Alg. 1 result line), the
+    primal quantities <pi, C> = s~ (Eq. (15)) and H(pi), the final residuals of
+    Eq. (Error) and, if ``record``, the states after every half-step.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    C = cost_matrix(x, y, r)
+    K = np.exp(-C / eps)
+    u = np.ones(len(a))
+    v = np.ones(len(b))
+    history = [(u.copy(), v.copy())] if record else None
+    for _ in range(iters):
+        u = a / (K @ v)            # Delta odd
+        if record:
+            history.append((u.copy(), v.copy()))
+        v = b / (K.T @ u)          # Delta even
+        if record:
+            history.append((u.copy(), v.copy()))
+    pi = transport_plan(u, v, K)
+    err_row, err_col = marginal_residuals(u, v, a, b, K)
+    uKv = float(u @ K @ v)
+    return dict(
+        u=u, v=v, K=K, C=C, pi=pi,
+        s=sinkhorn_value(u, v, a, b, uKv, eps),
+        s_tilde=float(np.sum(pi * C)),
+        H_pi=plan_entropy(pi),
+        err_row=err_row, err_col=err_col,
+        history=history,
+    )
+
+
+def sinkhorn_matrix_free(x, a, y, b, eps, r, iters):
+    """Alg. 1 with every K-product formed row-chunk by row-chunk (Eqs. (matexp),
+    (matexpt)); the same iteration as ``sinkhorn_dense`` for sizes whose K does
+    not fit in memory.  Returns u, v, s (Alg. 1 result line) and the final
+    Eq. (Error) residuals."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    u = np.ones(len(a))
+    v = np.ones(len(b))
+    for _ in range(iters):
+        u = a / kernel_apply(x, y, v, eps, r)
+        v = b / kernel_apply_T(x, y, u, eps, r)
+    Kv = kernel_apply(x, y, v, eps, r)
+    KTu = kernel_apply_T(x, y, u, eps, r)
+    uKv = float(u @ Kv)
+    return dict(
+        u=u, v=v,
+        s=sinkhorn_value(u, v, a, b, uKv, eps),
+        err_row=float(np.linalg.norm(u * Kv - a)),
+        err_col=float(np.linalg.norm(v * KTu - b)),
+    )
+
+
+def kl_divergence(p, q):
+    """D_KL(p | q) = sum_i p_i log(p_i / q_i) (Notations, Sec. 2)."""
+    p = np.asarray(p, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    nz = p > 0
+    return float(np.sum(p[nz] * np.log(p[nz] / q[nz])))
+
+
+def objective_f(u, v, a, b, K):
+    """f(u, v) = u^T K v - sum a log u - sum b log v (Eq. (objfunc)), here with
+    the unnormalized K that Alg. 1 iterates with."""
+    return float(u @ K @ v - np.sum(a * np.log(u)) - np.sum(b * np.log(v)))
