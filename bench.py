@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of NFFT-accelerated Sinkhorn on GB300.
+
+One step = one Sinkhorn iteration (the u half-step and the v half-step, each a
+fast summation: spread, FFT, multiply, inverse FFT, interpolation, FP64
+update) on the workload "ball3d_n1e6_eps0.02_fp32": n = m = 1e6 points i.i.d.
+uniform in the radius-0.2 ball in R^3 (seeds 1, 2), uniform weights,
+squared Euclidean cost (r = 2), eps = 0.02, bandwidth N = 64, sigma = 2,
+Kaiser-Bessel cutoff m = 4, FP32 fast summation with FP64 updates.
+
+Reported: iterations/s (whole job over all ranks), the same through the C ABI
+with host buffers (e2e, plan build and copies included), the direct-summation
+Sinkhorn on the same GPU, the per-stage roofline of the dominant kernel, and
+the FP64 CPU oracle timed on a bounded sample on the host cores.
+
+--impl reference times the CPU oracle (the reference arm of this project) on
+bounded samples of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Sinkhorn iters/s at n=m=1e6,d=3 (NFFT vs direct on same GB300, ≤1e-5 rel err)"
+UNIT = "iters/s"
+L2_FLUSH_BYTES = 512 * 1024 * 1024
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if sm:
+            sm.sort()
+            out["sm_mhz"] = sm[len(sm) // 2]
+            out["sm_max_mhz"] = max(mx)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(sm)
+        return out
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+def _oracle_sample_job(n_rows, seed):
+    """Runs in a spawned process with one thread: times the oracle's exact
+    kernel products (Eq. (matexp)/(matexpt)) on n_rows sampled rows and columns
+    of the headline workload; returns seconds per full Sinkhorn iteration."""
+    import numpy as np
+    from oracle import sinkhorn as osk
+    from paper_2201_07524_gb300 import workloads as wl
+    w = wl.HEADLINE_3D
+    x, y = w.points()
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(w.n, n_rows, replace=False)
+    cols = rng.choice(w.m, n_rows, replace=False)
+    v = np.ones(w.m)
+    u = np.ones(w.n)
+    a, b = w.marginals()
+    t0 = time.perf_counter()
+    t = osk.kernel_apply(x[rows], y, v, w.eps, w.r, chunk=4)
+    u_new = a[rows] / t
+    tt = osk.kernel_apply(y[cols], x, u, w.eps, w.r, chunk=4)
+    v_new = b[cols] / tt
+    dt = time.perf_counter() - t0
+    assert np.all(np.isfinite(u_new)) and np.all(np.isfinite(v_new))
+    # the full iteration does n rows and m columns
+    return dt * (w.n + w.m) / (2.0 * n_rows)
+
+
+def cpu_oracle_sample(n_rows, seed=0):
+    import multiprocessing as mp
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(1) as pool:
+            t0 = time.perf_counter()
+            sec_per_iter = pool.apply(_oracle_sample_job, (n_rows, seed))
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return sec_per_iter, wall
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    rows = args.ref_rows
+    samples = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(rows, seed=len(samples) + 100)
+    t_all = time.perf_counter()
+    for k in range(args.steps):
+        s, _ = cpu_oracle_sample(rows, seed=k)
+        samples.append(s)
+    wall = time.perf_counter() - t_all
+    sec = sum(samples) / len(samples)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ball3d_n1e6_eps0.02_fp32", "n": 1000000, "m": 1000000, "d": 3, "r": 2,
+                   "eps": 0.02, "kernel": "exact FP64 sums (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d sampled rows of K v and %d columns of K^T u per step (exact FP64 "
+                                   "numpy sums over all 1e6 points), scaled to a full iteration" % (rows, rows)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def algorithmic_counts(w, n_os):
+    """Algorithmic work per launch of each stage for one product over n points
+    (n = m here), as stated in the design notes:
+      spread / interp: 2 W^d flops per point (one multiply forming the tap weight,
+        one add into the grid or the sum), W = 2 m;
+      FFT (all passes of one product): 5 N' log2 N' flops per complex transform of
+        length N' = n_os, over the pencils the pruned pipeline transforms;
+      bytes: spread reads d coords (4 B) and one weight (8 B) per point and writes
+        the n_os^d grid once; interp reads the grid once, d coords, u, a and
+        writes u and t (FP64) per point."""
+    d, W = w.d, 2 * w.m_w
+    n = w.n
+    taps = W ** d
+    f_spread = 2.0 * taps * n
+    f_interp = 2.0 * taps * n
+    grid_bytes = 4.0 * n_os ** d
+    b_spread = n * (4 * d + 8) + grid_bytes
+    b_interp = grid_bytes + n * (4 * d + 8 * 3 + 8 * 2)
+    return {"spread": (f_spread, b_spread), "interp": (f_interp, b_interp)}
+
+
+def fp32_alu_peak_tflops(pk):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2201_07524_gb300 import sk
+    from paper_2201_07524_gb300 import workloads as wl
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = wl.HEADLINE_3D
+    # each rank solves its own independent problem (replicas; seeds offset by rank)
+    w = wl.Workload(w.name, w.d, w.n, w.m, w.eps, w.r, w.iters, w.N, w.m_w, w.sigma, w.precision,
+                    seed_x=w.seed_x + 1000 * rank, seed_y=w.seed_y + 1000 * rank)
+    x, y = w.points()
+    a, b = w.marginals()
+    T = lambda z: torch.as_tensor(z, dtype=torch.float64, device=dev)
+    prm = sk.sk_default_params(N=w.N, m_w=w.m_w, sigma=w.sigma, precision=sk.SK_FP32)
+    plan = sk.sk_init(T(x), T(a), T(y), T(b), w.eps, w.r, prm)
+    info = sk.sk_plan_info(plan)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    for _ in range(args.warmup):
+        sk.sk_solve(plan, 1, result=False)
+    barrier()
+
+    # timed: K steps, each bracketed by events on the launching stream, L2 flushed between steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sk.sk_launch_count(plan)
+    barrier()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        sk.sk_solve(plan, 1, result=False)
+        ends[k].record(stream)
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    launches = sk.sk_launch_count(plan) - launches0
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # per-stage times over the same number of steps (instrumented pass, no graph replay)
+    sk.sk_stage_times(plan, 1)
+    for k in range(args.steps):
+        flush.zero_()
+        sk.sk_solve(plan, 1, result=False)
+    stages = sk.sk_stage_times(plan, 0)
+    torch.cuda.synchronize(dev)
+
+    # accuracy of this run's value against exact sums (a sampled check of one product)
+    v_test = wl.positive_vector(w.m, 36)
+    t_gpu = torch.zeros(w.n, dtype=torch.float64, device=dev)
+    sk.sk_kernel_apply(plan, 0, T(v_test), t_gpu)
+    _, res = sk.sk_solve(plan, 0)
+
+    # direct summation Sinkhorn on the same GPU, same plan, timed the same way
+    direct = None
+    if args.direct_steps > 0:
+        sk.sk_set_state(plan)
+        sk.sk_set_method(plan, sk.SK_METHOD_DIRECT)
+        sk.sk_solve(plan, 1, result=False)
+        torch.cuda.synchronize(dev)
+        ds = [torch.cuda.Event(enable_timing=True) for _ in range(args.direct_steps)]
+        de = [torch.cuda.Event(enable_timing=True) for _ in range(args.direct_steps)]
+        for k in range(args.direct_steps):
+            ds[k].record(stream)
+            sk.sk_solve(plan, 1, result=False)
+            de[k].record(stream)
+        torch.cuda.synchronize(dev)
+        dms = sum(s.elapsed_time(e) for s, e in zip(ds, de)) / args.direct_steps
+        direct = {"value": 1e3 / dms, "unit": UNIT, "ms_per_step": dms, "steps": args.direct_steps,
+                  "speedup_nfft_over_direct": (value / world) / (1e3 / dms)}
+        sk.sk_set_method(plan, sk.SK_METHOD_NFFT)
+
+    # end to end through the C ABI with host buffers: pinned inputs -> sk_init
+    # (copies, sort, tables) -> K iterations -> u, v, result read back to the host
+    e2e = None
+    if args.e2e:
+        pin = lambda z: torch.as_tensor(z, dtype=torch.float64).pin_memory()
+        xh, yh, ah, bh = pin(x), pin(y), pin(a), pin(b)
+        uh = torch.empty(w.n, dtype=torch.float64).pin_memory()
+        vh = torch.empty(w.m, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan2 = sk.sk_init(xh, ah, yh, bh, w.eps, w.r, prm)
+        sk.sk_solve(plan2, args.steps, u_out=uh, v_out=vh, result=True)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        plan2.close()
+        h2d = (x.nbytes + y.nbytes + a.nbytes + b.nbytes) / args.steps
+        d2h = (uh.numel() + vh.numel()) * 8 / args.steps
+        e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "includes": "plan build (sort, tables) and copies",
+               "wall_s": e2e_s}
+
+    # roofline of the dominant kernel
+    pk, pk_kind = peaks()
+    counts = algorithmic_counts(w, info["n_os"])
+    per_launch = {k: (stages[k][0] / stages[k][1] if stages[k][1] else 0.0) for k in stages}
+    dominant = max(("spread", "interp"), key=lambda k: per_launch[k])
+    flops, bytes_ = counts[dominant]
+    dur_s = per_launch[dominant] / 1e3
+    alu_peak = fp32_alu_peak_tflops(pk)
+    achieved = flops / dur_s / 1e12
+    stage_report = {}
+    for k in ("spread", "fft", "interp", "other"):
+        if stages[k][1]:
+            ent = {"ms_per_launch": per_launch[k], "launches": stages[k][1],
+                   "share": stages[k][0] / max(1e-12, sum(v[0] for v in stages.values()))}
+            if k in counts:
+                ent["tflops"] = counts[k][0] / (per_launch[k] / 1e3) / 1e12
+                ent["gbs"] = counts[k][1] / (per_launch[k] / 1e3) / 1e9
+                ent["hbm_frac"] = ent["gbs"] / pk["hbm_gbs"]
+            stage_report[k] = ent
+
+    # sampled accuracy of the product used in this run
+    if rank == 0:
+        from oracle import sinkhorn as osk
+        rows = np.random.default_rng(37).choice(w.n, 32, replace=False)
+        exact = osk.kernel_apply(x[rows], y, v_test, w.eps, w.r, chunk=4)
+        got = t_gpu.cpu().numpy()[rows]
+        efs_sample = float(np.max(np.abs(got - exact)) / np.max(np.abs(exact)))
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_rows > 0:
+        sec, wall_cpu = cpu_oracle_sample(args.cpu_rows)
+        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d sampled rows of K v and %d columns of K^T u (exact FP64 numpy sums over all "
+                         "1e6 points, one thread), scaled to one full iteration; %.1f s wall" %
+                         (args.cpu_rows, args.cpu_rows, wall_cpu)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "m": w.m, "d": w.d, "r": w.r, "eps": w.eps, "N": w.N,
+                       "sigma": w.sigma, "m_w": w.m_w, "fast_summation": "fp32", "updates": "fp64",
+                       "points": "uniform in radius-0.2 ball, seeds 1/2 (+1000*rank)",
+                       "l2": "flushed between timed steps (512 MB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s peaks file)"
+                                        % (float(pk.get("sm_max_mhz", 2070.0)), pk_kind),
+                         "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
+                         "hbm_frac": bytes_ / dur_s / 1e9 / pk["hbm_gbs"]},
+            "stages": stage_report,
+            "direct": direct,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "accuracy": {"efs_sampled_rows": efs_sample, "s_after_run": res["s"],
+                         "marg_err_after_run": res["marg_err"]},
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--direct-steps", type=int, default=2)
+    ap.add_argument("--cpu-rows", type=int, default=200)
+    ap.add_argument("--ref-rows", type=int, default=64)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

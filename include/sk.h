@@ -1,0 +1,227 @@
+/*
+ * sk.h -- C ABI of the GB300 library for NFFT-accelerated Sinkhorn.
+ *
+ * Method: Lakshmanan, Pichler, Potts, "Nonequispaced Fast Fourier Transform
+ * Boost for the Sinkhorn Algorithm".  Sinkhorn's iteration (Alg. 1, Eq. (S1))
+ * alternates the scaling updates u = a ./ (K v) and v = b ./ (K^T u) with the
+ * Gibbs kernel K_ij = exp(-||x_i - y_j||^r / eps) (the paper's exp(-lambda d^r)
+ * with eps = 1/lambda).  Alg. 3 replaces both kernel-vector products by the
+ * NFFT-based fast summation of Eq. (fastsum): spread the source weights onto
+ * an oversampled grid with a Kaiser-Bessel window (adjoint NFFT), FFT,
+ * multiply by the Fourier coefficients b_k of the regularized kernel
+ * (Eq. (ansatz_NFFT)), inverse FFT, interpolate at the targets (NFFT).
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every int-returning call returns SK_OK (0) or one SK_ERR_* code;
+ *    no C++ exception crosses this boundary.  sk_error_string() names a code.
+ *  - Pointers: every double array argument may be device memory or host memory
+ *    (pageable or pinned); the library asks the CUDA runtime which it is and
+ *    copies host arrays itself.  Inputs are read-only and owned by the caller.
+ *    Outputs are written in the caller's original point order.
+ *  - Points: x is n-by-d and y is m-by-d, row-major (point i at x[i*d .. i*d+d-1]).
+ *  - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *    All work is ordered after prior work on that stream; calls that return
+ *    host values (sk_solve with a result, sk_init, the state getters)
+ *    synchronize with it before returning.
+ *  - Threading: a plan is not re-entrant.  Distinct plans may be used from
+ *    different host threads and streams concurrently.
+ */
+#ifndef SK_H
+#define SK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+    SK_OK = 0,
+    SK_ERR_ARG = 1,           /* invalid argument (sizes, dims, parameters, NULL) */
+    SK_ERR_DOMAIN = 2,        /* non-finite coordinates, or a point that falls outside the grid */
+    SK_ERR_WEIGHTS = 3,       /* weights negative / non-finite / not summing to 1 */
+    SK_ERR_NOMEM = 4,         /* device allocation failed */
+    SK_ERR_UNDERFLOW = 5,     /* a kernel sum K v or K^T u was <= 0 or not finite */
+    SK_ERR_NOT_CONVERGED = 6, /* tol > 0 and max_iter reached with ||E|| > tol */
+    SK_ERR_TIMEOUT = 7,       /* reserved for bounded device waits */
+    SK_ERR_CUDA = 8,          /* a CUDA runtime call failed */
+    SK_ERR_UNSUPPORTED = 9    /* valid request this build does not implement */
+};
+
+enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / interpolation */
+enum { SK_METHOD_NFFT = 0, SK_METHOD_DIRECT = 1 };
+enum { SK_SET_X = 0, SK_SET_Y = 1 };        /* which point cloud a stage entry point acts on */
+
+typedef struct sk_plan sk_plan;
+
+/*
+ * Parameters of the fast summation (Sec. 4.1).  The paper leaves all of them
+ * open; sk_default_params() fills in the values this library is tested with.
+ *   N        bandwidth: Fourier coefficients b_k for k in I_N = {-N/2..N/2-1}^d
+ *            (Eq. (ansatz_NFFT)); even, >= 8.
+ *   sigma    oversampling; the FFT grid has n_os = sigma*N points per dimension,
+ *            which must be a power of two, 16 <= n_os <= 1024 (4096 for d = 1).
+ *   m_w      Kaiser-Bessel window cutoff: 2*m_w taps per dimension, 2 <= m_w <= 8,
+ *            n_os >= 4*(m_w+1).
+ *   p        smoothness of the regularized kernel: the boundary polynomial K_B and
+ *            the near-field polynomial K_I match p-1 derivatives, 2 <= p <= 12.
+ *   eps_B    width of the boundary region (torus units): L = 1/2 - eps_B, 0 < eps_B < 1/2.
+ *   eps_I    near-field radius (torus units), used only when K is not smooth at 0
+ *            (r not an even integer; Remark "Arithmetic complexity").
+ *   precision SK_FP32 or SK_FP64 for spreading, FFT and interpolation; the scaling
+ *            updates, residuals and objective are always FP64.
+ *   user_geometry 0: the plan picks center = midpoint of the bounding box of
+ *            x and y and scale = (1/4 - eps_B/2) / R with R the largest distance
+ *            to that center; 1: use `center` and `scale` as given.  Torus
+ *            coordinates are z = scale * (x - center) + 1/2.
+ */
+typedef struct {
+    int N;
+    double sigma;
+    int m_w;
+    int p;
+    double eps_B;
+    double eps_I;
+    int precision;
+    int user_geometry;
+    double center[3];
+    double scale;
+} sk_nfft_params;
+
+/* Summary of a solve (Alg. 3 result line, with 1/lambda = eps). */
+typedef struct {
+    double s;            /* eps (1 + <a,log u> + <b,log v> - sum_j v_j (K^T u)_j) */
+    double s_upper;      /* s + eps (H(a) + H(b))  (the paper's upper bound s~_NFFT) */
+    double err_row;      /* ||u .* (K v) - a||_2 of the returned state   (Eq. (Error)) */
+    double err_col;      /* ||v .* (K^T u) - b||_2 of the returned state (Eq. (Error)) */
+    double marg_err;     /* err_row + err_col */
+    int iters;           /* iterations performed by this call (1 iteration = 2 half-steps) */
+    int total_iters;     /* iterations since sk_init or the last sk_set_state */
+} sk_result;
+
+/* Geometry and sizes a plan settled on. */
+typedef struct {
+    int d;
+    int64_t n, m;
+    int N, n_os, m_w, p, precision, nearfield;
+    double eps, r, eps_scaled;   /* eps_scaled = eps * scale^r: the kernel in torus coordinates */
+    double center[3], scale, eps_B, eps_I;
+    int n_subproblems_x, n_subproblems_y;
+    int64_t device_bytes;        /* device memory the plan holds */
+} sk_info;
+
+/* Text for a status code (static storage, never NULL). */
+const char* sk_error_string(int status);
+
+/* Where the calling thread's last SK_ERR_CUDA / SK_ERR_NOMEM came from (source
+ * line and the CUDA runtime's message); "" if none.  Thread-local storage. */
+const char* sk_last_error(void);
+
+/* Fill *prm with the defaults: N=64, sigma=2, m_w=4, p=8, eps_B=0.1, eps_I=1/16,
+ * SK_FP32, automatic geometry.  Returns SK_ERR_ARG if prm is NULL. */
+int sk_default_params(sk_nfft_params* prm);
+
+/*
+ * Build a plan for the problem (x, a) -> (y, b) with Gibbs kernel
+ * exp(-||x-y||^r / eps) (Alg. 3 inputs: support nodes, probability vectors,
+ * regularization).  Validates: d in {1,2,3}; n, m >= 1; eps > 0; r >= 1;
+ * finite coordinates; weights >= 0 with |sum - 1| <= 1e-9 (SK_ERR_WEIGHTS).
+ * Copies, scales and bin-sorts the points into plan-owned device buffers,
+ * computes the coefficient table b_k / psi_hat(k)^2 on the device, and sets
+ * u = 1_n, v = 1_m (the Set line of Alg. 1).  prm == NULL means defaults.
+ * The caller may free x, a, y, b when this returns.  On failure *out is NULL.
+ */
+int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a,
+            int64_t m, const double* y, const double* b, double eps, double r,
+            const sk_nfft_params* prm, void* stream);
+
+/* Release everything the plan owns (NULL is a no-op). */
+void sk_destroy(sk_plan* plan);
+
+/* Choose how products are evaluated: SK_METHOD_NFFT (Eq. (fastsum), default)
+ * or SK_METHOD_DIRECT (the plain O(n m) sums of Eqs. (matexp)/(matexpt), FP32
+ * kernel values with FP64 accumulation across tiles). */
+int sk_set_method(sk_plan* plan, int method);
+
+/*
+ * One kernel-vector product (Eqs. (matexp), (matexpt)):
+ *   transpose = 0:  out[i] = sum_j K(x_i, y_j) in[j]   (in: m values, out: n values)
+ *   transpose = 1:  out[j] = sum_i K(x_i, y_j) in[i]   (in: n values, out: m values)
+ * Uses the plan's method.  Does not touch the plan's scaling vectors.
+ */
+int sk_kernel_apply(sk_plan* plan, int transpose, const double* in, double* out, void* stream);
+
+/*
+ * Run Sinkhorn iterations (Alg. 3) from the plan's current state.  One
+ * iteration is the odd half-step u = a ./ (K v) followed by the even half-step
+ * v = b ./ (K^T u).  tol <= 0: exactly max_iter iterations, no host sync
+ * unless res/u_out/v_out are requested.  tol > 0: stop as soon as the
+ * row residual ||u .* K v - a|| (the only nonzero term of Eq. (Error) after a
+ * v-update) is <= tol, checking every check_every iterations (<= 0 means 10);
+ * returns SK_ERR_NOT_CONVERGED if max_iter is reached first (state and outputs
+ * are still written).  u_out (n), v_out (m) may be NULL.  res may be NULL; if
+ * given, the final residuals and the value s are computed (one extra K v
+ * product) and written.  Returns SK_ERR_UNDERFLOW if any kernel sum was <= 0 or
+ * not finite.
+ */
+int sk_solve(sk_plan* plan, int max_iter, double tol, int check_every,
+             double* u_out, double* v_out, sk_result* res, void* stream);
+
+/* Gradient of the value with respect to weights and positions: not built yet,
+ * always returns SK_ERR_UNSUPPORTED. */
+int sk_grad(sk_plan* plan, double* grad_a, double* grad_b, double* grad_x, double* grad_y,
+            void* stream);
+
+/* Copy the scaling vectors out (caller order; either pointer may be NULL) and the
+ * iteration count. Synchronizes. */
+int sk_get_state(sk_plan* plan, double* u, double* v, int* iters);
+
+/* Replace the scaling vectors (caller order).  u == NULL and v == NULL resets
+ * both to ones.  iters sets the iteration counter. */
+int sk_set_state(sk_plan* plan, const double* u, const double* v, int iters);
+
+/* Geometry, sizes and memory of a plan. */
+int sk_plan_info(const sk_plan* plan, sk_info* info);
+
+/* ----------------------------------------------------- stage entry points --
+ * These expose single steps of the fast summation for testing and profiling.
+ */
+
+/* The coefficients b_k, k in I_N, of the regularized kernel in torus
+ * coordinates (Eq. (ansatz_NFFT)); out holds N^d doubles, entry
+ * [(k_1+N/2) ... (k_d+N/2)] row-major.  Host or device pointer. */
+int sk_fourier_coefficients(sk_plan* plan, double* out, void* stream);
+
+/* Adjoint NFFT of weights w on cloud `set` (inner sum of Eq. (fastsum)):
+ * fhat[k] = sum_j w_j exp(-2 pi i k.z_j), k in {-N/2..N/2}^d, z the torus
+ * coordinates; fhat holds (N+1)^d complex values as interleaved (re, im)
+ * doubles, row-major with index k_t + N/2.  Uses spreading, FFT and the
+ * window deconvolution of the plan's precision. */
+int sk_adjoint_nfft(sk_plan* plan, int set, const double* w, double* fhat, void* stream);
+
+/* NFFT on cloud `set` (outer sum of Eq. (fastsum)) of a Hermitian coefficient
+ * array (fhat[-k] = conj(fhat[k]); layout as in sk_adjoint_nfft):
+ * f_j = Re sum_{k in I_N} fhat[k] exp(2 pi i k.z_j), computed as
+ * sum_{k in {-N/2..N/2}^d} c_k fhat[k] exp(2 pi i k.z_j) with
+ * c_k = (1[k in I_N] + 1[-k in I_N]) / 2.  The kernel products use the same
+ * real part of the paper's sum over I_N. */
+int sk_nfft(sk_plan* plan, int set, const double* fhat, double* f, void* stream);
+
+/* Per-stage device times.  enable = 1 turns on CUDA-event timing of every
+ * stage on the plan's stream (and disables graph replay); enable = 0 turns it
+ * off.  ms_out (may be NULL) receives SK_NSTAGES accumulated milliseconds,
+ * counts_out (may be NULL) the number of launches timed per stage; both are
+ * reset after reading. */
+enum { SK_STAGE_SPREAD = 0, SK_STAGE_FFT = 1, SK_STAGE_INTERP = 2, SK_STAGE_OTHER = 3,
+       SK_STAGE_DIRECT = 4, SK_NSTAGES = 5 };
+int sk_stage_times(sk_plan* plan, int enable, double* ms_out, int64_t* counts_out);
+
+/* Number of kernels this plan has launched (graph replays count every kernel node). */
+int64_t sk_launch_count(const sk_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SK_H */

@@ -1,0 +1,1107 @@
+// C ABI of the library (include/sk.h): plan construction, the two half-steps
+// of Sinkhorn's iteration (Alg. 3) as sequences of device kernels, CUDA-graph
+// replay of an iteration, and the stage entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sk_internal.cuh"
+#include "sk_plan_kernels.cuh"
+
+using namespace sk;
+
+struct sk_plan {
+    int d = 0;
+    int64_t n = 0, m = 0;
+    double eps = 0, r = 0;
+    sk_nfft_params prm{};
+    int precision = SK_FP32;
+    int method = SK_METHOD_NFFT;
+    int N = 0, h = 0, n_os = 0, log2n = 0, W = 0, B = 0, nb[3] = {1, 1, 1}, nbins = 0;
+    double beta = 0, knorm = 0;
+    double center[3] = {0, 0, 0}, scale = 1, eps_s = 0;
+    int nearfield = 0;
+    KernelParams kp{};
+    Cloud X, Y;
+    FftPlan fft;
+    size_t grid_elems = 0;
+    double* bk = nullptr;       // N^d FP64
+    double* psihat = nullptr;   // 2h+1 FP64
+    double* partial = nullptr;  // reduction partials
+    int partial_blocks = 0;
+    unsigned* ticket = nullptr;
+    double* stats = nullptr;    // slots of 3 doubles
+    int* status = nullptr;
+    double* pinned = nullptr;   // host pinned readback area
+    double Ha = 0, Hb = 0;      // entropies of a and b
+    cudaStream_t ps = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_kernels = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;      // pairs
+    std::vector<int> tev_stage;
+    size_t tev_used = 0;
+    double stage_ms[SK_NSTAGES] = {0};
+    int64_t stage_cnt[SK_NSTAGES] = {0};
+    int iters = 0;
+    int64_t launches = 0;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    int device = 0;
+};
+
+namespace {
+
+enum Slot { SLOT_ROW = 0, SLOT_COL = 1, SLOT_RES_ROW = 2, SLOT_RES_COL = 3, SLOT_LOG = 4, NSLOTS = 6 };
+
+struct Fail {
+    int code;
+};
+
+thread_local char g_last_error[256] = "";
+
+[[noreturn]] void cuda_fail(cudaError_t e, int line) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "sk_api.cu:%d: %s", line, cudaGetErrorString(e));
+    cudaGetLastError();
+    throw Fail{e == cudaErrorMemoryAllocation ? SK_ERR_NOMEM : SK_ERR_CUDA};
+}
+
+#define CK(x)                                     \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) cuda_fail(e_, __LINE__); \
+    } while (0)
+
+inline unsigned nblk(int64_t n, int t = 256) { return unsigned((n + t - 1) / t); }
+
+void* dalloc(sk_plan* P, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{SK_ERR_NOMEM};
+    }
+    P->allocs.push_back(p);
+    P->bytes += int64_t(bytes);
+    return p;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array of `count` doubles: the pointer itself if it is
+// device memory, else `staging` after an async host-to-device copy.
+const double* device_view(sk_plan* P, const double* p, int64_t count, double* staging) {
+    if (is_device_ptr(p)) return p;
+    CK(cudaMemcpyAsync(staging, p, size_t(count) * sizeof(double), cudaMemcpyHostToDevice, P->ps));
+    return staging;
+}
+
+void enter(sk_plan* P, void* stream) {
+    CK(cudaSetDevice(P->device));
+    CK(cudaEventRecord(P->ev_in, static_cast<cudaStream_t>(stream)));
+    CK(cudaStreamWaitEvent(P->ps, P->ev_in, 0));
+}
+
+void leave(sk_plan* P, void* stream) {
+    CK(cudaEventRecord(P->ev_out, P->ps));
+    CK(cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), P->ev_out, 0));
+}
+
+// ------------------------------------------------------------ stage timing
+int stage_begin(sk_plan* P, int stage) {
+    if (!P->timing) return -1;
+    if (P->tev_used * 2 + 2 > P->tev.size()) {
+        for (int k = 0; k < 256; ++k) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            P->tev.push_back(e);
+        }
+        P->tev_stage.resize(P->tev.size() / 2);
+    }
+    const int idx = int(P->tev_used++);
+    P->tev_stage[idx] = stage;
+    CK(cudaEventRecord(P->tev[2 * idx], P->ps));
+    return idx;
+}
+
+void stage_end(sk_plan* P, int idx) {
+    if (idx < 0) return;
+    CK(cudaEventRecord(P->tev[2 * idx + 1], P->ps));
+}
+
+void stage_resolve(sk_plan* P) {
+    if (P->tev_used == 0) return;
+    CK(cudaStreamSynchronize(P->ps));
+    for (size_t k = 0; k < P->tev_used; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, P->tev[2 * k], P->tev[2 * k + 1]));
+        P->stage_ms[P->tev_stage[k]] += ms;
+        P->stage_cnt[P->tev_stage[k]] += 1;
+    }
+    P->tev_used = 0;
+}
+
+// ------------------------------------------------------------ host math
+// Derivatives 0..p-1 of K(rho) = exp(g(rho)), g = -rho^r / eps, at rho0, from
+// f^(k+1) = sum_j binom(k, j) g^(j+1) f^(k-j).
+void kernel_derivatives(double rho0, double eps, double r, int p, double* f) {
+    double g[kMaxP + 1];
+    g[0] = -std::pow(rho0, r) / eps;
+    for (int j = 1; j <= p; ++j) {
+        double fall = 1.0;
+        for (int q = 0; q < j; ++q) fall *= (r - q);
+        g[j] = -fall * std::pow(rho0, r - j) / eps;
+    }
+    f[0] = std::exp(g[0]);
+    for (int k = 0; k + 1 < p; ++k) {
+        double s = 0.0, binom = 1.0;
+        for (int j = 0; j <= k; ++j) {
+            s += binom * g[j + 1] * f[k - j];
+            binom = binom * double(k - j) / double(j + 1);
+        }
+        f[k + 1] = s;
+    }
+}
+
+// Solve A x = b (size k <= 2 kMaxP) by Gaussian elimination with partial pivoting.
+bool solve_dense(int k, double* A, double* b) {
+    for (int c = 0; c < k; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < k; ++r)
+            if (std::fabs(A[r * k + c]) > std::fabs(A[piv * k + c])) piv = r;
+        if (A[piv * k + c] == 0.0) return false;
+        if (piv != c) {
+            for (int j = 0; j < k; ++j) std::swap(A[c * k + j], A[piv * k + j]);
+            std::swap(b[c], b[piv]);
+        }
+        for (int r = c + 1; r < k; ++r) {
+            const double f = A[r * k + c] / A[c * k + c];
+            for (int j = c; j < k; ++j) A[r * k + j] -= f * A[c * k + j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int c = k - 1; c >= 0; --c) {
+        double s = b[c];
+        for (int j = c + 1; j < k; ++j) s -= A[c * k + j] * b[j];
+        b[c] = s / A[c * k + c];
+    }
+    return true;
+}
+
+double falling(int e, int j) {  // e! / (e - j)!
+    double v = 1.0;
+    for (int q = 0; q < j; ++q) v *= double(e - q);
+    return v;
+}
+
+// Two-point Taylor boundary polynomial in tau = (rho - L)/(1/2 - L): value and
+// derivatives 0..p-1 of K at rho = L, derivatives 1..p-1 zero at rho = 1/2.
+bool boundary_coefficients(KernelParams& kp) {
+    const int p = kp.p;
+    const double delta = 0.5 - kp.L;
+    double f[kMaxP];
+    kernel_derivatives(kp.L, kp.eps_s, kp.r, p, f);
+    double fact = 1.0;
+    for (int j = 0; j < p; ++j) {
+        if (j > 0) fact *= j;
+        kp.kb[j] = f[j] * std::pow(delta, j) / fact;
+    }
+    const int q = p - 1;
+    if (q == 0) return true;
+    double A[kMaxP * kMaxP], rhs[kMaxP];
+    for (int row = 0; row < q; ++row) {
+        const int order = row + 1;
+        double s = 0.0;
+        for (int e = order; e < p; ++e) s += kp.kb[e] * falling(e, order);
+        rhs[row] = -s;
+        for (int c = 0; c < q; ++c) A[row * q + c] = falling(p + c, order);
+    }
+    if (!solve_dense(q, A, rhs)) return false;
+    for (int c = 0; c < q; ++c) kp.kb[p + c] = rhs[c];
+    return true;
+}
+
+// Near-field polynomial sum_q ki[q] (rho/eps_I)^(2q) matching derivatives
+// 0..p-1 of K at rho = eps_I.
+bool nearfield_coefficients(KernelParams& kp) {
+    const int p = kp.p;
+    double f[kMaxP];
+    kernel_derivatives(kp.eps_I, kp.eps_s, kp.r, p, f);
+    double A[kMaxP * kMaxP], rhs[kMaxP];
+    for (int j = 0; j < p; ++j) {
+        rhs[j] = f[j] * std::pow(kp.eps_I, j);
+        for (int q = 0; q < p; ++q) A[j * p + q] = (2 * q >= j) ? falling(2 * q, j) : 0.0;
+    }
+    if (!solve_dense(p, A, rhs)) return false;
+    for (int q = 0; q < p; ++q) kp.ki[q] = rhs[q];
+    return true;
+}
+
+bool even_integer(double r) { return std::floor(r) == r && (int64_t(r) % 2 == 0); }
+
+// ------------------------------------------------------------ reductions
+// Reduce a partial table of `nf` fields with the given ops to host doubles.
+void combine_to_host(sk_plan* P, int nblocks, int nf, const int* ops, double* host) {
+    double* out = P->stats + 3 * NSLOTS;   // scratch after the slots
+    k_combine<<<1, 32, 0, P->ps>>>(P->partial, nblocks, nf, ops[0], nf > 1 ? ops[1] : 0, nf > 2 ? ops[2] : 0,
+                                   nf > 3 ? ops[3] : 0, nf > 4 ? ops[4] : 0, nf > 5 ? ops[5] : 0,
+                                   nf > 6 ? ops[6] : 0, out);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(P->pinned, out, size_t(nf) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    std::memcpy(host, P->pinned, size_t(nf) * sizeof(double));
+}
+
+constexpr int kRedBlocks = 256;
+
+// ------------------------------------------------------------ point clouds
+template <typename T>
+void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, int64_t n) {
+    c.n = n;
+    for (int t = 0; t < P->d; ++t) c.coord[t] = dalloc(P, size_t(n) * sizeof(T));
+    c.perm = static_cast<int*>(dalloc(P, size_t(n) * sizeof(int)));
+    c.marg = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
+    c.scal = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
+    c.t = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
+    c.work = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
+    c.stage = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
+    c.bin_start = static_cast<int*>(dalloc(P, size_t(P->nbins + 1) * sizeof(int)));
+
+    // temporaries
+    T* uo[3] = {nullptr, nullptr, nullptr};
+    T* us[3] = {nullptr, nullptr, nullptr};
+    void* tmp_u = nullptr;
+    int *bin = nullptr, *count = nullptr, *cursor = nullptr, *nsub = nullptr, *suboff = nullptr;
+    CK(cudaMallocAsync(&tmp_u, size_t(n) * 3 * sizeof(T), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&bin), size_t(n) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&count), size_t(P->nbins) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&cursor), size_t(P->nbins) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&nsub), size_t(P->nbins) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&suboff), size_t(P->nbins + 1) * sizeof(int), P->ps));
+    for (int t = 0; t < 3; ++t) {
+        uo[t] = static_cast<T*>(tmp_u) + size_t(t) * n;
+        us[t] = t < P->d ? static_cast<T*>(c.coord[t]) : uo[t];
+    }
+    CK(cudaMemsetAsync(count, 0, size_t(P->nbins) * sizeof(int), P->ps));
+    CK(cudaMemsetAsync(cursor, 0, size_t(P->nbins) * sizeof(int), P->ps));
+    launch_prepare_points<T>(xdev, n, P->d, P->center, P->scale, P->n_os, P->B, P->nb, P->prm.m_w, uo, bin, count,
+                             P->status, P->ps);
+    CK(cudaGetLastError());
+    k_scan_exclusive<<<1, 1024, 0, P->ps>>>(count, c.bin_start, P->nbins);
+    CK(cudaGetLastError());
+    k_scatter_perm<<<nblk(n), 256, 0, P->ps>>>(bin, n, c.bin_start, cursor, c.perm);
+    CK(cudaGetLastError());
+    launch_gather_points<T>(c.perm, n, P->d, uo, us, P->ps);
+    CK(cudaGetLastError());
+    k_gather<<<nblk(n), 256, 0, P->ps>>>(wdev, c.perm, n, c.marg);
+    CK(cudaGetLastError());
+    k_count_subs<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, P->nbins, kSpreadMaxPts, nsub);
+    CK(cudaGetLastError());
+    k_scan_exclusive<<<1, 1024, 0, P->ps>>>(nsub, suboff, P->nbins);
+    CK(cudaGetLastError());
+    int total = 0;
+    CK(cudaMemcpyAsync(&total, suboff + P->nbins, sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    c.nsub = total;
+    c.sub_start = static_cast<int*>(dalloc(P, size_t(std::max(total, 1)) * sizeof(int)));
+    c.sub_count = static_cast<int*>(dalloc(P, size_t(std::max(total, 1)) * sizeof(int)));
+    c.sub_bin = static_cast<int*>(dalloc(P, size_t(std::max(total, 1)) * sizeof(int)));
+    k_fill_subs<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, suboff, P->nbins, kSpreadMaxPts, c.sub_start,
+                                                  c.sub_count, c.sub_bin);
+    CK(cudaGetLastError());
+    k_fill<<<nblk(n), 256, 0, P->ps>>>(c.scal, n, 1.0);
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(tmp_u, P->ps));
+    CK(cudaFreeAsync(bin, P->ps));
+    CK(cudaFreeAsync(count, P->ps));
+    CK(cudaFreeAsync(cursor, P->ps));
+    CK(cudaFreeAsync(nsub, P->ps));
+    CK(cudaFreeAsync(suboff, P->ps));
+}
+
+template <typename T>
+void build_tables(sk_plan* P) {
+    const int d = P->d, N = P->N, h = P->h;
+    int64_t nN = 1;
+    for (int t = 0; t < d; ++t) nN *= N;
+    P->bk = static_cast<double*>(dalloc(P, size_t(nN) * sizeof(double)));
+    double* tmp = nullptr;
+    double* costab = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), size_t(nN) * sizeof(double), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&costab), size_t(N) * sizeof(double), P->ps));
+    k_cos_table<<<nblk(N), 256, 0, P->ps>>>(costab, N);
+    CK(cudaGetLastError());
+    // samples -> d cosine passes, ping-ponging so the result ends in P->bk
+    double* bufs[2] = {P->bk, tmp};
+    int cur = (d % 2 == 0) ? 0 : 1;
+    k_sample_kernel<<<nblk(nN), 256, 0, P->ps>>>(bufs[cur], N, d, P->kp);
+    CK(cudaGetLastError());
+    for (int axis = 0; axis < d; ++axis) {
+        k_cos_dft_axis<<<nblk(nN), 256, 0, P->ps>>>(bufs[cur], bufs[1 - cur], N, d, axis, costab);
+        CK(cudaGetLastError());
+        cur = 1 - cur;
+    }
+    // now bufs[cur] == P->bk holds N^d * b_k
+    P->psihat = static_cast<double*>(dalloc(P, size_t(2 * h + 1) * sizeof(double)));
+    k_window_transform<<<nblk(2 * h + 1), 256, 0, P->ps>>>(P->psihat, h, P->n_os, P->prm.m_w, P->beta);
+    CK(cudaGetLastError());
+    int64_t mtotal = h + 1;
+    for (int t = 0; t < d - 1; ++t) mtotal *= (2 * h + 1);
+    P->fft.mult = dalloc(P, size_t(mtotal) * sizeof(T));
+    const double inv_norm = 1.0 / double(nN);
+    launch_build_mult<T>(static_cast<T*>(P->fft.mult), d, h, P->bk, inv_norm, P->psihat, mtotal, P->ps);
+    CK(cudaGetLastError());
+    // keep b_k itself (normalized) for sk_fourier_coefficients
+    k_scale<<<nblk(nN), 256, 0, P->ps>>>(P->bk, nN, inv_norm);
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(tmp, P->ps));
+    CK(cudaFreeAsync(costab, P->ps));
+    // twiddles
+    P->fft.tw = dalloc(P, size_t(P->n_os / 2) * sizeof(typename Cplx<T>::type));
+    launch_twiddles<T>(P->fft.tw, P->n_os, P->ps);
+    CK(cudaGetLastError());
+}
+
+template <typename T>
+void build_grid(sk_plan* P) {
+    using C = typename Cplx<T>::type;
+    const int64_t n = P->n_os, H = P->h + 1, K = 2 * P->h + 1;
+    FftPlan& f = P->fft;
+    f.d = P->d;
+    f.n = P->n_os;
+    f.log2n = P->log2n;
+    f.h = P->h;
+    f.psihat = P->psihat;
+    if (P->d == 1) {
+        P->grid_elems = size_t(2 * n);
+        f.A1 = dalloc(P, size_t(2 * H) * sizeof(C));
+        f.A3 = nullptr;
+    } else if (P->d == 2) {
+        P->grid_elems = size_t(n * n);
+        f.A1 = dalloc(P, size_t(n * H) * sizeof(C));
+        f.A3 = dalloc(P, size_t(K * H) * sizeof(C));
+    } else {
+        P->grid_elems = size_t(n * n * n);
+        f.A1 = dalloc(P, size_t(n * n * H) * sizeof(C));
+        f.A2 = dalloc(P, size_t(n * K * H) * sizeof(C));
+        f.A3 = dalloc(P, size_t(K * K * H) * sizeof(C));
+    }
+    f.grid = dalloc(P, P->grid_elems * sizeof(T));
+    CK(cudaMemsetAsync(f.grid, 0, P->grid_elems * sizeof(T), P->ps));
+}
+
+template <typename T>
+void prepare_kernels(sk_plan* P) {
+    SpreadArgs a{};
+    a.nsub = 0;
+    CK(launch_spread<T>(P->d, P->W, a, P->ps));
+    CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
+}
+
+// ------------------------------------------------------------ products
+Epilogue make_epilogue(sk_plan* P, int mode, Cloud& dst, int slot, double* out) {
+    Epilogue e;
+    e.mode = mode;
+    e.n = dst.n;
+    e.perm = dst.perm;
+    e.out = out;
+    e.t_store = dst.t;
+    e.marg = dst.marg;
+    e.scal = dst.scal;
+    e.partial = P->partial;
+    e.ticket = P->ticket;
+    e.result = P->stats + 3 * slot;
+    e.status = P->status;
+    return e;
+}
+
+template <typename T>
+void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
+    int st = stage_begin(P, SK_STAGE_OTHER);
+    CK(cudaMemsetAsync(P->fft.grid, 0, P->grid_elems * sizeof(T), P->ps));
+    stage_end(P, st);
+    SpreadArgs a{};
+    for (int t = 0; t < 3; ++t) a.coord[t] = src.coord[t];
+    a.w = w;
+    a.sub_start = src.sub_start;
+    a.sub_count = src.sub_count;
+    a.sub_bin = src.sub_bin;
+    a.nsub = src.nsub;
+    a.n_os = P->n_os;
+    for (int t = 0; t < 3; ++t) a.nb[t] = P->nb[t];
+    a.B = P->B;
+    a.beta = P->beta;
+    a.knorm = P->knorm;
+    a.grid = P->fft.grid;
+    st = stage_begin(P, SK_STAGE_SPREAD);
+    CK(launch_spread<T>(P->d, P->W, a, P->ps));
+    if (src.nsub > 0) ++P->launches;
+    stage_end(P, st);
+}
+
+template <typename T>
+void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
+    InterpArgs a{};
+    for (int t = 0; t < 3; ++t) a.coord[t] = dst.coord[t];
+    a.n = dst.n;
+    a.n_os = P->n_os;
+    a.beta = P->beta;
+    a.knorm = P->knorm;
+    a.grid = P->fft.grid;
+    int st = stage_begin(P, SK_STAGE_INTERP);
+    CK(launch_interp<T>(P->d, P->W, a, e, &P->launches, P->ps));
+    stage_end(P, st);
+}
+
+// One product into `dst` from `src` with sorted source weights `w`.
+template <typename T>
+void product(sk_plan* P, Cloud& src, const double* w, Cloud& dst, const Epilogue& e) {
+    if (P->method == SK_METHOD_DIRECT) {
+        DirectArgs a{};
+        for (int t = 0; t < 3; ++t) { a.tcoord[t] = dst.coord[t]; a.scoord[t] = src.coord[t]; }
+        a.nt = dst.n;
+        a.w = w;
+        a.ns = src.n;
+        a.coef = 1.0 / (P->eps_s * std::pow(double(P->n_os), P->r));
+        a.r = P->r;
+        int st = stage_begin(P, SK_STAGE_DIRECT);
+        CK(launch_direct<T>(P->d, a, e, &P->launches, P->ps));
+        stage_end(P, st);
+        return;
+    }
+    if (P->nearfield) throw Fail{SK_ERR_UNSUPPORTED};
+    spread_into_grid<T>(P, src, w);
+    int st = stage_begin(P, SK_STAGE_FFT);
+    CK(launch_fft_convolve<T>(P->fft, P->ps, &P->launches));
+    stage_end(P, st);
+    interp_from_grid<T>(P, dst, e);
+}
+
+template <typename T>
+void iteration(sk_plan* P) {
+    // odd half-step: u = a ./ (K v)
+    product<T>(P, P->Y, P->Y.scal, P->X, make_epilogue(P, EPI_UPDATE, P->X, SLOT_ROW, nullptr));
+    // even half-step: v = b ./ (K^T u)
+    product<T>(P, P->X, P->X.scal, P->Y, make_epilogue(P, EPI_UPDATE, P->Y, SLOT_COL, nullptr));
+}
+
+void run_iteration(sk_plan* P) {
+    if (P->precision == SK_FP32)
+        iteration<float>(P);
+    else
+        iteration<double>(P);
+}
+
+void destroy_graph(sk_plan* P) {
+    if (P->gexec) {
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+    }
+}
+
+void ensure_graph(sk_plan* P) {
+    if (P->gexec) return;
+    const int64_t before = P->launches;
+    CK(cudaStreamBeginCapture(P->ps, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t g = nullptr;
+    try {
+        run_iteration(P);
+    } catch (...) {
+        cudaStreamEndCapture(P->ps, &g);
+        if (g) cudaGraphDestroy(g);
+        P->launches = before;
+        throw;
+    }
+    CK(cudaStreamEndCapture(P->ps, &g));
+    P->graph_kernels = P->launches - before;
+    P->launches = before;
+    cudaError_t e = cudaGraphInstantiate(&P->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+}
+
+void iterate(sk_plan* P, int k) {
+    for (int i = 0; i < k; ++i) {
+        if (P->timing) {
+            run_iteration(P);
+        } else {
+            ensure_graph(P);
+            CK(cudaGraphLaunch(P->gexec, P->ps));
+            P->launches += P->graph_kernels;
+        }
+        ++P->iters;
+    }
+}
+
+double read_slot(sk_plan* P, int slot, int field) {
+    CK(cudaMemcpyAsync(P->pinned, P->stats + 3 * slot + field, sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    return P->pinned[0];
+}
+
+int read_status(sk_plan* P) {
+    int st = 0;
+    CK(cudaMemcpyAsync(P->pinned, P->status, sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    std::memcpy(&st, P->pinned, sizeof(int));
+    return st;
+}
+
+void clear_status(sk_plan* P) { CK(cudaMemsetAsync(P->status, 0, sizeof(int), P->ps)); }
+
+double sum_marg_log(sk_plan* P, const Cloud& c) {
+    k_sum_marg_log<<<kRedBlocks, 256, 0, P->ps>>>(c.marg, c.scal, c.n, P->partial);
+    CK(cudaGetLastError());
+    ++P->launches;
+    const int ops[1] = {0};
+    double v = 0.0;
+    combine_to_host(P, kRedBlocks, 1, ops, &v);
+    ++P->launches;
+    return v;
+}
+
+template <typename T>
+void final_report(sk_plan* P, sk_result* res) {
+    product<T>(P, P->Y, P->Y.scal, P->X, make_epilogue(P, EPI_RESID, P->X, SLOT_RES_ROW, nullptr));
+    product<T>(P, P->X, P->X.scal, P->Y, make_epilogue(P, EPI_RESID, P->Y, SLOT_RES_COL, nullptr));
+    CK(cudaMemcpyAsync(P->pinned, P->stats, sizeof(double) * 3 * NSLOTS, cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    double st[3 * NSLOTS];
+    std::memcpy(st, P->pinned, sizeof(st));
+    const double row2 = st[3 * SLOT_RES_ROW + 0], uKv = st[3 * SLOT_RES_ROW + 2];
+    const double col2 = st[3 * SLOT_RES_COL + 0];
+    const double la = sum_marg_log(P, P->X), lb = sum_marg_log(P, P->Y);
+    res->s = P->eps * (1.0 + la + lb - uKv);
+    res->s_upper = res->s + P->eps * (P->Ha + P->Hb);
+    res->err_row = std::sqrt(row2);
+    res->err_col = std::sqrt(col2);
+    res->marg_err = res->err_row + res->err_col;
+    res->total_iters = P->iters;
+}
+
+void write_out(sk_plan* P, const Cloud& c, const double* sorted, double* out) {
+    if (!out) return;
+    if (is_device_ptr(out)) {
+        k_scatter<<<nblk(c.n), 256, 0, P->ps>>>(sorted, c.perm, c.n, out);
+        CK(cudaGetLastError());
+        ++P->launches;
+    } else {
+        k_scatter<<<nblk(c.n), 256, 0, P->ps>>>(sorted, c.perm, c.n, c.stage);
+        CK(cudaGetLastError());
+        ++P->launches;
+        CK(cudaMemcpyAsync(out, c.stage, size_t(c.n) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+    }
+}
+
+void read_in(sk_plan* P, const Cloud& c, const double* in, double* sorted) {
+    const double* src = device_view(P, in, c.n, c.stage);
+    k_gather<<<nblk(c.n), 256, 0, P->ps>>>(src, c.perm, c.n, sorted);
+    CK(cudaGetLastError());
+    ++P->launches;
+}
+
+int fail_code(const Fail& f) { return f.code; }
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char* sk_last_error(void) { return g_last_error; }
+
+const char* sk_error_string(int status) {
+    switch (status) {
+        case SK_OK: return "ok";
+        case SK_ERR_ARG: return "invalid argument";
+        case SK_ERR_DOMAIN: return "coordinates not finite or outside the grid";
+        case SK_ERR_WEIGHTS: return "weights negative, not finite or not summing to 1";
+        case SK_ERR_NOMEM: return "device allocation failed";
+        case SK_ERR_UNDERFLOW: return "a kernel sum was <= 0 or not finite";
+        case SK_ERR_NOT_CONVERGED: return "not converged within max_iter";
+        case SK_ERR_TIMEOUT: return "bounded device wait ran out";
+        case SK_ERR_CUDA: return "CUDA runtime error";
+        case SK_ERR_UNSUPPORTED: return "not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+int sk_default_params(sk_nfft_params* prm) {
+    if (!prm) return SK_ERR_ARG;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->N = 64;
+    prm->sigma = 2.0;
+    prm->m_w = 4;
+    prm->p = 8;
+    prm->eps_B = 0.1;
+    prm->eps_I = 1.0 / 16.0;
+    prm->precision = SK_FP32;
+    prm->user_geometry = 0;
+    prm->scale = 1.0;
+    return SK_OK;
+}
+
+static int validate_params(int d, const sk_nfft_params& p, int& n_os, int& log2n) {
+    if (p.N < 8 || (p.N % 2) != 0) return SK_ERR_ARG;
+    if (!(p.sigma > 1.0) || !std::isfinite(p.sigma)) return SK_ERR_ARG;
+    const double nd = p.sigma * p.N;
+    n_os = int(std::lround(nd));
+    if (std::fabs(nd - n_os) > 1e-9) return SK_ERR_ARG;
+    if (n_os < 16 || (n_os & (n_os - 1)) != 0) return SK_ERR_ARG;
+    if (n_os > (d == 1 ? 4096 : 1024)) return SK_ERR_ARG;
+    if (p.N > n_os / 2) return SK_ERR_ARG;
+    log2n = 0;
+    while ((1 << log2n) < n_os) ++log2n;
+    if (p.m_w < 2 || p.m_w > 8) return SK_ERR_ARG;
+    if (n_os < 4 * (p.m_w + 1)) return SK_ERR_ARG;
+    if (p.p < 2 || p.p > kMaxP) return SK_ERR_ARG;
+    if (!(p.eps_B > 0.0 && p.eps_B < 0.5)) return SK_ERR_ARG;
+    if (p.precision != SK_FP32 && p.precision != SK_FP64) return SK_ERR_ARG;
+    if (p.user_geometry && !(p.scale > 0.0 && std::isfinite(p.scale))) return SK_ERR_ARG;
+    return SK_OK;
+}
+
+int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, int64_t m, const double* y,
+            const double* b, double eps, double r, const sk_nfft_params* prm, void* stream) {
+    if (!out) return SK_ERR_ARG;
+    *out = nullptr;
+    if (d < 1 || d > 3 || n < 1 || m < 1 || n > INT32_MAX / 2 || m > INT32_MAX / 2) return SK_ERR_ARG;
+    if (!x || !a || !y || !b) return SK_ERR_ARG;
+    if (!(eps > 0.0) || !std::isfinite(eps) || !(r >= 1.0) || !std::isfinite(r)) return SK_ERR_ARG;
+    sk_nfft_params p;
+    if (prm)
+        p = *prm;
+    else
+        sk_default_params(&p);
+    int n_os = 0, log2n = 0;
+    int rc = validate_params(d, p, n_os, log2n);
+    if (rc != SK_OK) return rc;
+    const bool nearfield = !even_integer(r);
+    if (nearfield && !(p.eps_I > 0.0 && p.eps_I < 0.5 - p.eps_B)) return SK_ERR_ARG;
+
+    sk_plan* P = new (std::nothrow) sk_plan();
+    if (!P) return SK_ERR_NOMEM;
+    try {
+        CK(cudaGetDevice(&P->device));
+        P->d = d;
+        P->n = n;
+        P->m = m;
+        P->eps = eps;
+        P->r = r;
+        P->prm = p;
+        P->precision = p.precision;
+        P->N = p.N;
+        P->h = p.N / 2;
+        P->n_os = n_os;
+        P->log2n = log2n;
+        P->W = 2 * p.m_w;
+        P->B = bin_side(d);
+        P->nbins = 1;
+        for (int t = 0; t < 3; ++t) {
+            P->nb[t] = t < d ? (n_os + P->B - 1) / P->B : 1;
+            P->nbins *= P->nb[t];
+        }
+        P->beta = M_PI * (2.0 - 1.0 / p.sigma);
+        P->knorm = double(p.m_w) / std::sinh(P->beta * p.m_w);
+        P->nearfield = nearfield ? 1 : 0;
+
+        CK(cudaStreamCreateWithFlags(&P->ps, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+        CK(cudaMallocHost(reinterpret_cast<void**>(&P->pinned), 64 * sizeof(double)));
+        enter(P, stream);
+
+        const int64_t nmax = std::max(n, m);
+        P->partial_blocks = std::max<int64_t>(interp_blocks<double>(nmax), kRedBlocks);
+        P->partial = static_cast<double*>(dalloc(P, size_t(P->partial_blocks) * 8 * sizeof(double)));
+        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 4));
+        P->stats = static_cast<double*>(dalloc(P, sizeof(double) * (3 * NSLOTS + 8)));
+        P->status = static_cast<int*>(dalloc(P, sizeof(int) * 4));
+        CK(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned) * 4, P->ps));
+        CK(cudaMemsetAsync(P->stats, 0, sizeof(double) * (3 * NSLOTS + 8), P->ps));
+        CK(cudaMemsetAsync(P->status, 0, sizeof(int) * 4, P->ps));
+
+        // inputs on the device (staged through temporaries if on the host)
+        double *xd = nullptr, *yd = nullptr, *ad = nullptr, *bd = nullptr;
+        const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y), adev = is_device_ptr(a), bdev = is_device_ptr(b);
+        std::vector<void*> tmps;
+        auto stage_in = [&](const double* src, bool dev, int64_t cnt) -> const double* {
+            if (dev) return src;
+            double* dst = nullptr;
+            CK(cudaMallocAsync(reinterpret_cast<void**>(&dst), size_t(cnt) * sizeof(double), P->ps));
+            tmps.push_back(dst);
+            CK(cudaMemcpyAsync(dst, src, size_t(cnt) * sizeof(double), cudaMemcpyHostToDevice, P->ps));
+            return dst;
+        };
+        const double* xs = stage_in(x, xdev, n * d);
+        const double* ys = stage_in(y, ydev, m * d);
+        const double* as = stage_in(a, adev, n);
+        const double* bs = stage_in(b, bdev, m);
+        (void)xd;
+        (void)yd;
+        (void)ad;
+        (void)bd;
+
+        // validation: finite coordinates, bounding box; weights
+        const int bounds_ops[7] = {1, 1, 1, 2, 2, 2, 0};
+        double bx[7], by[7];
+        k_point_bounds<<<kRedBlocks, 256, 0, P->ps>>>(xs, n, d, P->partial);
+        CK(cudaGetLastError());
+        combine_to_host(P, kRedBlocks, 7, bounds_ops, bx);
+        k_point_bounds<<<kRedBlocks, 256, 0, P->ps>>>(ys, m, d, P->partial);
+        CK(cudaGetLastError());
+        combine_to_host(P, kRedBlocks, 7, bounds_ops, by);
+        if (bx[6] > 0 || by[6] > 0) throw Fail{SK_ERR_DOMAIN};
+        const int wops[4] = {0, 1, 0, 0};
+        double wa[4], wb[4];
+        k_weight_stats<<<kRedBlocks, 256, 0, P->ps>>>(as, n, P->partial);
+        CK(cudaGetLastError());
+        combine_to_host(P, kRedBlocks, 4, wops, wa);
+        k_weight_stats<<<kRedBlocks, 256, 0, P->ps>>>(bs, m, P->partial);
+        CK(cudaGetLastError());
+        combine_to_host(P, kRedBlocks, 4, wops, wb);
+        if (wa[2] > 0 || wb[2] > 0 || wa[1] < 0 || wb[1] < 0 || std::fabs(wa[0] - 1.0) > 1e-9 ||
+            std::fabs(wb[0] - 1.0) > 1e-9)
+            throw Fail{SK_ERR_WEIGHTS};
+        P->Ha = wa[3];
+        P->Hb = wb[3];
+
+        // geometry
+        if (p.user_geometry) {
+            for (int t = 0; t < 3; ++t) P->center[t] = t < d ? p.center[t] : 0.0;
+            P->scale = p.scale;
+        } else {
+            for (int t = 0; t < 3; ++t)
+                P->center[t] = t < d ? 0.5 * (std::min(bx[t], by[t]) + std::max(bx[3 + t], by[3 + t])) : 0.0;
+            const int rops[1] = {2};
+            double rx = 0, ry = 0;
+            k_point_radius<<<kRedBlocks, 256, 0, P->ps>>>(xs, n, d, P->center[0], P->center[1], P->center[2],
+                                                           P->partial);
+            CK(cudaGetLastError());
+            combine_to_host(P, kRedBlocks, 1, rops, &rx);
+            k_point_radius<<<kRedBlocks, 256, 0, P->ps>>>(ys, m, d, P->center[0], P->center[1], P->center[2],
+                                                           P->partial);
+            CK(cudaGetLastError());
+            combine_to_host(P, kRedBlocks, 1, rops, &ry);
+            const double R = std::sqrt(std::max(rx, ry));
+            P->scale = R > 0.0 ? (0.25 - 0.5 * p.eps_B) / R : 1.0;
+        }
+        P->eps_s = eps * std::pow(P->scale, r);
+
+        // kernel parameters in torus coordinates
+        P->kp.eps_s = P->eps_s;
+        P->kp.r = r;
+        P->kp.L = 0.5 - p.eps_B;
+        P->kp.eps_I = p.eps_I;
+        P->kp.p = p.p;
+        P->kp.nearfield = P->nearfield;
+        if (!boundary_coefficients(P->kp)) throw Fail{SK_ERR_ARG};
+        if (P->nearfield && !nearfield_coefficients(P->kp)) throw Fail{SK_ERR_ARG};
+
+        if (P->precision == SK_FP32) {
+            build_cloud<float>(P, P->X, xs, as, n);
+            build_cloud<float>(P, P->Y, ys, bs, m);
+            build_tables<float>(P);
+            build_grid<float>(P);
+        } else {
+            build_cloud<double>(P, P->X, xs, as, n);
+            build_cloud<double>(P, P->Y, ys, bs, m);
+            build_tables<double>(P);
+            build_grid<double>(P);
+        }
+        for (void* t : tmps) CK(cudaFreeAsync(t, P->ps));
+        // opt the kernels this plan uses into their shared-memory sizes now, so
+        // no attribute call happens while an iteration is being captured
+        if (P->precision == SK_FP32)
+            prepare_kernels<float>(P);
+        else
+            prepare_kernels<double>(P);
+        const int st = read_status(P);
+        if (st & 2) throw Fail{SK_ERR_DOMAIN};
+        leave(P, stream);
+        CK(cudaStreamSynchronize(P->ps));
+    } catch (const Fail& f) {
+        cudaStreamSynchronize(P->ps);
+        cudaGetLastError();
+        sk_destroy(P);
+        return fail_code(f);
+    }
+    *out = P;
+    return SK_OK;
+}
+
+void sk_destroy(sk_plan* P) {
+    if (!P) return;
+    cudaSetDevice(P->device);
+    if (P->ps) cudaStreamSynchronize(P->ps);
+    destroy_graph(P);
+    for (void* p : P->allocs) cudaFree(p);
+    for (cudaEvent_t e : P->tev) cudaEventDestroy(e);
+    if (P->pinned) cudaFreeHost(P->pinned);
+    if (P->ev_in) cudaEventDestroy(P->ev_in);
+    if (P->ev_out) cudaEventDestroy(P->ev_out);
+    if (P->ps) cudaStreamDestroy(P->ps);
+    delete P;
+}
+
+int sk_set_method(sk_plan* P, int method) {
+    if (!P || (method != SK_METHOD_NFFT && method != SK_METHOD_DIRECT)) return SK_ERR_ARG;
+    if (method != P->method) {
+        destroy_graph(P);
+        P->method = method;
+    }
+    return SK_OK;
+}
+
+int sk_kernel_apply(sk_plan* P, int transpose, const double* in, double* out, void* stream) {
+    if (!P || !in || !out || (transpose != 0 && transpose != 1)) return SK_ERR_ARG;
+    try {
+        enter(P, stream);
+        Cloud& src = transpose ? P->X : P->Y;
+        Cloud& dst = transpose ? P->Y : P->X;
+        read_in(P, src, in, src.work);
+        const bool host_out = !is_device_ptr(out);
+        Epilogue e = make_epilogue(P, EPI_APPLY, dst, 0, host_out ? dst.stage : out);
+        if (P->precision == SK_FP32)
+            product<float>(P, src, src.work, dst, e);
+        else
+            product<double>(P, src, src.work, dst, e);
+        if (host_out) {
+            CK(cudaMemcpyAsync(out, dst.stage, size_t(dst.n) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+            CK(cudaStreamSynchronize(P->ps));
+        }
+        leave(P, stream);
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return SK_OK;
+}
+
+int sk_solve(sk_plan* P, int max_iter, double tol, int check_every, double* u_out, double* v_out, sk_result* res,
+             void* stream) {
+    if (!P || max_iter < 0) return SK_ERR_ARG;
+    int rc = SK_OK;
+    try {
+        enter(P, stream);
+        clear_status(P);
+        const int every = check_every > 0 ? check_every : 10;
+        int done = 0;
+        bool converged = false;
+        if (tol > 0.0) {
+            while (done < max_iter) {
+                const int k = std::min(every, max_iter - done);
+                iterate(P, k);
+                done += k;
+                const double row2 = read_slot(P, SLOT_ROW, 0);
+                if (std::sqrt(row2) <= tol) {
+                    converged = true;
+                    break;
+                }
+            }
+            if (!converged) rc = SK_ERR_NOT_CONVERGED;
+        } else {
+            iterate(P, max_iter);
+            done = max_iter;
+        }
+        if (res) {
+            std::memset(res, 0, sizeof(*res));
+            if (P->precision == SK_FP32)
+                final_report<float>(P, res);
+            else
+                final_report<double>(P, res);
+            res->iters = done;
+        }
+        write_out(P, P->X, P->X.scal, u_out);
+        write_out(P, P->Y, P->Y.scal, v_out);
+        if (res || u_out || v_out || tol > 0.0) {
+            const int st = read_status(P);
+            if (st & 1) rc = SK_ERR_UNDERFLOW;
+        }
+        leave(P, stream);
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return rc;
+}
+
+int sk_grad(sk_plan* P, double*, double*, double*, double*, void*) {
+    if (!P) return SK_ERR_ARG;
+    return SK_ERR_UNSUPPORTED;
+}
+
+int sk_get_state(sk_plan* P, double* u, double* v, int* iters) {
+    if (!P) return SK_ERR_ARG;
+    try {
+        CK(cudaSetDevice(P->device));
+        write_out(P, P->X, P->X.scal, u);
+        write_out(P, P->Y, P->Y.scal, v);
+        CK(cudaStreamSynchronize(P->ps));
+        if (iters) *iters = P->iters;
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return SK_OK;
+}
+
+int sk_set_state(sk_plan* P, const double* u, const double* v, int iters) {
+    if (!P || iters < 0) return SK_ERR_ARG;
+    try {
+        CK(cudaSetDevice(P->device));
+        if (u)
+            read_in(P, P->X, u, P->X.scal);
+        else if (!v)
+            k_fill<<<nblk(P->X.n), 256, 0, P->ps>>>(P->X.scal, P->X.n, 1.0);
+        if (v)
+            read_in(P, P->Y, v, P->Y.scal);
+        else if (!u)
+            k_fill<<<nblk(P->Y.n), 256, 0, P->ps>>>(P->Y.scal, P->Y.n, 1.0);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(P->ps));
+        P->iters = iters;
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return SK_OK;
+}
+
+int sk_plan_info(const sk_plan* P, sk_info* info) {
+    if (!P || !info) return SK_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->d = P->d;
+    info->n = P->n;
+    info->m = P->m;
+    info->N = P->N;
+    info->n_os = P->n_os;
+    info->m_w = P->prm.m_w;
+    info->p = P->prm.p;
+    info->precision = P->precision;
+    info->nearfield = P->nearfield;
+    info->eps = P->eps;
+    info->r = P->r;
+    info->eps_scaled = P->eps_s;
+    for (int t = 0; t < 3; ++t) info->center[t] = P->center[t];
+    info->scale = P->scale;
+    info->eps_B = P->prm.eps_B;
+    info->eps_I = P->prm.eps_I;
+    info->n_subproblems_x = P->X.nsub;
+    info->n_subproblems_y = P->Y.nsub;
+    info->device_bytes = P->bytes;
+    return SK_OK;
+}
+
+int sk_fourier_coefficients(sk_plan* P, double* out, void* stream) {
+    if (!P || !out) return SK_ERR_ARG;
+    try {
+        enter(P, stream);
+        int64_t nN = 1;
+        for (int t = 0; t < P->d; ++t) nN *= P->N;
+        CK(cudaMemcpyAsync(out, P->bk, size_t(nN) * sizeof(double), cudaMemcpyDefault, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+        leave(P, stream);
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return SK_OK;
+}
+
+int sk_adjoint_nfft(sk_plan* P, int set, const double* w, double* fhat, void* stream) {
+    if (!P || !w || !fhat || (set != SK_SET_X && set != SK_SET_Y)) return SK_ERR_ARG;
+    try {
+        enter(P, stream);
+        Cloud& c = set == SK_SET_X ? P->X : P->Y;
+        read_in(P, c, w, c.work);
+        int64_t total = 1;
+        for (int t = 0; t < P->d; ++t) total *= (2 * P->h + 1);
+        const bool dev = is_device_ptr(fhat);
+        double* dout = fhat;
+        if (!dev) CK(cudaMallocAsync(reinterpret_cast<void**>(&dout), size_t(2 * total) * sizeof(double), P->ps));
+        if (P->precision == SK_FP32) {
+            spread_into_grid<float>(P, c, c.work);
+            CK(launch_fft_adjoint<float>(P->fft, dout, P->ps, &P->launches));
+        } else {
+            spread_into_grid<double>(P, c, c.work);
+            CK(launch_fft_adjoint<double>(P->fft, dout, P->ps, &P->launches));
+        }
+        if (!dev) {
+            CK(cudaMemcpyAsync(fhat, dout, size_t(2 * total) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+            CK(cudaFreeAsync(dout, P->ps));
+            CK(cudaStreamSynchronize(P->ps));
+        }
+        leave(P, stream);
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return SK_OK;
+}
+
+int sk_nfft(sk_plan* P, int set, const double* fhat, double* f, void* stream) {
+    if (!P || !fhat || !f || (set != SK_SET_X && set != SK_SET_Y)) return SK_ERR_ARG;
+    try {
+        enter(P, stream);
+        Cloud& c = set == SK_SET_X ? P->X : P->Y;
+        int64_t total = 1;
+        for (int t = 0; t < P->d; ++t) total *= (2 * P->h + 1);
+        const double* din = fhat;
+        double* tmp = nullptr;
+        if (!is_device_ptr(fhat)) {
+            CK(cudaMallocAsync(reinterpret_cast<void**>(&tmp), size_t(2 * total) * sizeof(double), P->ps));
+            CK(cudaMemcpyAsync(tmp, fhat, size_t(2 * total) * sizeof(double), cudaMemcpyHostToDevice, P->ps));
+            din = tmp;
+        }
+        const bool host_out = !is_device_ptr(f);
+        Epilogue e = make_epilogue(P, EPI_APPLY, c, 0, host_out ? c.stage : f);
+        if (P->precision == SK_FP32) {
+            CK(launch_fft_forward<float>(P->fft, din, P->ps, &P->launches));
+            interp_from_grid<float>(P, c, e);
+        } else {
+            CK(launch_fft_forward<double>(P->fft, din, P->ps, &P->launches));
+            interp_from_grid<double>(P, c, e);
+        }
+        if (tmp) CK(cudaFreeAsync(tmp, P->ps));
+        if (host_out) {
+            CK(cudaMemcpyAsync(f, c.stage, size_t(c.n) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+            CK(cudaStreamSynchronize(P->ps));
+        }
+        leave(P, stream);
+    } catch (const Fail& f2) {
+        return fail_code(f2);
+    }
+    return SK_OK;
+}
+
+int sk_stage_times(sk_plan* P, int enable, double* ms_out, int64_t* counts_out) {
+    if (!P || (enable != 0 && enable != 1)) return SK_ERR_ARG;
+    try {
+        CK(cudaSetDevice(P->device));
+        stage_resolve(P);
+        if (ms_out)
+            for (int s = 0; s < SK_NSTAGES; ++s) ms_out[s] = P->stage_ms[s];
+        if (counts_out)
+            for (int s = 0; s < SK_NSTAGES; ++s) counts_out[s] = P->stage_cnt[s];
+        for (int s = 0; s < SK_NSTAGES; ++s) {
+            P->stage_ms[s] = 0.0;
+            P->stage_cnt[s] = 0;
+        }
+        P->timing = enable == 1;
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return SK_OK;
+}
+
+int64_t sk_launch_count(const sk_plan* P) { return P ? P->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,403 @@
+// Plan-time and bookkeeping kernels: input validation reductions, scaling
+// into the torus and bin sorting, the coefficient table of the regularized
+// kernel (Eq. (ansatz_NFFT)), the window transform, twiddles, and the FP64
+// gathers / scatters / reductions of the solver.
+#include "sk_plan_kernels.cuh"
+
+namespace sk {
+
+// ------------------------------------------------------------ reductions
+// Per-block partials of (min_t, max_t for t < d, count of non-finite values).
+__global__ void k_point_bounds(const double* __restrict__ x, int64_t n, int d, double* __restrict__ partial) {
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double bad = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        for (int t = 0; t < d; ++t) {
+            const double v = x[i * d + t];
+            if (!isfinite(v)) { bad += 1.0; continue; }
+            mn[t] = fmin(mn[t], v);
+            mx[t] = fmax(mx[t], v);
+        }
+    }
+    __shared__ double s[7][256];
+    for (int t = 0; t < 3; ++t) { s[t][threadIdx.x] = mn[t]; s[3 + t][threadIdx.x] = mx[t]; }
+    s[6][threadIdx.x] = bad;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            for (int t = 0; t < 3; ++t) {
+                s[t][threadIdx.x] = fmin(s[t][threadIdx.x], s[t][threadIdx.x + w]);
+                s[3 + t][threadIdx.x] = fmax(s[3 + t][threadIdx.x], s[3 + t][threadIdx.x + w]);
+            }
+            s[6][threadIdx.x] += s[6][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int f = 0; f < 7; ++f) partial[blockIdx.x * 7 + f] = s[f][0];
+}
+
+// Per-block partials of (max |x_i - c|^2).
+__global__ void k_point_radius(const double* __restrict__ x, int64_t n, int d, double c0, double c1, double c2,
+                               double* __restrict__ partial) {
+    const double c[3] = {c0, c1, c2};
+    double mx = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        double r2 = 0.0;
+        for (int t = 0; t < d; ++t) {
+            const double dd = x[i * d + t] - c[t];
+            r2 += dd * dd;
+        }
+        mx = fmax(mx, r2);
+    }
+    __shared__ double s[256];
+    s[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
+}
+
+// Per-block partials of (sum w, min w, count non-finite, -sum w log w).
+__global__ void k_weight_stats(const double* __restrict__ w, int64_t n, double* __restrict__ partial) {
+    double sum = 0.0, mn = INFINITY, bad = 0.0, ent = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double v = w[i];
+        if (!isfinite(v)) { bad += 1.0; continue; }
+        sum += v;
+        mn = fmin(mn, v);
+        if (v > 0.0) ent -= v * log(v);
+    }
+    __shared__ double s[4][256];
+    s[0][threadIdx.x] = sum;
+    s[1][threadIdx.x] = mn;
+    s[2][threadIdx.x] = bad;
+    s[3][threadIdx.x] = ent;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + k];
+            s[1][threadIdx.x] = fmin(s[1][threadIdx.x], s[1][threadIdx.x + k]);
+            s[2][threadIdx.x] += s[2][threadIdx.x + k];
+            s[3][threadIdx.x] += s[3][threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int f = 0; f < 4; ++f) partial[blockIdx.x * 4 + f] = s[f][0];
+}
+
+// Per-block partial of sum_i marg_i log(scal_i).
+__global__ void k_sum_marg_log(const double* __restrict__ marg, const double* __restrict__ scal, int64_t n,
+                               double* __restrict__ partial) {
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double a = marg[i];
+        if (a > 0.0) acc += a * log(scal[i]);
+    }
+    __shared__ double s[256];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
+}
+
+// Combine nblocks rows of nf fields; op[f] = 0 sum, 1 min, 2 max.  One block.
+__global__ void k_combine(const double* __restrict__ partial, int nblocks, int nf, int op0, int op1, int op2,
+                          int op3, int op4, int op5, int op6, double* __restrict__ out) {
+    const int ops[7] = {op0, op1, op2, op3, op4, op5, op6};
+    if (threadIdx.x >= nf) return;
+    const int f = threadIdx.x;
+    double acc = ops[f] == 0 ? 0.0 : (ops[f] == 1 ? INFINITY : -INFINITY);
+    for (int b = 0; b < nblocks; ++b) {
+        const double v = partial[b * nf + f];
+        acc = ops[f] == 0 ? acc + v : (ops[f] == 1 ? fmin(acc, v) : fmax(acc, v));
+    }
+    out[f] = acc;
+}
+
+// ------------------------------------------------------------ bin sorting
+template <typename T>
+__global__ void k_prepare_points(const double* __restrict__ x, int64_t n, int d, double c0, double c1, double c2,
+                                 double scale, int n_os, int B, int nb0, int nb1, int nb2, int m,
+                                 T* __restrict__ u0, T* __restrict__ u1, T* __restrict__ u2,
+                                 int* __restrict__ bin, int* __restrict__ count, int* __restrict__ status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c[3] = {c0, c1, c2};
+    const int nb[3] = {nb0, nb1, nb2};
+    T* u[3] = {u0, u1, u2};
+    int lin = 0;
+    bool ok = true;
+    for (int t = 0; t < d; ++t) {
+        const double z = scale * (x[i * d + t] - c[t]) + 0.5;
+        const T ut = T(double(n_os) * z);
+        u[t][i] = ut;
+        const T fl = floor(ut);
+        int f = (fl > T(-1e9) && fl < T(1e9)) ? int(fl) : -1000000000;
+        ok = ok && (f - (m - 1) >= 0) && (f + m <= n_os - 1);
+        int bt = f / B;
+        bt = bt < 0 ? 0 : (bt >= nb[t] ? nb[t] - 1 : bt);
+        lin = lin * nb[t] + bt;
+    }
+    if (!ok) atomicOr(status, 2);
+    bin[i] = lin;
+    atomicAdd(&count[lin], 1);
+}
+
+// Exclusive scan of n ints into out[0..n] (out[n] = total).  One block of 1024 threads.
+__global__ void k_scan_exclusive(const int* __restrict__ in, int* __restrict__ out, int n) {
+    __shared__ int s[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? in[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int add = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+            __syncthreads();
+            s[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < n) out[i] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += s[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void k_scatter_perm(const int* __restrict__ bin, int64_t n, const int* __restrict__ start,
+                               int* __restrict__ cursor, int* __restrict__ perm) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = bin[i];
+    const int pos = start[b] + atomicAdd(&cursor[b], 1);
+    perm[pos] = int(i);
+}
+
+template <typename T>
+__global__ void k_gather_points(const int* __restrict__ perm, int64_t n, int d, const T* __restrict__ i0,
+                                const T* __restrict__ i1, const T* __restrict__ i2, T* __restrict__ o0,
+                                T* __restrict__ o1, T* __restrict__ o2) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = perm[i];
+    o0[i] = i0[p];
+    if (d > 1) o1[i] = i1[p];
+    if (d > 2) o2[i] = i2[p];
+}
+
+__global__ void k_count_subs(const int* __restrict__ bin_start, int nbins, int maxpts, int* __restrict__ nsub) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int cnt = bin_start[b + 1] - bin_start[b];
+    nsub[b] = (cnt + maxpts - 1) / maxpts;
+}
+
+__global__ void k_fill_subs(const int* __restrict__ bin_start, const int* __restrict__ sub_off, int nbins,
+                            int maxpts, int* __restrict__ sub_start, int* __restrict__ sub_count,
+                            int* __restrict__ sub_bin) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int s0 = bin_start[b], cnt = bin_start[b + 1] - s0;
+    const int o = sub_off[b], ns = sub_off[b + 1] - o;
+    for (int k = 0; k < ns; ++k) {
+        sub_start[o + k] = s0 + k * maxpts;
+        sub_count[o + k] = min(maxpts, cnt - k * maxpts);
+        sub_bin[o + k] = b;
+    }
+}
+
+// ------------------------------------------------------------ coefficient table
+// K_R(l/N) for l in {-N/2..N/2-1}^d, stored at index l + N/2 per dimension.
+__global__ void k_sample_kernel(double* __restrict__ out, int N, int d, KernelParams kp) {
+    int64_t total = 1;
+    for (int t = 0; t < d; ++t) total *= N;
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int64_t rem = idx;
+    double rho2 = 0.0;
+    for (int t = d - 1; t >= 0; --t) {
+        const int l = int(rem % N) - N / 2;
+        rem /= N;
+        const double y = double(l) / double(N);
+        rho2 += y * y;
+    }
+    const double rho = sqrt(rho2);
+    double v;
+    if (kp.nearfield && rho < kp.eps_I) {
+        const double s2 = rho2 / (kp.eps_I * kp.eps_I);
+        v = 0.0;
+        for (int q = kp.p - 1; q >= 0; --q) v = v * s2 + kp.ki[q];
+    } else if (rho <= kp.L) {
+        v = exp(-pow(rho, kp.r) / kp.eps_s);
+    } else {
+        const double tau = (fmin(rho, 0.5) - kp.L) / (0.5 - kp.L);
+        v = 0.0;
+        for (int i = 2 * kp.p - 2; i >= 0; --i) v = v * tau + kp.kb[i];
+    }
+    out[idx] = v;
+}
+
+// One cosine-DFT pass along `axis` of an N^d array indexed by l + N/2:
+// out[.. k ..] = sum_l in[.. l ..] cos(2 pi k l / N), k, l in -N/2..N/2-1.
+// (The samples are even in every coordinate, so the sine part vanishes.)
+__global__ void k_cos_dft_axis(const double* __restrict__ in, double* __restrict__ out, int N, int d, int axis,
+                               const double* __restrict__ costab) {
+    int64_t total = 1;
+    for (int t = 0; t < d; ++t) total *= N;
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int64_t stride = 1;
+    for (int t = d - 1; t > axis; --t) stride *= N;
+    const int ka = int((idx / stride) % N);
+    const int64_t base = idx - int64_t(ka) * stride;
+    const int k = ka - N / 2;
+    double acc = 0.0;
+    for (int la = 0; la < N; ++la) {
+        const int l = la - N / 2;
+        int j = (k * l) % N;
+        if (j < 0) j += N;
+        acc += in[base + int64_t(la) * stride] * costab[j];
+    }
+    out[idx] = acc;
+}
+
+__global__ void k_cos_table(double* __restrict__ c, int N) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) c[j] = cospi(2.0 * double(j) / double(N));
+}
+
+// psihat_n(k / n_os) for k = -h..h: the Fourier transform of the window
+// normalized to 1 at 0, pi m / sinh(beta m) * I_0(m sqrt(beta^2 - (2 pi k / n_os)^2)).
+// I_0 by its power series sum_j ((x/2)^(2j)) / (j!)^2.
+__global__ void k_window_transform(double* __restrict__ out, int h, int n_os, int m, double beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > 2 * h) return;
+    const int k = i - h;
+    const double w = 2.0 * M_PI * double(k) / double(n_os);
+    const double arg = double(m) * sqrt(beta * beta - w * w);
+    const double q = 0.25 * arg * arg;
+    double term = 1.0, sum = 1.0;
+    for (int j = 1; j < 400; ++j) {
+        term *= q / (double(j) * double(j));
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    out[i] = M_PI * double(m) / sinh(beta * double(m)) * sum;
+}
+
+// M over the kept half spectrum: c_k b_k / prod_t psihat(k_t)^2, last axis k = 0..h,
+// with c_k the weight of the real part of the sum over I_N (re_weight).
+template <typename T>
+__global__ void k_build_mult(T* __restrict__ M, int d, int h, const double* __restrict__ bk, double inv_norm,
+                             const double* __restrict__ psihat) {
+    const int K = 2 * h + 1, N = 2 * h;
+    int64_t total = h + 1;
+    for (int t = 0; t < d - 1; ++t) total *= K;
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int k[3] = {0, 0, 0};
+    int64_t rem = idx;
+    k[d - 1] = int(rem % (h + 1));
+    rem /= (h + 1);
+    for (int t = d - 2; t >= 0; --t) { k[t] = int(rem % K) - h; rem /= K; }
+    int64_t bi = 0;
+    double c = inv_norm;
+    for (int t = 0; t < d; ++t) {
+        const int kt = k[t] == h ? -h : k[t];      // b is N-periodic: b_{N/2} = b_{-N/2}
+        bi = bi * N + (kt + h);
+        const double ph = psihat[k[t] + h];
+        c /= ph * ph;
+    }
+    c *= re_weight(k, d, h);
+    M[idx] = T(c * bk[bi]);
+}
+
+template <typename C>
+__global__ void k_twiddles(C* __restrict__ tw, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n / 2) return;
+    double s, c;
+    sincospi(-2.0 * double(k) / double(n), &s, &c);
+    tw[k].x = decltype(tw[k].x)(c);
+    tw[k].y = decltype(tw[k].y)(s);
+}
+
+// ------------------------------------------------------------ vectors
+__global__ void k_fill(double* __restrict__ p, int64_t n, double v) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+__global__ void k_scale(double* __restrict__ p, int64_t n, double f) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) p[i] *= f;
+}
+
+// out[i] = in[perm[i]]: caller order -> sorted order
+__global__ void k_gather(const double* __restrict__ in, const int* __restrict__ perm, int64_t n,
+                         double* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[perm[i]];
+}
+
+// out[perm[i]] = in[i]: sorted order -> caller order
+__global__ void k_scatter(const double* __restrict__ in, const int* __restrict__ perm, int64_t n,
+                          double* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = in[i];
+}
+
+// ------------------------------------------------------------ host launchers
+template <typename T>
+void launch_prepare_points(const double* x, int64_t n, int d, const double c[3], double scale, int n_os, int B,
+                           const int nb[3], int m, T* const u[3], int* bin, int* count, int* status,
+                           cudaStream_t s) {
+    k_prepare_points<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, n, d, c[0], c[1], c[2], scale, n_os, B, nb[0],
+                                                                  nb[1], nb[2], m, u[0], u[1], u[2], bin, count,
+                                                                  status);
+}
+
+template <typename T>
+void launch_gather_points(const int* perm, int64_t n, int d, T* const in[3], T* const out[3], cudaStream_t s) {
+    k_gather_points<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(perm, n, d, in[0], in[1], in[2], out[0], out[1],
+                                                                 out[2]);
+}
+
+template <typename T>
+void launch_build_mult(T* M, int d, int h, const double* bk, double inv_norm, const double* psihat,
+                       int64_t total, cudaStream_t s) {
+    k_build_mult<T><<<unsigned((total + 255) / 256), 256, 0, s>>>(M, d, h, bk, inv_norm, psihat);
+}
+
+template <typename T>
+void launch_twiddles(void* tw, int n, cudaStream_t s) {
+    using C = typename Cplx<T>::type;
+    k_twiddles<C><<<unsigned((n / 2 + 255) / 256), 256, 0, s>>>(static_cast<C*>(tw), n);
+}
+
+template void launch_prepare_points<float>(const double*, int64_t, int, const double[3], double, int, int,
+                                           const int[3], int, float* const[3], int*, int*, int*, cudaStream_t);
+template void launch_prepare_points<double>(const double*, int64_t, int, const double[3], double, int, int,
+                                            const int[3], int, double* const[3], int*, int*, int*, cudaStream_t);
+template void launch_gather_points<float>(const int*, int64_t, int, float* const[3], float* const[3], cudaStream_t);
+template void launch_gather_points<double>(const int*, int64_t, int, double* const[3], double* const[3],
+                                           cudaStream_t);
+template void launch_build_mult<float>(float*, int, int, const double*, double, const double*, int64_t,
+                                       cudaStream_t);
+template void launch_build_mult<double>(double*, int, int, const double*, double, const double*, int64_t,
+                                        cudaStream_t);
+template void launch_twiddles<float>(void*, int, cudaStream_t);
+template void launch_twiddles<double>(void*, int, cudaStream_t);
+
+}  // namespace sk

@@ -1,0 +1,44 @@
+// Declarations of the plan-time and bookkeeping kernels (sk_plan_kernels.cu).
+#pragma once
+
+#include "sk_internal.cuh"
+
+namespace sk {
+
+int bin_side(int d);
+
+__global__ void k_point_bounds(const double* x, int64_t n, int d, double* partial);
+__global__ void k_point_radius(const double* x, int64_t n, int d, double c0, double c1, double c2, double* partial);
+__global__ void k_weight_stats(const double* w, int64_t n, double* partial);
+__global__ void k_sum_marg_log(const double* marg, const double* scal, int64_t n, double* partial);
+__global__ void k_combine(const double* partial, int nblocks, int nf, int op0, int op1, int op2, int op3, int op4,
+                          int op5, int op6, double* out);
+
+template <typename T>
+void launch_prepare_points(const double* x, int64_t n, int d, const double c[3], double scale, int n_os, int B,
+                           const int nb[3], int m, T* const u[3], int* bin, int* count, int* status,
+                           cudaStream_t s);
+__global__ void k_scan_exclusive(const int* in, int* out, int n);
+__global__ void k_scatter_perm(const int* bin, int64_t n, const int* start, int* cursor, int* perm);
+template <typename T>
+void launch_gather_points(const int* perm, int64_t n, int d, T* const in[3], T* const out[3], cudaStream_t s);
+__global__ void k_count_subs(const int* bin_start, int nbins, int maxpts, int* nsub);
+__global__ void k_fill_subs(const int* bin_start, const int* sub_off, int nbins, int maxpts, int* sub_start,
+                            int* sub_count, int* sub_bin);
+
+__global__ void k_sample_kernel(double* out, int N, int d, KernelParams kp);
+__global__ void k_cos_dft_axis(const double* in, double* out, int N, int d, int axis, const double* costab);
+__global__ void k_cos_table(double* c, int N);
+__global__ void k_window_transform(double* out, int h, int n_os, int m, double beta);
+template <typename T>
+void launch_build_mult(T* M, int d, int h, const double* bk, double inv_norm, const double* psihat, int64_t total,
+                       cudaStream_t s);
+template <typename T>
+void launch_twiddles(void* tw, int n, cudaStream_t s);
+
+__global__ void k_fill(double* p, int64_t n, double v);
+__global__ void k_scale(double* p, int64_t n, double f);
+__global__ void k_gather(const double* in, const int* perm, int64_t n, double* out);
+__global__ void k_scatter(const double* in, const int* perm, int64_t n, double* out);
+
+}  // namespace sk

@@ -1,0 +1,349 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated in the tests below):
+  * fast summation E_fs = max_i |t_i - t_i^exact| / max_i |t_i^exact|:
+    <= 1e-6 for the FP64 path, <= 1e-5 for the FP32 path;
+  * Sinkhorn value s: relative error <= 1e-5;
+  * stage entry points (adjoint NFFT, NFFT): max error <= 1e-6 (FP64) /
+    1e-5 (FP32) relative to the l1 norm of their input, the scale of the
+    Kaiser-Bessel window error with m = 4, sigma = 2;
+  * Fourier coefficients b_k: both sides sample K_R in FP64 and take its DFT;
+    the boundary polynomial's coefficients come from two independent FP64
+    linear solves whose rounding differs, so agreement to 1e-10 of max |b_k|;
+  * direct summation: FP64 1e-12 per element; FP32 1e-5 per element (FP32
+    coordinates carry ~6e-8 relative rounding, amplified by |d K / d x|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import fastsum as ofs          # noqa: E402
+from oracle import sinkhorn as osk         # noqa: E402
+from paper_2201_07524_gb300 import workloads as wl   # noqa: E402
+
+sk = pytest.importorskip("paper_2201_07524_gb300.sk")
+
+DEV = "cuda"
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def plan_for(x, y, a=None, b=None, eps=0.05, r=2.0, precision=sk.SK_FP64, user_geometry=True, **kw):
+    n, m = len(x), len(y)
+    a = wl.uniform_weights(n) if a is None else a
+    b = wl.uniform_weights(m) if b is None else b
+    prm = sk.sk_default_params(precision=precision, **kw)
+    if user_geometry:
+        prm.user_geometry = 1
+        prm.scale = 1.0
+        for t in range(3):
+            prm.center[t] = 0.0
+    return sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), eps, r, prm)
+
+
+def efs(t, exact):
+    return float(np.max(np.abs(t - exact)) / np.max(np.abs(exact)))
+
+
+TOL_FS = {sk.SK_FP64: 1e-6, sk.SK_FP32: 1e-5}
+
+
+# --------------------------------------------------------- coefficients
+@pytest.mark.parametrize("d,N,eps", [(1, 64, 0.05), (2, 64, 0.05), (3, 32, 0.02), (2, 128, 0.01)])
+def test_fourier_coefficients_match_oracle(d, N, eps):
+    x = wl.uniform_ball(50, d, 0.2, 1)
+    y = wl.uniform_ball(60, d, 0.2, 2)
+    plan = plan_for(x, y, eps=eps, N=N)
+    got = np.zeros((N,) * d)
+    sk.sk_fourier_coefficients(plan, got)
+    want = ofs.fourier_coefficients(N, d, eps, 2.0, 0.4, 8)
+    assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
+
+
+def test_fourier_coefficients_follow_auto_scaling():
+    # automatic geometry: the kernel in torus coordinates is exp(-rho^r / (eps scale^r))
+    d, N, eps = 2, 64, 0.05
+    x = wl.uniform_ball(300, d, 0.2, 3) + 0.7
+    y = wl.uniform_ball(200, d, 0.2, 4) + 0.7
+    plan = plan_for(x, y, eps=eps, N=N, user_geometry=False)
+    info = sk.sk_plan_info(plan)
+    got = np.zeros((N,) * d)
+    sk.sk_fourier_coefficients(plan, got)
+    want = ofs.fourier_coefficients(N, d, eps * info["scale"] ** 2, 2.0, 0.4, 8)
+    assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
+    assert info["eps_scaled"] == pytest.approx(eps * info["scale"] ** 2, rel=1e-15)
+
+
+# --------------------------------------------------------- NFFT stages
+def _common(arr, h, d):
+    return arr[tuple([slice(0, 2 * h)] * d)]
+
+
+@pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
+@pytest.mark.parametrize("d,N", [(1, 32), (2, 32), (3, 16)])
+def test_adjoint_nfft_matches_adjoint_ndft(d, N, precision):
+    h = N // 2
+    x = wl.uniform_ball(333, d, 0.2, 5)
+    y = wl.uniform_ball(211, d, 0.2, 6)
+    plan = plan_for(x, y, N=N, precision=precision)
+    w = np.random.default_rng(7).standard_normal(333)
+    out = np.zeros(((2 * h + 1),) * d + (2,))
+    sk.sk_adjoint_nfft(plan, sk.SK_SET_X, w, out.reshape(-1))
+    got = out[..., 0] + 1j * out[..., 1]
+    want = ofs.adjoint_ndft(x + 0.5, w, N)
+    err = np.max(np.abs(_common(got, h, d) - want)) / np.sum(np.abs(w))
+    assert err <= TOL_FS[precision]
+    # Hermitian symmetry of the real-data spectrum, including the +N/2 planes
+    flip = got[tuple([slice(None, None, -1)] * d)]
+    assert np.max(np.abs(got - np.conj(flip))) <= 1e-12 * np.max(np.abs(got)) + 1e-300
+
+
+@pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
+@pytest.mark.parametrize("d,N", [(1, 32), (2, 32), (3, 16)])
+def test_nfft_matches_ndft(d, N, precision):
+    h = N // 2
+    x = wl.uniform_ball(129, d, 0.2, 8)
+    y = wl.uniform_ball(301, d, 0.2, 9)
+    plan = plan_for(x, y, N=N, precision=precision)
+    rng = np.random.default_rng(10)
+    A = rng.standard_normal((2 * h + 1,) * d) + 1j * rng.standard_normal((2 * h + 1,) * d)
+    F = 0.5 * (A + np.conj(A[tuple([slice(None, None, -1)] * d)]))       # Hermitian: F[-k] = conj F[k]
+    buf = np.stack([F.real, F.imag], axis=-1).reshape(-1).copy()
+    got = np.zeros(301)
+    sk.sk_nfft(plan, sk.SK_SET_Y, buf, got)
+    # the stage computes the real part of the sum over I_N
+    want = ofs.ndft(y + 0.5, _common(F, h, d), N).real
+    assert np.max(np.abs(got - want)) / np.sum(np.abs(F)) <= TOL_FS[precision]
+
+
+# --------------------------------------------------------- kernel products
+@pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
+@pytest.mark.parametrize("d,n,m,N,eps", [(1, 1000, 777, 64, 0.05), (2, 2000, 1337, 64, 0.05),
+                                         (3, 1500, 1999, 64, 0.02), (2, 1024, 1000, 128, 0.01)])
+def test_kernel_apply_matches_exact_sums(d, n, m, N, eps, precision):
+    x = wl.uniform_ball(n, d, 0.2, 11)
+    y = wl.uniform_ball(m, d, 0.2, 12)
+    plan = plan_for(x, y, eps=eps, N=N, precision=precision, user_geometry=False)
+    v = wl.positive_vector(m, 13)
+    u = wl.positive_vector(n, 14)
+    t = torch.zeros(n, dtype=torch.float64, device=DEV)
+    tt = torch.zeros(m, dtype=torch.float64, device=DEV)
+    sk.sk_kernel_apply(plan, 0, cuda(v), t)
+    sk.sk_kernel_apply(plan, 1, cuda(u), tt)
+    torch.cuda.synchronize()
+    assert efs(t.cpu().numpy(), osk.kernel_apply(x, y, v, eps, 2.0)) <= TOL_FS[precision]
+    assert efs(tt.cpu().numpy(), osk.kernel_apply_T(x, y, u, eps, 2.0)) <= TOL_FS[precision]
+
+
+def test_kernel_apply_host_buffers_and_ragged_tiny_sizes():
+    # host (numpy) in/out buffers; sizes below one block and not multiples of anything
+    for n, m in [(1, 1), (1, 5), (7, 1), (33, 65)]:
+        x = wl.uniform_ball(n, 2, 0.2, 15 + n)
+        y = wl.uniform_ball(m, 2, 0.2, 16 + m)
+        plan = plan_for(x, y)
+        v = wl.positive_vector(m, 17)
+        t = np.zeros(n)
+        sk.sk_kernel_apply(plan, 0, v, t)
+        assert efs(t, osk.kernel_apply(x, y, v, 0.05, 2.0)) <= 1e-6
+
+
+def test_identical_points_and_degenerate_geometry():
+    # all points at one location: bounding radius 0, scale falls back to 1
+    x = np.full((10, 3), 0.123)
+    y = np.full((4, 3), 0.123)
+    plan = plan_for(x, y, user_geometry=False, eps=0.02)
+    t = np.zeros(10)
+    sk.sk_kernel_apply(plan, 0, np.ones(4), t)
+    np.testing.assert_allclose(t, 4.0, rtol=1e-6)
+
+
+@pytest.mark.parametrize("precision,tol", [(sk.SK_FP64, 1e-12), (sk.SK_FP32, 1e-5)])
+@pytest.mark.parametrize("r", [2.0, 1.0, 1.5])
+def test_direct_method_matches_exact_sums(precision, tol, r):
+    d, n, m, eps = 3, 700, 901, 0.02
+    x = wl.uniform_ball(n, d, 0.2, 18)
+    y = wl.uniform_ball(m, d, 0.2, 19)
+    plan = plan_for(x, y, eps=eps, r=r, precision=precision, user_geometry=False)
+    sk.sk_set_method(plan, sk.SK_METHOD_DIRECT)
+    v = wl.positive_vector(m, 20)
+    t = np.zeros(n)
+    sk.sk_kernel_apply(plan, 0, v, t)
+    exact = osk.kernel_apply(x, y, v, eps, r)
+    assert np.max(np.abs(t - exact) / exact) <= tol
+
+
+# --------------------------------------------------------- Sinkhorn
+def test_solve_matches_dense_oracle_small_2d_fp64():
+    w = wl.SMALL_2D
+    x, y = w.points()
+    a, b = w.marginals()
+    ref = osk.sinkhorn_dense(x, a, y, b, w.eps, w.r, w.iters)
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), w.eps, w.r,
+                      sk.sk_default_params(N=w.N, m_w=w.m_w, precision=sk.SK_FP64))
+    u = torch.zeros(w.n, dtype=torch.float64, device=DEV)
+    v = torch.zeros(w.m, dtype=torch.float64, device=DEV)
+    st, res = sk.sk_solve(plan, w.iters, 0.0, 10, u, v)
+    assert st == sk.SK_OK and res["iters"] == w.iters and res["total_iters"] == w.iters
+    assert abs(res["s"] - ref["s"]) / abs(ref["s"]) <= 1e-5
+    ent = osk.entropy(a) + osk.entropy(b)
+    assert res["s_upper"] == pytest.approx(res["s"] + w.eps * ent, rel=1e-12)
+    # the scaling vectors follow the oracle's iterates
+    np.testing.assert_allclose(u.cpu().numpy(), ref["u"], rtol=1e-4)
+    np.testing.assert_allclose(v.cpu().numpy(), ref["v"], rtol=1e-4)
+    assert res["err_row"] == pytest.approx(ref["err_row"], abs=1e-6)
+    assert res["err_col"] < 1e-6
+
+
+@pytest.mark.parametrize("precision", [sk.SK_FP32, sk.SK_FP64])
+def test_solve_matches_dense_oracle_3d(precision):
+    d, n, m, eps, iters = 3, 2500, 2100, 0.02, 30
+    x = wl.uniform_ball(n, d, 0.2, 21)
+    y = wl.uniform_ball(m, d, 0.2, 22)
+    a, b = wl.dirichlet_weights(n, 23), wl.dirichlet_weights(m, 24)
+    ref = osk.sinkhorn_dense(x, a, y, b, eps, 2.0, iters)
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), eps, 2.0,
+                      sk.sk_default_params(N=64, m_w=4, precision=precision))
+    st, res = sk.sk_solve(plan, iters)
+    assert st == sk.SK_OK
+    assert abs(res["s"] - ref["s"]) / abs(ref["s"]) <= 1e-5
+
+
+def test_solve_direct_method_matches_oracle():
+    d, n, m, eps, iters = 2, 900, 1100, 0.05, 20
+    x = wl.uniform_ball(n, d, 0.2, 25)
+    y = wl.uniform_ball(m, d, 0.2, 26)
+    a, b = wl.uniform_weights(n), wl.uniform_weights(m)
+    ref = osk.sinkhorn_dense(x, a, y, b, eps, 2.0, iters)
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), eps, 2.0, sk.sk_default_params(precision=sk.SK_FP32))
+    sk.sk_set_method(plan, sk.SK_METHOD_DIRECT)
+    st, res = sk.sk_solve(plan, iters)
+    assert abs(res["s"] - ref["s"]) / abs(ref["s"]) <= 1e-5
+
+
+def test_state_checkpoint_and_resume_is_exact():
+    x = wl.uniform_ball(800, 2, 0.2, 27)
+    y = wl.uniform_ball(600, 2, 0.2, 28)
+    plan = plan_for(x, y, user_geometry=False)
+    st, r_full = sk.sk_solve(plan, 12)
+    u_full = np.zeros(800)
+    v_full = np.zeros(600)
+    assert sk.sk_get_state(plan, u_full, v_full) == 12
+    sk.sk_set_state(plan)                      # back to u = v = 1
+    sk.sk_solve(plan, 5, result=False)
+    u5 = np.zeros(800)
+    v5 = np.zeros(600)
+    assert sk.sk_get_state(plan, u5, v5) == 5
+    sk.sk_set_state(plan)
+    sk.sk_set_state(plan, u5, v5, 5)           # resume from the checkpoint
+    st, r_res = sk.sk_solve(plan, 7)
+    assert r_res["total_iters"] == 12
+    u_res = np.zeros(800)
+    sk.sk_get_state(plan, u_res, None)
+    np.testing.assert_allclose(u_res, u_full, rtol=1e-12)
+    assert r_res["s"] == pytest.approx(r_full["s"], rel=1e-12)
+
+
+def test_tolerance_stopping():
+    x = wl.uniform_ball(500, 2, 0.2, 29)
+    y = wl.uniform_ball(500, 2, 0.2, 30)
+    plan = plan_for(x, y, user_geometry=False)
+    st, res = sk.sk_solve(plan, 400, tol=1e-9, check_every=5)
+    assert st == sk.SK_OK
+    assert res["iters"] < 400 and res["iters"] % 5 == 0
+    assert res["err_row"] <= 1e-9
+    plan2 = plan_for(x, y, user_geometry=False)
+    st2, res2 = sk.sk_solve(plan2, 3, tol=1e-14, check_every=1, raise_on_error=False)
+    assert st2 == sk.SK_ERR_NOT_CONVERGED and res2["iters"] == 3
+
+
+def test_input_errors_are_reported():
+    x = wl.uniform_ball(20, 2, 0.2, 31)
+    y = wl.uniform_ball(20, 2, 0.2, 32)
+    with pytest.raises(sk.SkError) as e:
+        plan_for(x, y, a=np.full(20, 0.1))
+    assert e.value.status == sk.SK_ERR_WEIGHTS
+    bad = x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(sk.SkError) as e:
+        plan_for(bad, y)
+    assert e.value.status == sk.SK_ERR_DOMAIN
+    with pytest.raises(sk.SkError) as e:
+        plan_for(x + 0.4, y)                  # user geometry: points leave the torus box
+    assert e.value.status == sk.SK_ERR_DOMAIN
+    neg = wl.uniform_weights(20)
+    neg[0], neg[1] = -0.05, neg[1] + 0.1
+    with pytest.raises(sk.SkError) as e:
+        plan_for(x, y, a=neg)
+    assert e.value.status == sk.SK_ERR_WEIGHTS
+
+
+def test_grad_reports_unsupported():
+    x = wl.uniform_ball(20, 2, 0.2, 33)
+    plan = plan_for(x, x)
+    assert sk.sk_grad(plan) == sk.SK_ERR_UNSUPPORTED
+
+
+def test_launch_count_and_stage_timing():
+    x = wl.uniform_ball(3000, 3, 0.2, 34)
+    y = wl.uniform_ball(3000, 3, 0.2, 35)
+    plan = plan_for(x, y, user_geometry=False, precision=sk.SK_FP32)
+    c0 = sk.sk_launch_count(plan)
+    sk.sk_solve(plan, 4, result=False)
+    torch.cuda.synchronize()
+    per_iter = (sk.sk_launch_count(plan) - c0) / 4
+    assert per_iter == 2 * (1 + 5 + 1)        # spread, 5 FFT passes, interp per half-step (3-D)
+    sk.sk_stage_times(plan, 1)
+    sk.sk_solve(plan, 3, result=False)
+    times = sk.sk_stage_times(plan, 0)
+    assert times["spread"][1] == 6 and times["fft"][1] == 6 and times["interp"][1] == 6
+    assert all(times[k][0] > 0 for k in ("spread", "fft", "interp"))
+
+
+# --------------------------------------------------------- full-size workloads
+def _sampled_rows(x, y, v, eps, r, rows):
+    return osk.kernel_apply(x[rows], y, v, eps, r, chunk=4)
+
+
+@pytest.mark.parametrize("work", [wl.HEADLINE_3D, wl.GMM_2D], ids=lambda w: w.name)
+def test_full_size_kernel_apply_sampled_rows(work):
+    x, y = work.points()
+    a, b = work.marginals()
+    prm = sk.sk_default_params(N=work.N, m_w=work.m_w,
+                               precision=sk.SK_FP32 if work.precision == "fp32" else sk.SK_FP64)
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), work.eps, work.r, prm)
+    v = wl.positive_vector(work.m, 36)
+    t = torch.zeros(work.n, dtype=torch.float64, device=DEV)
+    sk.sk_kernel_apply(plan, 0, cuda(v), t)
+    rows = np.random.default_rng(37).choice(work.n, 64, replace=False)
+    rows = np.concatenate([rows, [0, work.n - 1]])
+    exact = _sampled_rows(x, y, v, work.eps, work.r, rows)
+    got = t.cpu().numpy()[rows]
+    # E_fs over the sample, normalized by the largest sum in the sample
+    assert np.max(np.abs(got - exact)) / np.max(np.abs(exact)) <= 1e-5
+
+
+def test_full_size_solve_marginal_property():
+    # after the even half-step the column marginal v * (K^T u) equals b; check it
+    # on sampled columns with exact FP64 sums over all 1e6 rows.
+    work = wl.HEADLINE_3D
+    x, y = work.points()
+    a, b = work.marginals()
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), work.eps, work.r,
+                      sk.sk_default_params(N=work.N, m_w=work.m_w))
+    u = np.zeros(work.n)
+    v = np.zeros(work.m)
+    st, res = sk.sk_solve(plan, 10, u_out=u, v_out=v)
+    assert st == sk.SK_OK and math.isfinite(res["s"])
+    cols = np.random.default_rng(38).choice(work.m, 16, replace=False)
+    marg = np.empty(len(cols))
+    for k, j in enumerate(cols):
+        d2 = np.sum((x - y[j]) ** 2, axis=1)
+        marg[k] = v[j] * np.dot(u, np.exp(-d2 / work.eps))
+    np.testing.assert_allclose(marg, b[cols], rtol=1e-4)
+    assert res["err_col"] < 1e-4 * np.linalg.norm(b)
