@@ -46,7 +46,8 @@ enum {
     SK_ERR_NOT_CONVERGED = 6, /* tol > 0 and max_iter reached with ||E|| > tol */
     SK_ERR_TIMEOUT = 7,       /* reserved for bounded device waits */
     SK_ERR_CUDA = 8,          /* a CUDA runtime call failed */
-    SK_ERR_UNSUPPORTED = 9    /* valid request this build does not implement */
+    SK_ERR_UNSUPPORTED = 9,   /* valid request this build does not implement */
+    SK_ERR_TOO_LARGE = 10     /* size beyond the fixed scratch of sk_direct_residual_noalloc */
 };
 
 enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / interpolation */
@@ -219,6 +220,35 @@ int sk_stage_times(sk_plan* plan, int enable, double* ms_out, int64_t* counts_ou
 
 /* Number of kernels this plan has launched (graph replays count every kernel node). */
 int64_t sk_launch_count(const sk_plan* plan);
+
+/* ---------------------------------------------- no-allocation entry point --
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory (code running under a framework whose memory pool
+ * already owns the GPU's memory, services that must not allocate after
+ * start-up because cudaMalloc can synchronize the device, callers that hand
+ * the library only buffers they own).  It needs no plan and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Computes, by direct FP32 kernel evaluation with FP64 accumulation across
+ * 1024-source tiles (the direct method of sk_set_method),
+ *   t_out[i]     = sum_j v_j exp(-||x_i - y_j||^r / eps)            (Eq. (matexp))
+ *   stats_out[0] = sum_i (u_i t_out[i] - a_i)^2   (squared row term of Eq. (Error))
+ *   stats_out[1] = sum_i u_i t_out[i]             (u^T K v)
+ * x: n-by-d, y: m-by-d row-major; u, a: n; v: m; t_out: n; stats_out: 2.
+ * Every pointer must be device (or managed) memory, else SK_ERR_ARG.  The call
+ * is asynchronous on `stream`.
+ *
+ * Scratch: the per-block partial sums live in one file-scope device array of
+ * 64 KB + 256 B, present on every GPU that loads the library until the process
+ * exits.  It bounds n <= 2,097,152 (4096 blocks of 512 targets); larger n
+ * returns SK_ERR_TOO_LARGE before any GPU work.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call on each device before any stream capture.  All calls share the
+ * array: calls whose kernels overlap on the GPU (concurrent streams or host
+ * threads on one device) race and return wrong sums, so serialize them. */
+int sk_direct_residual_noalloc(int d, int64_t n, const double* x, const double* u, const double* a,
+                               int64_t m, const double* y, const double* v, double eps, double r,
+                               double* t_out, double* stats_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 # status codes / enums (include/sk.h)
 SK_OK, SK_ERR_ARG, SK_ERR_DOMAIN, SK_ERR_WEIGHTS, SK_ERR_NOMEM = 0, 1, 2, 3, 4
 SK_ERR_UNDERFLOW, SK_ERR_NOT_CONVERGED, SK_ERR_TIMEOUT, SK_ERR_CUDA, SK_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
+SK_ERR_TOO_LARGE = 10
 SK_FP32, SK_FP64 = 0, 1
 SK_METHOD_NFFT, SK_METHOD_DIRECT = 0, 1
 SK_SET_X, SK_SET_Y = 0, 1
@@ -73,6 +74,8 @@ _SIGS = {
     "sk_stage_times": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64)]),
     "sk_launch_count": (ctypes.c_int64, [_P]),
+    "sk_direct_residual_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _D, _D, _D, ctypes.c_int64, _D, _D,
+                                                  ctypes.c_double, ctypes.c_double, _D, _D, _S]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -266,3 +269,15 @@ def sk_stage_times(plan, enable):
 
 def sk_launch_count(plan):
     return int(_lib.sk_launch_count(plan.handle))
+
+
+def sk_direct_residual_noalloc(x, u, a, y, v, eps, r, t_out, stats_out, stream=None):
+    """Direct-sum t = K v plus (sum (u t - a)^2, sum u t) into caller-owned device
+    buffers, with no device allocation (see include/sk.h)."""
+    n, d = x.shape
+    m = y.shape[0]
+    _check(_lib.sk_direct_residual_noalloc(int(d), int(n), _ptr(x, n * d, "x"), _ptr(u, n, "u"), _ptr(a, n, "a"),
+                                           int(m), _ptr(y, m * d, "y"), _ptr(v, m, "v"), float(eps), float(r),
+                                           _ptr(t_out, n, "t_out"), _ptr(stats_out, 2, "stats_out"),
+                                           _stream(stream)), "sk_direct_residual_noalloc")
+    return t_out, stats_out
