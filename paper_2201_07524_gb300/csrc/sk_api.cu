@@ -19,11 +19,13 @@ struct sk_plan {
     sk_nfft_params prm{};
     int precision = SK_FP32;
     int method = SK_METHOD_NFFT;
-    int N = 0, h = 0, n_os = 0, log2n = 0, W = 0, B = 0, nb[3] = {1, 1, 1}, nbins = 0;
+    int N = 0, h = 0, n_os = 0, log2n = 0, W = 0, B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 0, bvol = 1;
+    int64_t nkeys = 0;
     double beta = 0, knorm = 0;
     double center[3] = {0, 0, 0}, scale = 1, eps_s = 0;
     int nearfield = 0;
     KernelParams kp{};
+    WindowPoly wp{};
     Cloud X, Y;
     FftPlan fft;
     size_t grid_elems = 0;
@@ -251,6 +253,57 @@ bool nearfield_coefficients(KernelParams& kp) {
 
 bool even_integer(double r) { return std::floor(r) == r && (int64_t(r) % 2 == 0); }
 
+// Kaiser-Bessel window in grid units, normalized to 1 at 0 (host, FP64).
+double kb_host(double x, int m, double beta, double knorm) {
+    const double z2 = double(m) * m - x * x;
+    if (z2 < 0.0) return 0.0;
+    if (z2 == 0.0) return beta * knorm;
+    const double z = std::sqrt(z2);
+    return std::sinh(beta * z) / z * knorm;
+}
+
+// Chebyshev interpolant of degree `deg` of f on [-1, 1], in monomials of s.
+template <typename F>
+void chebyshev_monomials(F f, int deg, double* c) {
+    const int np = deg + 1;
+    double vals[32], a[32];
+    for (int i = 0; i < np; ++i) vals[i] = f(std::cos(M_PI * (i + 0.5) / np));
+    for (int j = 0; j < np; ++j) {
+        double acc = 0.0;
+        for (int i = 0; i < np; ++i) acc += vals[i] * std::cos(M_PI * j * (i + 0.5) / np);
+        a[j] = (j == 0 ? 1.0 : 2.0) * acc / np;
+    }
+    // T_j in monomials: T_0 = 1, T_1 = s, T_{j+1} = 2 s T_j - T_{j-1}
+    double tm1[32] = {0}, t0[32] = {0}, t1[32] = {0};
+    for (int i = 0; i <= deg; ++i) c[i] = 0.0;
+    t0[0] = 1.0;
+    for (int i = 0; i <= deg; ++i) c[i] += a[0] * t0[i];
+    if (deg >= 1) {
+        t1[1] = 1.0;
+        for (int i = 0; i <= deg; ++i) c[i] += a[1] * t1[i];
+    }
+    for (int j = 2; j <= deg; ++j) {
+        double tn[32] = {0};
+        for (int i = 0; i <= deg; ++i) tn[i] = (i > 0 ? 2.0 * t1[i - 1] : 0.0) - t0[i];
+        for (int i = 0; i <= deg; ++i) c[i] += a[j] * tn[i];
+        for (int i = 0; i <= deg; ++i) { tm1[i] = t0[i]; t0[i] = t1[i]; t1[i] = tn[i]; }
+    }
+}
+
+// Piecewise-polynomial window: tap k of a point with fractional offset frac is
+// psi(frac + m - 1 - k), approximated in s = 2 frac - 1 (see WindowPoly).
+void window_polynomials(int m, double beta, double knorm, WindowPoly& wp) {
+    std::memset(&wp, 0, sizeof(wp));
+    for (int k = 0; k < 2 * m; ++k) {
+        auto f = [&](double s) { return kb_host(0.5 * (s + 1.0) + m - 1 - k, m, beta, knorm); };
+        double c[32];
+        chebyshev_monomials(f, kPolyDeg32, c);
+        for (int i = 0; i <= kPolyDeg32; ++i) wp.c32[k][i] = float(c[i]);
+        chebyshev_monomials(f, kPolyDeg64, c);
+        for (int i = 0; i <= kPolyDeg64; ++i) wp.c64[k][i] = c[i];
+    }
+}
+
 // ------------------------------------------------------------ reductions
 // Reduce a partial table of `nf` fields with the given ops to host doubles.
 void combine_to_host(sk_plan* P, int nblocks, int nf, const int* ops, double* host) {
@@ -267,6 +320,23 @@ void combine_to_host(sk_plan* P, int nblocks, int nf, const int* ops, double* ho
 constexpr int kRedBlocks = 256;
 
 // ------------------------------------------------------------ point clouds
+// Exclusive scan into out[0..n] through the multi-block scan, with its scratch
+// taken from the stream-ordered pool.
+void scan_ints(sk_plan* P, const int* in, int* out, int n) {
+    int* scratch = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&scratch), size_t(scan_scratch_ints(n)) * sizeof(int), P->ps));
+    launch_scan_exclusive(in, out, n, scratch, P->ps);
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(scratch, P->ps));
+}
+
+int read_int(sk_plan* P, const int* dev) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, dev, sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    return v;
+}
+
 template <typename T>
 void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, int64_t n) {
     c.n = n;
@@ -277,43 +347,44 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
     c.t = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
     c.work = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
     c.stage = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
+    c.key_start = static_cast<int*>(dalloc(P, size_t(P->nkeys + 1) * sizeof(int)));
     c.bin_start = static_cast<int*>(dalloc(P, size_t(P->nbins + 1) * sizeof(int)));
 
     // temporaries
     T* uo[3] = {nullptr, nullptr, nullptr};
     T* us[3] = {nullptr, nullptr, nullptr};
     void* tmp_u = nullptr;
-    int *bin = nullptr, *count = nullptr, *cursor = nullptr, *nsub = nullptr, *suboff = nullptr;
+    int *key = nullptr, *count = nullptr, *cursor = nullptr, *nsub = nullptr, *suboff = nullptr;
     CK(cudaMallocAsync(&tmp_u, size_t(n) * 3 * sizeof(T), P->ps));
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&bin), size_t(n) * sizeof(int), P->ps));
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&count), size_t(P->nbins) * sizeof(int), P->ps));
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&cursor), size_t(P->nbins) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&key), size_t(n) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&count), size_t(P->nkeys) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&cursor), size_t(P->nkeys) * sizeof(int), P->ps));
     CK(cudaMallocAsync(reinterpret_cast<void**>(&nsub), size_t(P->nbins) * sizeof(int), P->ps));
     CK(cudaMallocAsync(reinterpret_cast<void**>(&suboff), size_t(P->nbins + 1) * sizeof(int), P->ps));
     for (int t = 0; t < 3; ++t) {
         uo[t] = static_cast<T*>(tmp_u) + size_t(t) * n;
         us[t] = t < P->d ? static_cast<T*>(c.coord[t]) : uo[t];
     }
-    CK(cudaMemsetAsync(count, 0, size_t(P->nbins) * sizeof(int), P->ps));
-    CK(cudaMemsetAsync(cursor, 0, size_t(P->nbins) * sizeof(int), P->ps));
-    launch_prepare_points<T>(xdev, n, P->d, P->center, P->scale, P->n_os, P->B, P->nb, P->prm.m_w, uo, bin, count,
+    CK(cudaMemsetAsync(count, 0, size_t(P->nkeys) * sizeof(int), P->ps));
+    CK(cudaMemsetAsync(cursor, 0, size_t(P->nkeys) * sizeof(int), P->ps));
+    launch_prepare_points<T>(xdev, n, P->d, P->center, P->scale, P->n_os, P->B, P->nb, P->prm.m_w, uo, key, count,
                              P->status, P->ps);
     CK(cudaGetLastError());
-    k_scan_exclusive<<<1, 1024, 0, P->ps>>>(count, c.bin_start, P->nbins);
-    CK(cudaGetLastError());
-    k_scatter_perm<<<nblk(n), 256, 0, P->ps>>>(bin, n, c.bin_start, cursor, c.perm);
+    scan_ints(P, count, c.key_start, int(P->nkeys));
+    k_scatter_perm<<<nblk(n), 256, 0, P->ps>>>(key, n, c.key_start, cursor, c.perm);
     CK(cudaGetLastError());
     launch_gather_points<T>(c.perm, n, P->d, uo, us, P->ps);
     CK(cudaGetLastError());
     k_gather<<<nblk(n), 256, 0, P->ps>>>(wdev, c.perm, n, c.marg);
     CK(cudaGetLastError());
+    k_bin_starts<<<nblk(P->nbins + 1), 256, 0, P->ps>>>(c.key_start, P->nbins, P->bvol, c.bin_start);
+    CK(cudaGetLastError());
+
+    // subproblems of the per-point spreading kernel
     k_count_subs<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, P->nbins, kSpreadMaxPts, nsub);
     CK(cudaGetLastError());
-    k_scan_exclusive<<<1, 1024, 0, P->ps>>>(nsub, suboff, P->nbins);
-    CK(cudaGetLastError());
-    int total = 0;
-    CK(cudaMemcpyAsync(&total, suboff + P->nbins, sizeof(int), cudaMemcpyDeviceToHost, P->ps));
-    CK(cudaStreamSynchronize(P->ps));
+    scan_ints(P, nsub, suboff, P->nbins);
+    const int total = read_int(P, suboff + P->nbins);
     c.nsub = total;
     c.sub_start = static_cast<int*>(dalloc(P, size_t(std::max(total, 1)) * sizeof(int)));
     c.sub_count = static_cast<int*>(dalloc(P, size_t(std::max(total, 1)) * sizeof(int)));
@@ -321,10 +392,22 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
     k_fill_subs<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, suboff, P->nbins, kSpreadMaxPts, c.sub_start,
                                                   c.sub_count, c.sub_bin);
     CK(cudaGetLastError());
+
+    // column tasks of the 3-D column kernels
+    if (column_kernels(P->d, P->W)) {
+        const int ncol = P->B[0] * P->B[1];
+        k_count_tasks<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, P->nbins, kTaskMaxPts, ncol, nsub);
+        CK(cudaGetLastError());
+        scan_ints(P, nsub, suboff, P->nbins);
+        c.ntasks = read_int(P, suboff + P->nbins);
+        c.tasks = static_cast<int*>(dalloc(P, size_t(3 * std::max(c.ntasks, 1)) * sizeof(int)));
+        k_fill_tasks<<<nblk(P->nbins), 256, 0, P->ps>>>(suboff, P->nbins, ncol, c.tasks);
+        CK(cudaGetLastError());
+    }
     k_fill<<<nblk(n), 256, 0, P->ps>>>(c.scal, n, 1.0);
     CK(cudaGetLastError());
     CK(cudaFreeAsync(tmp_u, P->ps));
-    CK(cudaFreeAsync(bin, P->ps));
+    CK(cudaFreeAsync(key, P->ps));
     CK(cudaFreeAsync(count, P->ps));
     CK(cudaFreeAsync(cursor, P->ps));
     CK(cudaFreeAsync(nsub, P->ps));
@@ -406,7 +489,13 @@ template <typename T>
 void prepare_kernels(sk_plan* P) {
     SpreadArgs a{};
     a.nsub = 0;
+    a.ntasks = 0;
     CK(launch_spread<T>(P->d, P->W, a, P->ps));
+    if (column_kernels(P->d, P->W)) {
+        InterpArgs ia{};
+        ia.ntasks = 0;
+        CK(launch_interp3<T>(P->W, ia, Epilogue{}, P->ps));
+    }
     CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
 }
 
@@ -439,15 +528,18 @@ void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
     a.sub_count = src.sub_count;
     a.sub_bin = src.sub_bin;
     a.nsub = src.nsub;
+    a.key_start = src.key_start;
+    a.tasks = src.tasks;
+    a.ntasks = src.ntasks;
     a.n_os = P->n_os;
     for (int t = 0; t < 3; ++t) a.nb[t] = P->nb[t];
-    a.B = P->B;
     a.beta = P->beta;
     a.knorm = P->knorm;
     a.grid = P->fft.grid;
+    a.wp = P->wp;
     st = stage_begin(P, SK_STAGE_SPREAD);
     CK(launch_spread<T>(P->d, P->W, a, P->ps));
-    if (src.nsub > 0) ++P->launches;
+    if ((column_kernels(P->d, P->W) ? src.ntasks : src.nsub) > 0) ++P->launches;
     stage_end(P, st);
 }
 
@@ -456,10 +548,15 @@ void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
     InterpArgs a{};
     for (int t = 0; t < 3; ++t) a.coord[t] = dst.coord[t];
     a.n = dst.n;
+    a.key_start = dst.key_start;
+    a.tasks = dst.tasks;
+    a.ntasks = dst.ntasks;
+    for (int t = 0; t < 3; ++t) a.nb[t] = P->nb[t];
     a.n_os = P->n_os;
     a.beta = P->beta;
     a.knorm = P->knorm;
     a.grid = P->fft.grid;
+    a.wp = P->wp;
     int st = stage_begin(P, SK_STAGE_INTERP);
     CK(launch_interp<T>(P->d, P->W, a, e, &P->launches, P->ps));
     stage_end(P, st);
@@ -709,14 +806,18 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         P->n_os = n_os;
         P->log2n = log2n;
         P->W = 2 * p.m_w;
-        P->B = bin_side(d);
+        bin_shape(d, P->W, P->B);
         P->nbins = 1;
+        P->bvol = 1;
         for (int t = 0; t < 3; ++t) {
-            P->nb[t] = t < d ? (n_os + P->B - 1) / P->B : 1;
+            P->nb[t] = t < d ? (n_os + P->B[t] - 1) / P->B[t] : 1;
             P->nbins *= P->nb[t];
+            P->bvol *= t < d ? P->B[t] : 1;
         }
+        P->nkeys = int64_t(P->nbins) * P->bvol;
         P->beta = M_PI * (2.0 - 1.0 / p.sigma);
         P->knorm = double(p.m_w) / std::sinh(P->beta * p.m_w);
+        window_polynomials(p.m_w, P->beta, P->knorm, P->wp);
         P->nearfield = nearfield ? 1 : 0;
 
         CK(cudaStreamCreateWithFlags(&P->ps, cudaStreamNonBlocking));
@@ -824,6 +925,12 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
             build_grid<double>(P);
         }
         for (void* t : tmps) CK(cudaFreeAsync(t, P->ps));
+        // the column kernels reduce one partial per task
+        const int need = std::max(P->X.ntasks, P->Y.ntasks);
+        if (need > P->partial_blocks) {
+            P->partial_blocks = need;
+            P->partial = static_cast<double*>(dalloc(P, size_t(need) * 8 * sizeof(double)));
+        }
         // opt the kernels this plan uses into their shared-memory sizes now, so
         // no attribute call happens while an iteration is being captured
         if (P->precision == SK_FP32)

@@ -26,6 +26,7 @@ namespace sk {
 constexpr int kMaxP = 12;            // smoothness limit of the regularized kernel
 constexpr int kFftElems = 4096;      // complex elements per FFT block (P pencils x n)
 constexpr int kSpreadMaxPts = 1024;  // points per spreading subproblem
+constexpr int kTaskMaxPts = 4096;    // points per column task before a bin is split
 
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
@@ -52,7 +53,10 @@ struct Cloud {
     double* t = nullptr;        // sorted kernel sums of the last product into this cloud
     double* work = nullptr;     // sorted scratch (gathered weights)
     double* stage = nullptr;    // caller-order scratch for host<->device staging
+    int* key_start = nullptr;   // CSR over sort keys (bin, cell in bin), nkeys + 1
     int* bin_start = nullptr;   // CSR over bins, nbins + 1
+    int* tasks = nullptr;       // column tasks (3-D)
+    int ntasks = 0;
     int* sub_start = nullptr;   // spreading subproblems
     int* sub_count = nullptr;
     int* sub_bin = nullptr;
@@ -76,27 +80,49 @@ struct Epilogue {
     int* status = nullptr;       // bit 0 set when some t_i <= 0 or not finite (UPDATE)
 };
 
+// Piecewise-polynomial form of the Kaiser-Bessel window (the Horner scheme of
+// Barnett, Magland and af Klinteberg's FINUFFT): on each of its W = 2m unit
+// intervals the window, as a function of s = 2 frac - 1 in [-1, 1], is
+// replaced by its Chebyshev interpolant of degree 9 (FP32) or 14 (FP64),
+// written in monomials of s.  Tap k of a point with fractional offset frac is
+// psi(frac + m - 1 - k) ~ sum_i c[k][i] s^i.  The interpolation error is below
+// 4e-9 (degree 9) and 1e-14 (degree 14) of the window's peak for m >= 2.
+constexpr int kPolyDeg32 = 9;
+constexpr int kPolyDeg64 = 14;
+struct WindowPoly {
+    float c32[16][kPolyDeg32 + 1];
+    double c64[16][kPolyDeg64 + 1];
+};
+
 struct SpreadArgs {
     const void* coord[3];
     const double* w;       // sorted weights
-    const int* sub_start;
+    const int* sub_start;  // subproblems of the per-point kernel
     const int* sub_count;
     const int* sub_bin;
     int nsub;
+    const int* key_start;  // CSR over sort keys (bin, cell in bin)
+    const int* tasks;      // column tasks: (bin, first column, end column)
+    int ntasks;
     int n_os;
     int nb[3];             // bins per dimension
-    int B;                 // bin side in cells
     double beta;           // Kaiser-Bessel shape
     double knorm;          // m / sinh(beta m): normalizes the window to 1 at 0
     void* grid;            // T*, n_os^d, zeroed by the caller
+    WindowPoly wp;
 };
 
 struct InterpArgs {
     const void* coord[3];
     int64_t n;
+    const int* key_start;
+    const int* tasks;
+    int ntasks;
+    int nb[3];
     int n_os;
     double beta, knorm;
     const void* grid;
+    WindowPoly wp;
 };
 
 struct DirectArgs {
@@ -129,6 +155,10 @@ template <typename T> cudaError_t launch_spread(int d, int W, const SpreadArgs& 
 template <typename T> cudaError_t launch_interp(int d, int W, const InterpArgs& a, const Epilogue& e,
                                                 int64_t* launches, cudaStream_t s);
 template <typename T> int interp_blocks(int64_t n);
+template <typename T> cudaError_t launch_spread3(int W, const SpreadArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_interp3(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s);
+bool column_kernels(int d, int W);
+void bin_shape(int d, int W, int B[3]);
 template <typename T> cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches);
 template <typename T> cudaError_t launch_fft_adjoint(const FftPlan& f, double* fhat, cudaStream_t s,
                                                      int64_t* launches);
@@ -170,6 +200,21 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// a / t in FP64 for t > 0 in the FP32 normal range: an FP32 reciprocal seed
+// (relative error ~2^-23) refined by one Newton-Raphson step for 1/t, which
+// squares the error, then a Newton correction of the quotient itself,
+// q <- q + r (a - t q).  Five FP64 operations instead of a full IEEE division,
+// whose FP64 cost dominates on this GPU; outside that range it divides.
+__device__ __forceinline__ double div_newton(double a, double t) {
+    const float tf = float(t);
+    if (!(tf >= 1.17549435e-38f) || !(tf <= 3.0e38f)) return a / t;
+    double r = double(__frcp_rn(tf));
+    r = fma(r, fma(-t, r, 1.0), r);
+    double q = a * r;
+    q = fma(r, fma(-t, q, a), q);
+    return q;
+}
+
 // Per-point FP64 epilogue (Eq. (S1) update and Eq. (Error) residual terms).
 __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t,
                                           double& sq, double& bad, double& dot) {
@@ -177,14 +222,14 @@ __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t
         e.out[e.perm[i]] = t;
         return;
     }
-    double q = e.scal[i];
-    double a = e.marg[i];
-    double r = q * t - a;
-    sq += r * r;
-    dot += q * t;
+    const double q = e.scal[i];
+    const double a = e.marg[i];
+    const double r = fma(q, t, -a);
+    sq = fma(r, r, sq);
+    dot = fma(q, t, dot);
     e.t_store[i] = t;
     if (e.mode == EPI_UPDATE) {
-        double qn = a / t;
+        const double qn = div_newton(a, t);
         if (!(t > 0.0) || !isfinite(qn)) bad += 1.0;
         e.scal[i] = qn;
     }

@@ -122,17 +122,22 @@ __global__ void k_combine(const double* __restrict__ partial, int nblocks, int n
 }
 
 // ------------------------------------------------------------ bin sorting
+// Sort key of a point: its bin (bins of B[0] x .. x B[d-1] cells, last axis
+// fastest) times the cells per bin, plus its cell inside the bin (last axis
+// fastest).  Sorting by this key keeps every bin contiguous and, inside a bin,
+// every column of cells along the last axis contiguous.
 template <typename T>
 __global__ void k_prepare_points(const double* __restrict__ x, int64_t n, int d, double c0, double c1, double c2,
-                                 double scale, int n_os, int B, int nb0, int nb1, int nb2, int m,
+                                 double scale, int n_os, int B0, int B1, int B2, int nb0, int nb1, int nb2, int m,
                                  T* __restrict__ u0, T* __restrict__ u1, T* __restrict__ u2,
-                                 int* __restrict__ bin, int* __restrict__ count, int* __restrict__ status) {
+                                 int* __restrict__ key, int* __restrict__ count, int* __restrict__ status) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double c[3] = {c0, c1, c2};
     const int nb[3] = {nb0, nb1, nb2};
+    const int B[3] = {B0, B1, B2};
     T* u[3] = {u0, u1, u2};
-    int lin = 0;
+    int bin = 0, loc = 0, bvol = 1;
     bool ok = true;
     for (int t = 0; t < d; ++t) {
         const double z = scale * (x[i * d + t] - c[t]) + 0.5;
@@ -141,46 +146,96 @@ __global__ void k_prepare_points(const double* __restrict__ x, int64_t n, int d,
         const T fl = floor(ut);
         int f = (fl > T(-1e9) && fl < T(1e9)) ? int(fl) : -1000000000;
         ok = ok && (f - (m - 1) >= 0) && (f + m <= n_os - 1);
-        int bt = f / B;
-        bt = bt < 0 ? 0 : (bt >= nb[t] ? nb[t] - 1 : bt);
-        lin = lin * nb[t] + bt;
+        if (f < 0) f = 0;
+        if (f > n_os - 1) f = n_os - 1;
+        int bt = f / B[t];
+        bt = bt >= nb[t] ? nb[t] - 1 : bt;
+        bin = bin * nb[t] + bt;
+        loc = loc * B[t] + (f - bt * B[t]);
+        bvol *= B[t];
     }
     if (!ok) atomicOr(status, 2);
-    bin[i] = lin;
-    atomicAdd(&count[lin], 1);
+    const int k = bin * bvol + loc;
+    key[i] = k;
+    atomicAdd(&count[k], 1);
 }
 
-// Exclusive scan of n ints into out[0..n] (out[n] = total).  One block of 1024 threads.
-__global__ void k_scan_exclusive(const int* __restrict__ in, int* __restrict__ out, int n) {
-    __shared__ int s[1024];
+// Exclusive scan of n ints into out[0..n] (out[n] = total) in three passes:
+// per-block scans of kScanBlock elements, a scan of the block totals (one
+// block), and the addition of the block offsets.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 4;
+constexpr int kScanBlock = kScanThreads * kScanPerThread;
+
+__global__ void k_scan_local(const int* __restrict__ in, int* __restrict__ out, int n, int* __restrict__ totals) {
+    __shared__ int s[kScanThreads];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPerThread;
+    int v[kScanPerThread];
+    int sum = 0;
+    for (int k = 0; k < kScanPerThread; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        sum += v[k];
+    }
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        const int add = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int run = s[threadIdx.x] - sum;
+    for (int k = 0; k < kScanPerThread; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == kScanThreads - 1) totals[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_scan_totals(int* __restrict__ totals, int nblocks, int* __restrict__ grand) {
+    __shared__ int s[kScanThreads];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += 1024) {
-        const int i = base + threadIdx.x;
-        const int v = i < n ? in[i] : 0;
+    for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nblocks ? totals[i] : 0;
         s[threadIdx.x] = v;
         __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
+        for (int off = 1; off < kScanThreads; off <<= 1) {
             const int add = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
             __syncthreads();
             s[threadIdx.x] += add;
             __syncthreads();
         }
-        if (i < n) out[i] = carry + s[threadIdx.x] - v;
+        if (i < nblocks) totals[i] = carry + s[threadIdx.x] - v;
         __syncthreads();
-        if (threadIdx.x == 1023) carry += s[1023];
+        if (threadIdx.x == kScanThreads - 1) carry += s[threadIdx.x];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[n] = carry;
+    if (threadIdx.x == 0) *grand = carry;
 }
 
-__global__ void k_scatter_perm(const int* __restrict__ bin, int64_t n, const int* __restrict__ start,
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ totals) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += totals[i / kScanBlock];
+}
+
+void launch_scan_exclusive(const int* in, int* out, int n, int* scratch, cudaStream_t s) {
+    const int nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_local<<<nb, kScanThreads, 0, s>>>(in, out, n, scratch);
+    k_scan_totals<<<1, kScanThreads, 0, s>>>(scratch, nb, out + n);
+    k_scan_add<<<unsigned((n + 255) / 256), 256, 0, s>>>(out, n, scratch);
+}
+
+int scan_scratch_ints(int n) { return (n + kScanBlock - 1) / kScanBlock + 1; }
+
+__global__ void k_scatter_perm(const int* __restrict__ key, int64_t n, const int* __restrict__ start,
                                int* __restrict__ cursor, int* __restrict__ perm) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int b = bin[i];
-    const int pos = start[b] + atomicAdd(&cursor[b], 1);
+    const int k = key[i];
+    const int pos = start[k] + atomicAdd(&cursor[k], 1);
     perm[pos] = int(i);
 }
 
@@ -194,6 +249,12 @@ __global__ void k_gather_points(const int* __restrict__ perm, int64_t n, int d, 
     o0[i] = i0[p];
     if (d > 1) o1[i] = i1[p];
     if (d > 2) o2[i] = i2[p];
+}
+
+// bin_start[b] = key_start[b * bvol], b = 0..nbins
+__global__ void k_bin_starts(const int* __restrict__ key_start, int nbins, int bvol, int* __restrict__ bin_start) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b <= nbins) bin_start[b] = key_start[int64_t(b) * bvol];
 }
 
 __global__ void k_count_subs(const int* __restrict__ bin_start, int nbins, int maxpts, int* __restrict__ nsub) {
@@ -214,6 +275,28 @@ __global__ void k_fill_subs(const int* __restrict__ bin_start, const int* __rest
         sub_start[o + k] = s0 + k * maxpts;
         sub_count[o + k] = min(maxpts, cnt - k * maxpts);
         sub_bin[o + k] = b;
+    }
+}
+
+// Column tasks of the 3-D column kernels: a non-empty bin with up to maxpts
+// points is one task over all its ncol columns; a heavier bin is split into
+// up to ncol tasks over equal ranges of its columns.
+__global__ void k_count_tasks(const int* __restrict__ bin_start, int nbins, int maxpts, int ncol,
+                              int* __restrict__ ntask) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int cnt = bin_start[b + 1] - bin_start[b];
+    ntask[b] = cnt == 0 ? 0 : min(ncol, (cnt + maxpts - 1) / maxpts);
+}
+
+__global__ void k_fill_tasks(const int* __restrict__ ntask_off, int nbins, int ncol, int* __restrict__ task) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int o = ntask_off[b], nt = ntask_off[b + 1] - o;
+    for (int k = 0; k < nt; ++k) {
+        task[3 * (o + k) + 0] = b;
+        task[3 * (o + k) + 1] = (k * ncol) / nt;
+        task[3 * (o + k) + 2] = ((k + 1) * ncol) / nt;
     }
 }
 
@@ -360,12 +443,12 @@ __global__ void k_scatter(const double* __restrict__ in, const int* __restrict__
 
 // ------------------------------------------------------------ host launchers
 template <typename T>
-void launch_prepare_points(const double* x, int64_t n, int d, const double c[3], double scale, int n_os, int B,
-                           const int nb[3], int m, T* const u[3], int* bin, int* count, int* status,
+void launch_prepare_points(const double* x, int64_t n, int d, const double c[3], double scale, int n_os,
+                           const int B[3], const int nb[3], int m, T* const u[3], int* key, int* count, int* status,
                            cudaStream_t s) {
-    k_prepare_points<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, n, d, c[0], c[1], c[2], scale, n_os, B, nb[0],
-                                                                  nb[1], nb[2], m, u[0], u[1], u[2], bin, count,
-                                                                  status);
+    k_prepare_points<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, n, d, c[0], c[1], c[2], scale, n_os, B[0], B[1],
+                                                                  B[2], nb[0], nb[1], nb[2], m, u[0], u[1], u[2], key,
+                                                                  count, status);
 }
 
 template <typename T>
@@ -386,9 +469,9 @@ void launch_twiddles(void* tw, int n, cudaStream_t s) {
     k_twiddles<C><<<unsigned((n / 2 + 255) / 256), 256, 0, s>>>(static_cast<C*>(tw), n);
 }
 
-template void launch_prepare_points<float>(const double*, int64_t, int, const double[3], double, int, int,
+template void launch_prepare_points<float>(const double*, int64_t, int, const double[3], double, int, const int[3],
                                            const int[3], int, float* const[3], int*, int*, int*, cudaStream_t);
-template void launch_prepare_points<double>(const double*, int64_t, int, const double[3], double, int, int,
+template void launch_prepare_points<double>(const double*, int64_t, int, const double[3], double, int, const int[3],
                                             const int[3], int, double* const[3], int*, int*, int*, cudaStream_t);
 template void launch_gather_points<float>(const int*, int64_t, int, float* const[3], float* const[3], cudaStream_t);
 template void launch_gather_points<double>(const int*, int64_t, int, double* const[3], double* const[3],

@@ -5,7 +5,7 @@
 
 namespace sk {
 
-int bin_side(int d);
+void bin_shape(int d, int W, int B[3]);
 
 __global__ void k_point_bounds(const double* x, int64_t n, int d, double* partial);
 __global__ void k_point_radius(const double* x, int64_t n, int d, double c0, double c1, double c2, double* partial);
@@ -15,13 +15,17 @@ __global__ void k_combine(const double* partial, int nblocks, int nf, int op0, i
                           int op5, int op6, double* out);
 
 template <typename T>
-void launch_prepare_points(const double* x, int64_t n, int d, const double c[3], double scale, int n_os, int B,
-                           const int nb[3], int m, T* const u[3], int* bin, int* count, int* status,
+void launch_prepare_points(const double* x, int64_t n, int d, const double c[3], double scale, int n_os,
+                           const int B[3], const int nb[3], int m, T* const u[3], int* key, int* count, int* status,
                            cudaStream_t s);
-__global__ void k_scan_exclusive(const int* in, int* out, int n);
-__global__ void k_scatter_perm(const int* bin, int64_t n, const int* start, int* cursor, int* perm);
+void launch_scan_exclusive(const int* in, int* out, int n, int* scratch, cudaStream_t s);
+int scan_scratch_ints(int n);
+__global__ void k_scatter_perm(const int* key, int64_t n, const int* start, int* cursor, int* perm);
 template <typename T>
 void launch_gather_points(const int* perm, int64_t n, int d, T* const in[3], T* const out[3], cudaStream_t s);
+__global__ void k_bin_starts(const int* key_start, int nbins, int bvol, int* bin_start);
+__global__ void k_count_tasks(const int* bin_start, int nbins, int maxpts, int ncol, int* ntask);
+__global__ void k_fill_tasks(const int* ntask_off, int nbins, int ncol, int* task);
 __global__ void k_count_subs(const int* bin_start, int nbins, int maxpts, int* nsub);
 __global__ void k_fill_subs(const int* bin_start, const int* sub_off, int nbins, int maxpts, int* sub_start,
                             int* sub_count, int* sub_bin);

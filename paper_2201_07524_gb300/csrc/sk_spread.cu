@@ -16,21 +16,26 @@
 
 namespace sk {
 
-template <int D> struct BinSide;
-template <> struct BinSide<1> { static constexpr int B = 512; };
-template <> struct BinSide<2> { static constexpr int B = 32; };
-template <> struct BinSide<3> { static constexpr int B = 8; };
+// Bin shapes in cells (last axis fastest).  In 3-D a bin is 4 x 4 x 8 so that
+// its 16 xy-columns of 8 cells feed the column kernels (sk_spread3.cu).
+template <int D> struct BinShape;
+template <> struct BinShape<1> { static constexpr int B0 = 512, B1 = 1, B2 = 1; };
+template <> struct BinShape<2> { static constexpr int B0 = 32, B1 = 32, B2 = 1; };
+template <> struct BinShape<3> { static constexpr int B0 = 4, B1 = 4, B2 = 8; };
 
-int bin_side(int d) { return d == 1 ? BinSide<1>::B : (d == 2 ? BinSide<2>::B : BinSide<3>::B); }
-
-template <int D, int W>
-constexpr int spread_side() { return BinSide<D>::B + W - 1; }
-
-template <int D, int W>
-constexpr int spread_cells() {
-    return D == 1 ? spread_side<D, W>() : (D == 2 ? spread_side<D, W>() * spread_side<D, W>()
-                                                  : spread_side<D, W>() * spread_side<D, W>() * spread_side<D, W>());
+void bin_shape(int d, int, int B[3]) {
+    if (d == 1) { B[0] = BinShape<1>::B0; B[1] = 1; B[2] = 1; }
+    else if (d == 2) { B[0] = BinShape<2>::B0; B[1] = BinShape<2>::B1; B[2] = 1; }
+    else { B[0] = BinShape<3>::B0; B[1] = BinShape<3>::B1; B[2] = BinShape<3>::B2; }
 }
+
+template <int D, int W>
+struct SubGrid {
+    static constexpr int S0 = BinShape<D>::B0 + W - 1;
+    static constexpr int S1 = D > 1 ? BinShape<D>::B1 + W - 1 : 1;
+    static constexpr int S2 = D > 2 ? BinShape<D>::B2 + W - 1 : 1;
+    static constexpr int CELLS = S0 * S1 * S2;
+};
 
 // Window weights of one coordinate for the W = 2m taps starting at cell f - (m-1).
 template <int W, typename T>
@@ -45,9 +50,10 @@ __device__ __forceinline__ void tap_weights(T u, T beta, T knorm, int& f, T (&w)
 
 template <int D, int W, typename T>
 __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
-    constexpr int B = BinSide<D>::B;
-    constexpr int S = spread_side<D, W>();
-    constexpr int NC = spread_cells<D, W>();
+    using SG = SubGrid<D, W>;
+    constexpr int NC = SG::CELLS;
+    const int B[3] = {BinShape<D>::B0, BinShape<D>::B1, BinShape<D>::B2};
+    const int S[3] = {SG::S0, SG::S1, SG::S2};
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sub = reinterpret_cast<T*>(smem_raw);
 
@@ -72,33 +78,33 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
         T w0[W], w1[W], w2[W];
         int f0 = 0, f1 = 0, f2 = 0;
         tap_weights<W, T>(c0[p], beta, knorm, f0, w0);
-        const int l0 = f0 - bc[0] * B;
+        const int l0 = f0 - bc[0] * B[0];
         if (D == 1) {
 #pragma unroll
             for (int i = 0; i < W; ++i) atomicAdd(&sub[l0 + i], val * w0[i]);
             continue;
         }
         tap_weights<W, T>(c1[p], beta, knorm, f1, w1);
-        const int l1 = f1 - bc[1] * B;
+        const int l1 = f1 - bc[1] * B[1];
         if (D == 2) {
 #pragma unroll
             for (int i = 0; i < W; ++i) {
                 const T v0 = val * w0[i];
-                T* row = sub + (l0 + i) * S + l1;
+                T* row = sub + (l0 + i) * SG::S1 + l1;
 #pragma unroll
                 for (int j = 0; j < W; ++j) atomicAdd(row + j, v0 * w1[j]);
             }
             continue;
         }
         tap_weights<W, T>(c2[p], beta, knorm, f2, w2);
-        const int l2 = f2 - bc[2] * B;
+        const int l2 = f2 - bc[2] * B[2];
 #pragma unroll 1
         for (int i = 0; i < W; ++i) {
             const T v0 = val * w0[i];
 #pragma unroll 2
             for (int j = 0; j < W; ++j) {
                 const T v1 = v0 * w1[j];
-                T* row = sub + ((l0 + i) * S + (l1 + j)) * S + l2;
+                T* row = sub + ((l0 + i) * SG::S1 + (l1 + j)) * SG::S2 + l2;
 #pragma unroll
                 for (int k = 0; k < W; ++k) atomicAdd(row + k, v1 * w2[k]);
             }
@@ -109,13 +115,13 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
     T* grid = static_cast<T*>(a.grid);
     const int n = a.n_os;
     int org[3];
-    for (int t = 0; t < D; ++t) org[t] = bc[t] * B - (W / 2 - 1);
+    for (int t = 0; t < D; ++t) org[t] = bc[t] * B[t] - (W / 2 - 1);
     for (int c = threadIdx.x; c < NC; c += blockDim.x) {
         const T v = sub[c];
         if (v == T(0)) continue;
         int loc[3] = {0, 0, 0};
         int rem = c;
-        for (int t = D - 1; t >= 0; --t) { loc[t] = rem % S; rem /= S; }
+        for (int t = D - 1; t >= 0; --t) { loc[t] = rem % S[t]; rem /= S[t]; }
         int64_t gi = 0;
         bool ok = true;
         for (int t = 0; t < D; ++t) {
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, Epilogue e) {
 
 template <int D, int W, typename T>
 static cudaError_t spread_one(const SpreadArgs& a, cudaStream_t s) {
-    constexpr size_t bytes = size_t(spread_cells<D, W>()) * sizeof(T);
+    constexpr size_t bytes = size_t(SubGrid<D, W>::CELLS) * sizeof(T);
     static unsigned long long configured = 0ull;   // one bit per device
     int dev = 0;
     cudaGetDevice(&dev);
@@ -213,6 +219,7 @@ static cudaError_t spread_w(int W, const SpreadArgs& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_spread(int d, int W, const SpreadArgs& a, cudaStream_t s) {
+    if (column_kernels(d, W)) return launch_spread3<T>(W, a, s);
     switch (d) {
         case 1: return spread_w<1, T>(W, a, s);
         case 2: return spread_w<2, T>(W, a, s);
@@ -249,6 +256,10 @@ static cudaError_t interp_w(int W, const InterpArgs& a, const Epilogue& e, int64
 template <typename T>
 cudaError_t launch_interp(int d, int W, const InterpArgs& a, const Epilogue& e, int64_t* launches,
                           cudaStream_t s) {
+    if (column_kernels(d, W)) {
+        if (launches && a.ntasks > 0) ++*launches;
+        return launch_interp3<T>(W, a, e, s);
+    }
     switch (d) {
         case 1: return interp_w<1, T>(W, a, e, launches, s);
         case 2: return interp_w<2, T>(W, a, e, launches, s);

@@ -1,0 +1,426 @@
+// 3-D spreading and interpolation by column tasks (adjoint NFFT / NFFT steps
+// of Eq. (fastsum) for d = 3).
+//
+// Points are sorted by bin (4 x 4 x 8 cells) and, inside a bin, by cell with
+// the z axis fastest, so each xy-column of a bin (8 cells along z) is a
+// contiguous range of points.  Every point of a column touches the same W x W
+// rows of grid cells (W = 2m taps per dimension) over the z-cells of its own
+// window, so a warp keeps the column's whole window -- W^2 rows by (8 + W - 1)
+// z-cells -- in registers, two rows per lane for W = 8:
+//
+//   * one lane per point evaluates that point's 3W window weights and writes
+//     them to a per-warp table in shared memory;
+//   * for each point, every lane forms wx[i] wy[j] for its rows and adds
+//     (or, when interpolating, gathers) the W z-taps with plain FMAs; the
+//     points of a batch are sorted by their z-offset inside the column, so the
+//     batch is walked in segments of equal offset (found with a warp ballot)
+//     and the register indices are compile-time constants in each segment;
+//   * spreading flushes a finished column into the bin's shared-memory
+//     sub-grid with shared-memory atomics (one per register, not one per tap),
+//     and the block adds the sub-grid to the global grid once;
+//   * interpolation loads the column's window from the grid once, reduces each
+//     point's 32 lane partials through shared memory, and runs the FP64
+//     epilogue with one lane per point.
+#include <utility>
+
+#include "sk_internal.cuh"
+
+namespace sk {
+
+template <int W> struct Col3 {
+    static constexpr int BX = 4, BY = 4, BZ = 8;
+    static constexpr int NCOL = BX * BY;
+    static constexpr int SX = BX + W - 1, SY = BY + W - 1, SZ = BZ + W - 1;
+    static constexpr int E = SZ;                       // z-cells of a column window
+    static constexpr int ROWS = W * W;
+    static constexpr int Q = (ROWS + 31) / 32;         // rows per lane
+    static constexpr int WZP = (W + 3) / 4 * 4;        // wz padded to whole 16-byte vectors
+    static constexpr int WZ = 0, WX = WZP, WY = WZP + W;
+    static constexpr int STRIDE = (WZP + 2 * W + 3) / 4 * 4;   // table entries per point
+    static constexpr int SUB = SX * SY * SZ;
+};
+
+constexpr int kWarps = 8;
+
+template <typename T> struct PolyDeg;
+template <> struct PolyDeg<float> { static constexpr int D = kPolyDeg32; };
+template <> struct PolyDeg<double> { static constexpr int D = kPolyDeg64; };
+
+template <typename T>
+__device__ __forceinline__ T poly_coef(const WindowPoly& wp, int k, int i);
+template <> __device__ __forceinline__ float poly_coef<float>(const WindowPoly& wp, int k, int i) {
+    return wp.c32[k][i];
+}
+template <> __device__ __forceinline__ double poly_coef<double>(const WindowPoly& wp, int k, int i) {
+    return wp.c64[k][i];
+}
+
+// The W window weights of one coordinate (taps starting at cell f - (m-1)),
+// by Horner's rule on the piecewise polynomial; `scale` multiplies them.
+template <int W, typename T>
+__device__ __forceinline__ void window_poly(T u, const WindowPoly& wp, T scale, int& f, T* w) {
+    constexpr int DEG = PolyDeg<T>::D;
+    const T fl = floor(u);
+    f = int(fl);
+    const T s = T(2) * (u - fl) - T(1);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        T acc = poly_coef<T>(wp, k, DEG);
+#pragma unroll
+        for (int i = DEG - 1; i >= 0; --i) acc = fma(acc, s, poly_coef<T>(wp, k, i));
+        w[k] = acc * scale;
+    }
+}
+
+// Weights of point p into the warp's table row; returns the z-offset of its
+// cell inside the column.
+template <int W, typename T>
+__device__ __forceinline__ int fill_row(T* row, const T* c0, const T* c1, const T* c2, int p, T scale,
+                                        const WindowPoly& wp, int z0) {
+    using G = Col3<W>;
+    int f0, f1, f2;
+    window_poly<W, T>(c0[p], wp, T(1), f0, row + G::WX);
+    window_poly<W, T>(c1[p], wp, T(1), f1, row + G::WY);
+    window_poly<W, T>(c2[p], wp, scale, f2, row + G::WZ);
+    return f2 - z0;
+}
+
+template <int W, typename T>
+__device__ __forceinline__ void load_wz(const T* row, T (&wz)[W]) {
+    if (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < W; k += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(row + k);
+            wz[k] = v.x;
+            if (k + 1 < W) wz[k + 1] = v.y;
+            if (k + 2 < W) wz[k + 2] = v.z;
+            if (k + 3 < W) wz[k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; k += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(row + k);
+            wz[k] = v.x;
+            if (k + 1 < W) wz[k + 1] = v.y;
+        }
+    }
+}
+
+// One segment of a batch: the points whose cell has z-offset DZ0 in the column.
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void spread_segment(T (&acc)[Q][E], const T* wt, int mydz, const int (&ri)[Q],
+                                               const int (&rj)[Q], const bool (&rv)[Q]);
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void interp_segment(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
+                                               const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]);
+
+template <int W, int Q, int E, typename T, int... DZ>
+__device__ __forceinline__ void spread_batch(T (&acc)[Q][E], const T* wt, int mydz, const int (&ri)[Q],
+                                             const int (&rj)[Q], const bool (&rv)[Q],
+                                             std::integer_sequence<int, DZ...>) {
+    (spread_segment<W, Q, E, DZ, T>(acc, wt, mydz, ri, rj, rv), ...);
+}
+
+template <int W, int Q, int E, typename T, int... DZ>
+__device__ __forceinline__ void interp_batch(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
+                                             const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q],
+                                             std::integer_sequence<int, DZ...>) {
+    (interp_segment<W, Q, E, DZ, T>(win, wt, rd, lane, mydz, ri, rj, rv), ...);
+}
+
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void add_taps(T (&acc)[Q][E], const T (&a)[Q], const T (&wz)[W]) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q][DZ0 + k] = fma(a[q], wz[k], acc[q][DZ0 + k]);
+    }
+}
+
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ T dot_taps(const T (&win)[Q][E], const T (&a)[Q], const T (&wz)[W]) {
+    T r = T(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < W; ++k) s = fma(win[q][DZ0 + k], wz[k], s);
+        r = fma(a[q], s, r);
+    }
+    return r;
+}
+
+// Lanes owning a row (i, j) of the W x W column window: row lane + 32 q.
+template <int W, int Q>
+__device__ __forceinline__ void lane_rows(int lane, int (&ri)[Q], int (&rj)[Q], bool (&rv)[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        rv[q] = r < W * W;
+        ri[q] = rv[q] ? r / W : 0;
+        rj[q] = rv[q] ? r % W : 0;
+    }
+}
+
+template <int W, int Q, typename T>
+__device__ __forceinline__ void row_products(const T* row, const int (&ri)[Q], const int (&rj)[Q],
+                                             const bool (&rv)[Q], T (&av)[Q]) {
+    using G = Col3<W>;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) av[q] = rv[q] ? row[G::WX + ri[q]] * row[G::WY + rj[q]] : T(0);
+}
+
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void spread_segment(T (&acc)[Q][E], const T* wt, int mydz, const int (&ri)[Q],
+                                               const int (&rj)[Q], const bool (&rv)[Q]) {
+    using G = Col3<W>;
+    unsigned mask = __ballot_sync(0xffffffffu, mydz == DZ0);
+    while (mask) {
+        const int pp = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const T* row = wt + pp * G::STRIDE;
+        T av[Q];
+        row_products<W, Q, T>(row, ri, rj, rv, av);
+        T wz[W];
+        load_wz<W, T>(row + G::WZ, wz);
+        add_taps<W, Q, E, DZ0, T>(acc, av, wz);
+    }
+}
+
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void interp_segment(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
+                                               const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]) {
+    using G = Col3<W>;
+    unsigned mask = __ballot_sync(0xffffffffu, mydz == DZ0);
+    while (mask) {
+        const int pp = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const T* row = wt + pp * G::STRIDE;
+        T av[Q];
+        row_products<W, Q, T>(row, ri, rj, rv, av);
+        T wz[W];
+        load_wz<W, T>(row + G::WZ, wz);
+        rd[pp * 33 + lane] = dot_taps<W, Q, E, DZ0, T>(win, av, wz);
+    }
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
+    using G = Col3<W>;
+    constexpr int Q = G::Q, E = G::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sub = reinterpret_cast<T*>(smem_raw);
+    T* tab = sub + ((G::SUB + 3) / 4) * 4;
+    __shared__ int col_next;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* wt = tab + warp * 32 * G::STRIDE;
+
+    const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
+    const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
+    for (int c = threadIdx.x; c < G::SUB; c += blockDim.x) sub[c] = T(0);
+    if (threadIdx.x == 0) col_next = col0 + kWarps;
+    __syncthreads();
+
+    const T* c0 = static_cast<const T*>(a.coord[0]);
+    const T* c1 = static_cast<const T*>(a.coord[1]);
+    const T* c2 = static_cast<const T*>(a.coord[2]);
+    int ri[Q], rj[Q];
+    bool rv[Q];
+    lane_rows<W, Q>(lane, ri, rj, rv);
+    const int z0 = bz * G::BZ;
+    const int64_t kbase = int64_t(bin) * (G::NCOL * G::BZ);
+
+    int col = col0 + warp;
+    while (col < col1) {
+        const int start = a.key_start[kbase + col * G::BZ];
+        const int end = a.key_start[kbase + (col + 1) * G::BZ];
+        if (start < end) {
+            T acc[Q][E];
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[q][e] = T(0);
+            for (int base = start; base < end; base += 32) {
+                const int cnt = min(32, end - base);
+                int mydz = -1;
+                if (lane < cnt)
+                    mydz = fill_row<W, T>(wt + lane * G::STRIDE, c0, c1, c2, base + lane, T(a.w[base + lane]),
+                                          a.wp, z0);
+                __syncwarp();
+                spread_batch<W, Q, E, T>(acc, wt, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
+                __syncwarp();
+            }
+            const int cx = col / G::BY, cy = col % G::BY;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                if (!rv[q]) continue;
+                T* srow = sub + ((cx + ri[q]) * G::SY + (cy + rj[q])) * G::SZ;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (acc[q][e] != T(0)) atomicAdd(srow + e, acc[q][e]);
+            }
+        }
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&col_next, 1);
+        col = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    __syncthreads();
+
+    T* grid = static_cast<T*>(a.grid);
+    const int n = a.n_os;
+    const int ox = bx * G::BX - (W / 2 - 1), oy = by * G::BY - (W / 2 - 1), oz = z0 - (W / 2 - 1);
+    for (int c = threadIdx.x; c < G::SUB; c += blockDim.x) {
+        const T v = sub[c];
+        if (v == T(0)) continue;
+        const int lz = c % G::SZ, ly = (c / G::SZ) % G::SY, lx = c / (G::SZ * G::SY);
+        const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+        if (gx < 0 || gx >= n || gy < 0 || gy >= n || gz < 0 || gz >= n) continue;
+        atomicAdd(&grid[(int64_t(gx) * n + gy) * n + gz], v);
+    }
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_interp3_col(InterpArgs a, Epilogue e) {
+    using G = Col3<W>;
+    constexpr int Q = G::Q, E = G::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tab = reinterpret_cast<T*>(smem_raw);
+    T* red = tab + kWarps * 32 * G::STRIDE;
+    __shared__ int col_next;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* wt = tab + warp * 32 * G::STRIDE;
+    T* rd = red + warp * 32 * 33;
+
+    const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
+    const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
+    if (threadIdx.x == 0) col_next = col0 + kWarps;
+    __syncthreads();
+    const T* c0 = static_cast<const T*>(a.coord[0]);
+    const T* c1 = static_cast<const T*>(a.coord[1]);
+    const T* c2 = static_cast<const T*>(a.coord[2]);
+    const T* grid = static_cast<const T*>(a.grid);
+    const int n = a.n_os;
+    int ri[Q], rj[Q];
+    bool rv[Q];
+    lane_rows<W, Q>(lane, ri, rj, rv);
+    const int z0 = bz * G::BZ;
+    const int gz0 = z0 - (W / 2 - 1);
+    const int64_t kbase = int64_t(bin) * (G::NCOL * G::BZ);
+    double sq = 0.0, bad = 0.0, dot = 0.0;
+
+    int col = col0 + warp;
+    while (col < col1) {
+        const int start = a.key_start[kbase + col * G::BZ];
+        const int end = a.key_start[kbase + (col + 1) * G::BZ];
+        if (start < end) {
+            const int cx = col / G::BY, cy = col % G::BY;
+            T win[Q][E];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int gx = bx * G::BX + cx - (W / 2 - 1) + ri[q];
+                const int gy = by * G::BY + cy - (W / 2 - 1) + rj[q];
+                const T* grow = grid + (int64_t(gx) * n + gy) * n;
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int gz = gz0 + k;
+                    win[q][k] = (rv[q] && gz >= 0 && gz < n) ? __ldg(grow + gz) : T(0);
+                }
+            }
+            for (int base = start; base < end; base += 32) {
+                const int cnt = min(32, end - base);
+                int mydz = -1;
+                if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, c0, c1, c2, base + lane, T(1), a.wp, z0);
+                __syncwarp();
+                interp_batch<W, Q, E, T>(win, wt, rd, lane, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
+                __syncwarp();
+                if (lane < cnt) {
+                    T t = T(0);
+#pragma unroll 8
+                    for (int l = 0; l < 32; ++l) t += rd[lane * 33 + l];
+                    epi_point(e, base + lane, double(t), sq, bad, dot);
+                }
+                __syncwarp();
+            }
+        }
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&col_next, 1);
+        col = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    epi_finish(e, sq, bad, dot);
+}
+
+// ------------------------------------------------------------------ dispatch
+template <int W, typename T>
+size_t spread3_smem() {
+    using G = Col3<W>;
+    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kWarps) * 32 * G::STRIDE) * sizeof(T);
+}
+
+template <int W, typename T>
+size_t interp3_smem() {
+    using G = Col3<W>;
+    return (size_t(kWarps) * 32 * G::STRIDE + size_t(kWarps) * 32 * 33) * sizeof(T);
+}
+
+template <auto K>
+static cudaError_t opt_in(size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static unsigned long long configured = 0ull;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured & (1ull << (dev & 63))) return cudaSuccess;
+    cudaError_t err = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (err == cudaSuccess) configured |= (1ull << (dev & 63));
+    return err;
+}
+
+template <int W, typename T>
+static cudaError_t spread3_one(const SpreadArgs& a, cudaStream_t s) {
+    const size_t bytes = spread3_smem<W, T>();
+    cudaError_t err = opt_in<k_spread3_col<W, T>>(bytes);
+    if (err != cudaSuccess) return err;
+    if (a.ntasks == 0) return cudaSuccess;
+    k_spread3_col<W, T><<<a.ntasks, 256, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int W, typename T>
+static cudaError_t interp3_one(const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
+    const size_t bytes = interp3_smem<W, T>();
+    cudaError_t err = opt_in<k_interp3_col<W, T>>(bytes);
+    if (err != cudaSuccess) return err;
+    if (a.ntasks == 0) return cudaSuccess;
+    k_interp3_col<W, T><<<a.ntasks, 256, bytes, s>>>(a, e);
+    return cudaGetLastError();
+}
+
+bool column_kernels(int d, int W) { return d == 3 && W <= 10; }
+
+template <typename T>
+cudaError_t launch_spread3(int W, const SpreadArgs& a, cudaStream_t s) {
+    switch (W) {
+        case 4: return spread3_one<4, T>(a, s);
+        case 6: return spread3_one<6, T>(a, s);
+        case 8: return spread3_one<8, T>(a, s);
+        case 10: return spread3_one<10, T>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_interp3(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
+    switch (W) {
+        case 4: return interp3_one<4, T>(a, e, s);
+        case 6: return interp3_one<6, T>(a, e, s);
+        case 8: return interp3_one<8, T>(a, e, s);
+        case 10: return interp3_one<10, T>(a, e, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_spread3<float>(int, const SpreadArgs&, cudaStream_t);
+template cudaError_t launch_spread3<double>(int, const SpreadArgs&, cudaStream_t);
+template cudaError_t launch_interp3<float>(int, const InterpArgs&, const Epilogue&, cudaStream_t);
+template cudaError_t launch_interp3<double>(int, const InterpArgs&, const Epilogue&, cudaStream_t);
+
+}  // namespace sk
