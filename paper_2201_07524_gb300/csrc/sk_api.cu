@@ -403,6 +403,25 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
         c.tasks = static_cast<int*>(dalloc(P, size_t(3 * std::max(c.ntasks, 1)) * sizeof(int)));
         k_fill_tasks<<<nblk(P->nbins), 256, 0, P->ps>>>(suboff, P->nbins, ncol, c.tasks);
         CK(cudaGetLastError());
+        // heaviest tasks first (longest-processing-time order), so the blocks
+        // that start last are the short ones
+        std::vector<int> tk(size_t(3) * c.ntasks), bs(size_t(P->nbins) + 1);
+        CK(cudaMemcpyAsync(tk.data(), c.tasks, tk.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaMemcpyAsync(bs.data(), c.bin_start, bs.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+        std::vector<int> order(c.ntasks);
+        std::vector<double> load(c.ntasks);
+        for (int i = 0; i < c.ntasks; ++i) {
+            order[i] = i;
+            const int b = tk[3 * i];
+            load[i] = double(bs[b + 1] - bs[b]) * (tk[3 * i + 2] - tk[3 * i + 1]) / ncol;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return load[p] > load[q]; });
+        std::vector<int> sorted(tk.size());
+        for (int i = 0; i < c.ntasks; ++i)
+            for (int k = 0; k < 3; ++k) sorted[3 * i + k] = tk[3 * order[i] + k];
+        CK(cudaMemcpyAsync(c.tasks, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
     }
     k_fill<<<nblk(n), 256, 0, P->ps>>>(c.scal, n, 1.0);
     CK(cudaGetLastError());
@@ -482,7 +501,40 @@ void build_grid(sk_plan* P) {
         f.A3 = dalloc(P, size_t(K * K * H) * sizeof(C));
     }
     f.grid = dalloc(P, P->grid_elems * sizeof(T));
+    f.grid_out = dalloc(P, P->grid_elems * sizeof(T));
     CK(cudaMemsetAsync(f.grid, 0, P->grid_elems * sizeof(T), P->ps));
+    CK(cudaMemsetAsync(f.grid_out, 0, P->grid_elems * sizeof(T), P->ps));
+    // the spectra are zero outside the band between products (see sk_fft.cu)
+    if (P->d == 1) {
+        CK(cudaMemsetAsync(f.A1, 0, size_t(2 * H) * sizeof(C), P->ps));
+    } else if (P->d == 2) {
+        CK(cudaMemsetAsync(f.A1, 0, size_t(n * H) * sizeof(C), P->ps));
+    } else {
+        CK(cudaMemsetAsync(f.A1, 0, size_t(n * n * H) * sizeof(C), P->ps));
+        CK(cudaMemsetAsync(f.A2, 0, size_t(n * K * H) * sizeof(C), P->ps));
+    }
+    // band of cells holding every point's window taps, from both clouds
+    int* bounds = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&bounds), 6 * sizeof(int), P->ps));
+    k_init_bounds<<<1, 32, 0, P->ps>>>(bounds);
+    CK(cudaGetLastError());
+    launch_cell_bounds<T>(P->X.coord, P->X.n, P->d, bounds, P->ps);
+    launch_cell_bounds<T>(P->Y.coord, P->Y.n, P->d, bounds, P->ps);
+    CK(cudaGetLastError());
+    int hb[6];
+    CK(cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    CK(cudaFreeAsync(bounds, P->ps));
+    const int m = P->prm.m_w;
+    for (int t = 0; t < 3; ++t) {
+        if (t < P->d) {
+            f.lo[t] = std::max(0, hb[t] - (m - 1));
+            f.hi[t] = std::min(P->n_os - 1, hb[3 + t] + m);
+        } else {
+            f.lo[t] = 0;
+            f.hi[t] = 0;
+        }
+    }
 }
 
 template <typename T>
@@ -518,9 +570,7 @@ Epilogue make_epilogue(sk_plan* P, int mode, Cloud& dst, int slot, double* out) 
 
 template <typename T>
 void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
-    int st = stage_begin(P, SK_STAGE_OTHER);
-    CK(cudaMemsetAsync(P->fft.grid, 0, P->grid_elems * sizeof(T), P->ps));
-    stage_end(P, st);
+    // the grid is zero here: the first FFT pass zeroes what spreading wrote
     SpreadArgs a{};
     for (int t = 0; t < 3; ++t) a.coord[t] = src.coord[t];
     a.w = w;
@@ -537,7 +587,7 @@ void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
     a.knorm = P->knorm;
     a.grid = P->fft.grid;
     a.wp = P->wp;
-    st = stage_begin(P, SK_STAGE_SPREAD);
+    const int st = stage_begin(P, SK_STAGE_SPREAD);
     CK(launch_spread<T>(P->d, P->W, a, P->ps));
     if ((column_kernels(P->d, P->W) ? src.ntasks : src.nsub) > 0) ++P->launches;
     stage_end(P, st);
@@ -555,7 +605,7 @@ void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
     a.n_os = P->n_os;
     a.beta = P->beta;
     a.knorm = P->knorm;
-    a.grid = P->fft.grid;
+    a.grid = P->fft.grid_out;
     a.wp = P->wp;
     int st = stage_begin(P, SK_STAGE_INTERP);
     CK(launch_interp<T>(P->d, P->W, a, e, &P->launches, P->ps));

@@ -2,8 +2,9 @@
 // Eq. (fastsum)) and the pointwise multiply by the kernel's Fourier
 // coefficients, written for shared memory:
 //
-//   * Every block loads P pencils of length n (P * n = kFftElems complex
-//     values) into shared memory, runs a radix-2 FFT there and writes back.
+//   * Every block loads P pencils of length n (P * n = kFftBlockElems complex
+//     values, or one pencil when n is larger) into shared memory, runs a
+//     radix-2 FFT there and writes back.
 //     Pencils are padded to n+1 elements so that the loads, which walk the
 //     pencils in parallel, do not collide in shared-memory banks.
 //   * The grid is real, so the first pass packs two real rows into one complex
@@ -14,6 +15,14 @@
 //   * The multiply by c_k b_k / psihat(k)^2 is fused into the pass along
 //     axis 0: forward FFT, multiply, inverse FFT in one kernel.
 //
+//   * Band pruning: every point and all its window taps lie inside a box
+//     [lo_t, hi_t] per axis (known at plan time), so outside it the spread grid
+//     is zero and the interpolated grid is never read.  The first pass only
+//     transforms rows inside the box (and zeroes them after reading, so the next
+//     spreading starts from a zero grid without a memset), the axis-1 passes
+//     only pencils whose axis-0 index is inside the box, and the last pass only
+//     rows inside the box, into a second grid that interpolation reads.
+//
 // Convolution pipeline (n = n_os, h = N/2, grid g[x][y][z] with z contiguous):
 //   3-D: r2c(z) -> fwd(y, keep 2h+1) -> [fwd(x) * M, inv(x)] -> inv(y) -> c2r(z)
 //   2-D: r2c(y) -> [fwd(x) * M, inv(x)] -> c2r(y)
@@ -23,6 +32,23 @@
 namespace sk {
 
 enum { FULL = 0, CENTERED = 1 };
+
+constexpr int kFftBlockElems = 1024;
+
+__host__ __device__ __forceinline__ int fft_pencils(int n) { return n >= kFftBlockElems ? 1 : kFftBlockElems / n; }
+
+// Row pairs of the real passes: pair q covers rows r0 = o * ostride + y and
+// r0 + 1 with o = olo + q / npo and y = ylo + 2 (q % npo).
+struct RowPairs {
+    int64_t olo, ostride;
+    int ylo, npo;
+    int64_t npairs;
+};
+
+__device__ __forceinline__ int64_t pair_row(const RowPairs& rp, int64_t q) {
+    const int64_t o = rp.olo + q / rp.npo;
+    return o * rp.ostride + rp.ylo + 2 * (q % rp.npo);
+}
 
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
@@ -96,15 +122,16 @@ __device__ void fft_dif(typename Cplx<T>::type* buf, int ns, int n, int log2n, i
     __syncthreads();
 }
 
-// Two real rows (2q, 2q+1) of length n -> two half spectra of length h+1.
+// Two real rows of length n -> two half spectra of length h+1 (output rows
+// are the same row indices in A1).  The input rows are zeroed after reading.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_r2c_rows(const T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
-                                                      int64_t npairs, int n, int log2n, int h,
+__global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
+                                                      RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ tw) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
-    const int P = kFftElems >> log2n;
+    const int P = fft_pencils(n);
     const int ns = n + 1;
     const int64_t q0 = int64_t(blockIdx.x) * P;
     for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
@@ -114,9 +141,12 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(const T* __restrict__ g, t
         C z;
         z.x = T(0);
         z.y = T(0);
-        if (q < npairs) {
-            z.x = g[(2 * q) * n + l];
-            z.y = g[(2 * q + 1) * n + l];
+        if (q < rp.npairs) {
+            const int64_t r0 = pair_row(rp, q);
+            z.x = g[r0 * n + l];
+            z.y = g[(r0 + 1) * n + l];
+            g[r0 * n + l] = T(0);
+            g[(r0 + 1) * n + l] = T(0);
         }
         buf[p * ns + bitrev(l, log2n)] = z;
     }
@@ -126,7 +156,8 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(const T* __restrict__ g, t
         const int p = e / H;
         const int k = e - p * H;
         const int64_t q = q0 + p;
-        if (q >= npairs) continue;
+        if (q >= rp.npairs) continue;
+        const int64_t r0 = pair_row(rp, q);
         const C zk = buf[p * ns + k];
         const C zm = buf[p * ns + ((n - k) & (n - 1))];
         C A, Bv;
@@ -134,20 +165,20 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(const T* __restrict__ g, t
         A.y = (zk.y - zm.y) * T(0.5);
         Bv.x = (zk.y + zm.y) * T(0.5);
         Bv.y = (zm.x - zk.x) * T(0.5);
-        out[(2 * q) * H + k] = A;
-        out[(2 * q + 1) * H + k] = Bv;
+        out[r0 * H + k] = A;
+        out[(r0 + 1) * H + k] = Bv;
     }
 }
 
-// Two half spectra (rows 2q, 2q+1) -> two real rows, by Hermitian completion.
+// Two half spectra -> two real rows, by Hermitian completion.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
-                                                      int64_t npairs, int n, int log2n, int h,
+                                                      RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ tw) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
-    const int P = kFftElems >> log2n;
+    const int P = fft_pencils(n);
     const int ns = n + 1;
     const int H = h + 1;
     const int64_t q0 = int64_t(blockIdx.x) * P;
@@ -158,17 +189,18 @@ __global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::ty
         C z;
         z.x = T(0);
         z.y = T(0);
-        if (q < npairs) {
+        if (q < rp.npairs) {
+            const int64_t r0 = pair_row(rp, q);
             const int k = pos <= (n >> 1) ? pos : pos - n;
             if (k >= 0 && k <= h) {
-                C A = in[(2 * q) * H + k];
-                C Bv = in[(2 * q + 1) * H + k];
+                C A = in[r0 * H + k];
+                C Bv = in[(r0 + 1) * H + k];
                 if (k == 0) { A.y = T(0); Bv.y = T(0); }
                 z.x = A.x - Bv.y;
                 z.y = A.y + Bv.x;
             } else if (k < 0 && -k <= h) {
-                const C A = in[(2 * q) * H - k];
-                const C Bv = in[(2 * q + 1) * H - k];
+                const C A = in[r0 * H - k];
+                const C Bv = in[(r0 + 1) * H - k];
                 z.x = A.x + Bv.y;
                 z.y = Bv.x - A.y;
             }
@@ -180,30 +212,35 @@ __global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::ty
         const int p = e >> log2n;
         const int l = e & (n - 1);
         const int64_t q = q0 + p;
-        if (q >= npairs) continue;
+        if (q >= rp.npairs) continue;
+        const int64_t r0 = pair_row(rp, q);
         const C v = buf[p * ns + bitrev(l, log2n)];
-        g[(2 * q) * n + l] = v.x;
-        g[(2 * q + 1) * n + l] = v.y;
+        g[r0 * n + l] = v.x;
+        g[(r0 + 1) * n + l] = v.y;
     }
 }
 
 // Pencils along the middle axis of an (O, L, I) array: element k of pencil
-// q = o*I + i sits at (o*L + k)*I + i.  FULL keeps all n entries along the
-// axis; CENTERED stores frequencies -h..h at positions 0..2h.
+// (o, i) sits at (o*L + k)*I + i.  FULL keeps all n entries along the axis;
+// CENTERED stores frequencies -h..h at positions 0..2h.  Only pencils with
+// o in [olo, olo + ocnt) are transformed, and a FULL output is stored only for
+// k in [klo, klo + kcnt).
 template <typename T, int INM, int OUTM, bool INV>
 __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* __restrict__ in,
-                                                  typename Cplx<T>::type* __restrict__ out, int64_t O, int64_t I,
-                                                  int n, int log2n, int h,
+                                                  typename Cplx<T>::type* __restrict__ out, int64_t olo, int64_t ocnt,
+                                                  int64_t I, int klo, int kcnt, int n, int log2n, int h,
                                                   const typename Cplx<T>::type* __restrict__ tw) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
-    const int P = kFftElems >> log2n;
+    const int P = fft_pencils(n);
     const int ns = n + 1;
-    const int64_t Q = O * I;
+    const int64_t Q = ocnt * I;
     const int64_t q0 = int64_t(blockIdx.x) * P;
     const int Lin = INM == FULL ? n : 2 * h + 1;
     const int Lout = OUTM == FULL ? n : 2 * h + 1;
+    const int k0 = OUTM == FULL ? klo : 0;
+    const int kn = OUTM == FULL ? kcnt : Lout;
     if (INM == CENTERED) {
         for (int e = threadIdx.x; e < P * ns; e += blockDim.x) {
             buf[e].x = T(0);
@@ -216,17 +253,18 @@ __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* 
         const int pl = e - k * P;
         const int64_t q = q0 + pl;
         if (q >= Q) continue;
-        const int64_t o = q / I, i = q - o * I;
+        const int64_t o = olo + q / I, i = q % I;
         const int pos = INM == FULL ? k : ((k - h) & (n - 1));
         buf[pl * ns + bitrev(pos, log2n)] = in[(o * Lin + k) * I + i];
     }
     fft_dit<T, INV>(buf, ns, n, log2n, P, tw);
-    for (int e = threadIdx.x; e < P * Lout; e += blockDim.x) {
-        const int k = e / P;
-        const int pl = e - k * P;
+    for (int e = threadIdx.x; e < P * kn; e += blockDim.x) {
+        const int kk = e / P;
+        const int pl = e - kk * P;
         const int64_t q = q0 + pl;
         if (q >= Q) continue;
-        const int64_t o = q / I, i = q - o * I;
+        const int k = k0 + kk;
+        const int64_t o = olo + q / I, i = q % I;
         const int pos = OUTM == FULL ? k : ((k - h) & (n - 1));
         out[(o * Lout + k) * I + i] = buf[pl * ns + pos];
     }
@@ -234,14 +272,17 @@ __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* 
 
 // Pencils along axis 0 of an (n, I) array: forward FFT, multiply the kept
 // frequencies by M[(k+h)*I + q] and zero the rest, inverse FFT, in place.
+// Only axis-0 positions in [xlo, xlo + xcnt) are loaded (the rest are zero)
+// and stored (the rest are never read).
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::type* __restrict__ data, int64_t I,
-                                                            int n, int log2n, int h, const T* __restrict__ mult,
+                                                            int xlo, int xcnt, int n, int log2n, int h,
+                                                            const T* __restrict__ mult,
                                                             const typename Cplx<T>::type* __restrict__ tw) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
-    const int P = kFftElems >> log2n;
+    const int P = fft_pencils(n);
     const int ns = n + 1;
     const int64_t q0 = int64_t(blockIdx.x) * P;
     for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
@@ -251,7 +292,7 @@ __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::ty
         C v;
         v.x = T(0);
         v.y = T(0);
-        if (q < I) v = data[int64_t(k) * I + q];
+        if (q < I && k >= xlo && k < xlo + xcnt) v = data[int64_t(k) * I + q];
         buf[pl * ns + bitrev(k, log2n)] = v;
     }
     fft_dit<T, false>(buf, ns, n, log2n, P, tw);
@@ -271,9 +312,9 @@ __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::ty
         }
     }
     fft_dif<T, true>(buf, ns, n, log2n, P, tw);
-    for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-        const int k = e / P;
-        const int pl = e - k * P;
+    for (int e = threadIdx.x; e < P * xcnt; e += blockDim.x) {
+        const int k = xlo + e / P;
+        const int pl = e % P;
         const int64_t q = q0 + pl;
         if (q < I) data[int64_t(k) * I + q] = buf[pl * ns + bitrev(k, log2n)];
     }
@@ -345,15 +386,14 @@ __global__ void k_fill_forward(const double* __restrict__ fhat, int d, int h, co
 
 template <typename T>
 static size_t fft_smem_bytes(int n) {
-    const int P = kFftElems / n;
-    return size_t(P) * size_t(n + 1) * sizeof(typename Cplx<T>::type);
+    return size_t(fft_pencils(n)) * size_t(n + 1) * sizeof(typename Cplx<T>::type);
 }
 
 // Largest dynamic shared memory any FFT launch of this precision can use:
-// P (n+1) complex values with P n = kFftElems and n >= 16.
+// one pencil of the largest length, 4096 (P (n + 1) is largest there).
 template <typename T>
 static size_t fft_smem_max() {
-    return size_t(kFftElems + kFftElems / 16) * sizeof(typename Cplx<T>::type);
+    return size_t(4096 + 1) * sizeof(typename Cplx<T>::type);
 }
 
 // Opt a kernel into its largest shared-memory size once per device (the cache
@@ -377,56 +417,89 @@ static cudaError_t ensure_smem() {
         if (e_ != cudaSuccess) return e_;           \
     } while (0)
 
+// Row pairs of the real passes for the plan's grid: all rows of the 1-D grid
+// (the data row and its zero partner); in 2-D the rows x of the band, paired
+// (x, x+1); in 3-D the rows (x, y) of the band, paired along y.
+static RowPairs row_pairs(const FftPlan& f) {
+    RowPairs rp{};
+    if (f.d == 1) {
+        rp.olo = 0; rp.ostride = 0; rp.ylo = 0; rp.npo = 1; rp.npairs = 1;
+        return rp;
+    }
+    const int a = f.d == 2 ? 0 : 1;                 // the axis whose rows are paired
+    const int ylo = f.lo[a] & ~1;
+    const int yhi = f.hi[a] | 1;                    // inclusive, odd
+    rp.ylo = ylo;
+    rp.npo = (yhi - ylo + 1) / 2;
+    if (f.d == 2) {
+        rp.olo = 0; rp.ostride = 0; rp.npairs = rp.npo;
+    } else {
+        rp.olo = f.lo[0]; rp.ostride = f.n; rp.npairs = int64_t(f.hi[0] - f.lo[0] + 1) * rp.npo;
+    }
+    return rp;
+}
+
 template <typename T>
-static cudaError_t run_r2c(const FftPlan& f, int64_t nrows, int64_t* launches, cudaStream_t s) {
+static cudaError_t run_r2c(const FftPlan& f, int64_t* launches, cudaStream_t s) {
     using C = typename Cplx<T>::type;
-    const size_t bytes = fft_smem_bytes<T>(f.n);
     SK_TRY((ensure_smem<T, k_fft_r2c_rows<T>>()));
-    const int64_t npairs = nrows / 2;
-    const int P = kFftElems / f.n;
-    k_fft_r2c_rows<T><<<unsigned((npairs + P - 1) / P), 256, bytes, s>>>(
-        static_cast<const T*>(f.grid), static_cast<C*>(f.A1), npairs, f.n, f.log2n, f.h,
-        static_cast<const C*>(f.tw));
+    const RowPairs rp = row_pairs(f);
+    const int P = fft_pencils(f.n);
+    k_fft_r2c_rows<T><<<unsigned((rp.npairs + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+        static_cast<T*>(f.grid), static_cast<C*>(f.A1), rp, f.n, f.log2n, f.h, static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t run_c2r(const FftPlan& f, int64_t nrows, int64_t* launches, cudaStream_t s) {
+static cudaError_t run_c2r(const FftPlan& f, int64_t* launches, cudaStream_t s) {
     using C = typename Cplx<T>::type;
-    const size_t bytes = fft_smem_bytes<T>(f.n);
     SK_TRY((ensure_smem<T, k_fft_c2r_rows<T>>()));
-    const int64_t npairs = nrows / 2;
-    const int P = kFftElems / f.n;
-    k_fft_c2r_rows<T><<<unsigned((npairs + P - 1) / P), 256, bytes, s>>>(
-        static_cast<const C*>(f.A1), static_cast<T*>(f.grid), npairs, f.n, f.log2n, f.h,
+    const RowPairs rp = row_pairs(f);
+    const int P = fft_pencils(f.n);
+    k_fft_c2r_rows<T><<<unsigned((rp.npairs + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+        static_cast<const C*>(f.A1), static_cast<T*>(f.grid_out), rp, f.n, f.log2n, f.h,
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
 template <typename T, int INM, int OUTM, bool INV>
-static cudaError_t run_axis(const FftPlan& f, const void* in, void* out, int64_t O, int64_t I,
-                            int64_t* launches, cudaStream_t s) {
+static cudaError_t run_axis(const FftPlan& f, const void* in, void* out, int64_t olo, int64_t ocnt, int64_t I,
+                            int klo, int kcnt, int64_t* launches, cudaStream_t s) {
     using C = typename Cplx<T>::type;
-    const size_t bytes = fft_smem_bytes<T>(f.n);
     SK_TRY((ensure_smem<T, k_fft_axis<T, INM, OUTM, INV>>()));
-    const int P = kFftElems / f.n;
-    const int64_t Q = O * I;
-    k_fft_axis<T, INM, OUTM, INV><<<unsigned((Q + P - 1) / P), 256, bytes, s>>>(
-        static_cast<const C*>(in), static_cast<C*>(out), O, I, f.n, f.log2n, f.h, static_cast<const C*>(f.tw));
+    const int P = fft_pencils(f.n);
+    const int64_t Q = ocnt * I;
+    k_fft_axis<T, INM, OUTM, INV><<<unsigned((Q + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+        static_cast<const C*>(in), static_cast<C*>(out), olo, ocnt, I, klo, kcnt, f.n, f.log2n, f.h,
+        static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
+}
+
+// Axis-0 positions the spectra hold outside zero: the band, widened to the
+// row pairs in 2-D (where axis 0 is the paired axis).
+static void axis0_range(const FftPlan& f, int& lo, int& cnt) {
+    lo = f.lo[0];
+    int hi = f.hi[0];
+    if (f.d == 2) {
+        lo &= ~1;
+        hi |= 1;
+    }
+    cnt = hi - lo + 1;
 }
 
 template <typename T>
 static cudaError_t run_axis0_convolve(const FftPlan& f, void* data, int64_t I, int64_t* launches, cudaStream_t s) {
     using C = typename Cplx<T>::type;
-    const size_t bytes = fft_smem_bytes<T>(f.n);
     SK_TRY((ensure_smem<T, k_fft_axis0_convolve<T>>()));
-    const int P = kFftElems / f.n;
-    k_fft_axis0_convolve<T><<<unsigned((I + P - 1) / P), 256, bytes, s>>>(
-        static_cast<C*>(data), I, f.n, f.log2n, f.h, static_cast<const T*>(f.mult), static_cast<const C*>(f.tw));
+    const int P = fft_pencils(f.n);
+    int xlo, xcnt;
+    axis0_range(f, xlo, xcnt);
+    k_fft_axis0_convolve<T><<<unsigned((I + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+        static_cast<C*>(data), I, xlo, xcnt, f.n, f.log2n, f.h, static_cast<const T*>(f.mult),
+        static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
 }
@@ -436,41 +509,45 @@ cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launc
     using C = typename Cplx<T>::type;
     const int64_t n = f.n, H = f.h + 1, K = 2 * f.h + 1;
     if (f.d == 1) {
-        SK_TRY(run_r2c<T>(f, 2, launches, s));
+        SK_TRY(run_r2c<T>(f, launches, s));
         k_mult_half<T><<<unsigned((H + 255) / 256), 256, 0, s>>>(static_cast<C*>(f.A1), f.h,
                                                                  static_cast<const T*>(f.mult));
         if (launches) ++*launches;
         SK_TRY(cudaGetLastError());
-        return run_c2r<T>(f, 2, launches, s);
+        return run_c2r<T>(f, launches, s);
     }
     if (f.d == 2) {
-        SK_TRY(run_r2c<T>(f, n, launches, s));
+        SK_TRY(run_r2c<T>(f, launches, s));
         SK_TRY(run_axis0_convolve<T>(f, f.A1, H, launches, s));
-        return run_c2r<T>(f, n, launches, s);
+        return run_c2r<T>(f, launches, s);
     }
-    SK_TRY(run_r2c<T>(f, n * n, launches, s));
-    SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A1, f.A2, n, H, launches, s)));
+    const int64_t xlo = f.lo[0], xcnt = f.hi[0] - f.lo[0] + 1;
+    const int ylo = f.lo[1] & ~1, ycnt = (f.hi[1] | 1) - ylo + 1;   // the row pairs of the real passes
+    SK_TRY(run_r2c<T>(f, launches, s));
+    SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A1, f.A2, xlo, xcnt, H, 0, 0, launches, s)));
     SK_TRY(run_axis0_convolve<T>(f, f.A2, K * H, launches, s));
-    SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A2, f.A1, n, H, launches, s)));
-    return run_c2r<T>(f, n * n, launches, s);
+    SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A2, f.A1, xlo, xcnt, H, ylo, ycnt, launches, s)));
+    (void)n;
+    return run_c2r<T>(f, launches, s);
 }
 
 template <typename T>
 cudaError_t launch_fft_adjoint(const FftPlan& f, double* fhat, cudaStream_t s, int64_t* launches) {
     using C = typename Cplx<T>::type;
-    const int64_t n = f.n, H = f.h + 1, K = 2 * f.h + 1;
+    const int64_t H = f.h + 1, K = 2 * f.h + 1;
     const void* S = nullptr;
     if (f.d == 1) {
-        SK_TRY(run_r2c<T>(f, 2, launches, s));
+        SK_TRY(run_r2c<T>(f, launches, s));
         S = f.A1;
     } else if (f.d == 2) {
-        SK_TRY(run_r2c<T>(f, n, launches, s));
-        SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A1, f.A3, 1, H, launches, s)));
+        SK_TRY(run_r2c<T>(f, launches, s));
+        SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A1, f.A3, 0, 1, H, 0, 0, launches, s)));
         S = f.A3;
     } else {
-        SK_TRY(run_r2c<T>(f, n * n, launches, s));
-        SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A1, f.A2, n, H, launches, s)));
-        SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A2, f.A3, 1, K * H, launches, s)));
+        SK_TRY(run_r2c<T>(f, launches, s));
+        SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A1, f.A2, f.lo[0], f.hi[0] - f.lo[0] + 1, H, 0, 0,
+                                                   launches, s)));
+        SK_TRY((run_axis<T, FULL, CENTERED, false>(f, f.A2, f.A3, 0, 1, K * H, 0, 0, launches, s)));
         S = f.A3;
     }
     int64_t total = 1;
@@ -492,14 +569,18 @@ cudaError_t launch_fft_forward(const FftPlan& f, const double* fhat, cudaStream_
     k_fill_forward<T><<<unsigned((total + 255) / 256), 256, 0, s>>>(fhat, f.d, f.h, f.psihat, static_cast<C*>(S));
     if (launches) ++*launches;
     SK_TRY(cudaGetLastError());
-    if (f.d == 1) return run_c2r<T>(f, 2, launches, s);
+    int xlo, xcnt;
+    axis0_range(f, xlo, xcnt);
+    (void)n;
+    if (f.d == 1) return run_c2r<T>(f, launches, s);
     if (f.d == 2) {
-        SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A3, f.A1, 1, H, launches, s)));
-        return run_c2r<T>(f, n, launches, s);
+        SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A3, f.A1, 0, 1, H, xlo, xcnt, launches, s)));
+        return run_c2r<T>(f, launches, s);
     }
-    SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A3, f.A2, 1, K * H, launches, s)));
-    SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A2, f.A1, n, H, launches, s)));
-    return run_c2r<T>(f, n * n, launches, s);
+    const int ylo = f.lo[1] & ~1, ycnt = (f.hi[1] | 1) - ylo + 1;
+    SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A3, f.A2, 0, 1, K * H, xlo, xcnt, launches, s)));
+    SK_TRY((run_axis<T, CENTERED, FULL, true>(f, f.A2, f.A1, xlo, xcnt, H, ylo, ycnt, launches, s)));
+    return run_c2r<T>(f, launches, s);
 }
 
 template cudaError_t launch_fft_convolve<float>(const FftPlan&, cudaStream_t, int64_t*);

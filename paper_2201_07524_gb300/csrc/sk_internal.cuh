@@ -24,7 +24,6 @@
 namespace sk {
 
 constexpr int kMaxP = 12;            // smoothness limit of the regularized kernel
-constexpr int kFftElems = 4096;      // complex elements per FFT block (P pencils x n)
 constexpr int kSpreadMaxPts = 1024;  // points per spreading subproblem
 constexpr int kTaskMaxPts = 4096;    // points per column task before a bin is split
 
@@ -83,11 +82,12 @@ struct Epilogue {
 // Piecewise-polynomial form of the Kaiser-Bessel window (the Horner scheme of
 // Barnett, Magland and af Klinteberg's FINUFFT): on each of its W = 2m unit
 // intervals the window, as a function of s = 2 frac - 1 in [-1, 1], is
-// replaced by its Chebyshev interpolant of degree 9 (FP32) or 14 (FP64),
+// replaced by its Chebyshev interpolant of degree 8 (FP32) or 14 (FP64),
 // written in monomials of s.  Tap k of a point with fractional offset frac is
 // psi(frac + m - 1 - k) ~ sum_i c[k][i] s^i.  The interpolation error is below
-// 4e-9 (degree 9) and 1e-14 (degree 14) of the window's peak for m >= 2.
-constexpr int kPolyDeg32 = 9;
+// 7e-8 (degree 8, m = 2), 7e-9 (degree 8, m >= 4) and 1e-14 (degree 14) of
+// the window's peak; FP32 rounding of the evaluation is ~6e-8.
+constexpr int kPolyDeg32 = 8;
 constexpr int kPolyDeg64 = 14;
 struct WindowPoly {
     float c32[16][kPolyDeg32 + 1];
@@ -141,7 +141,10 @@ struct FftPlan {
     int n = 0;          // n_os
     int log2n = 0;
     int h = 0;          // N/2
-    void* grid = nullptr;     // T*
+    void* grid = nullptr;     // T*, spreading target; zero outside the band, zeroed again by the first pass
+    void* grid_out = nullptr; // T*, written by the last pass inside the band, read by interpolation
+    int lo[3] = {0, 0, 0};    // band: cells lo[t]..hi[t] (inclusive) hold every point's window taps
+    int hi[3] = {0, 0, 0};
     void* A1 = nullptr;       // Cplx<T>*
     void* A2 = nullptr;       // Cplx<T>*, 3-D only
     void* A3 = nullptr;       // Cplx<T>*, stage entry points only
@@ -216,6 +219,9 @@ __device__ __forceinline__ double div_newton(double a, double t) {
 }
 
 // Per-point FP64 epilogue (Eq. (S1) update and Eq. (Error) residual terms).
+// UPDATE: sq += (u_old t - a)^2 and u = a / t (the residual of the state before
+// the update; the sum u_old t and the kernel sums are not needed inside the
+// iteration).  RESID: sq, dot += u t, and t itself, for the final report.
 __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t,
                                           double& sq, double& bad, double& dot) {
     if (e.mode == EPI_APPLY) {
@@ -226,12 +232,109 @@ __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t
     const double a = e.marg[i];
     const double r = fma(q, t, -a);
     sq = fma(r, r, sq);
-    dot = fma(q, t, dot);
-    e.t_store[i] = t;
     if (e.mode == EPI_UPDATE) {
-        const double qn = div_newton(a, t);
-        if (!(t > 0.0) || !isfinite(qn)) bad += 1.0;
-        e.scal[i] = qn;
+        const float tf = float(t);
+        if (!(tf >= 1.17549435e-38f && tf <= 3.0e38f)) bad += 1.0;
+        e.scal[i] = div_newton(a, t);
+    } else {
+        dot = fma(q, t, dot);
+        e.t_store[i] = t;
+    }
+}
+
+// The epilogue's per-point inputs (old scaling value and marginal), loaded one
+// batch ahead of their use.
+struct EpiPrefetch {
+    double q = 0.0, a = 0.0;
+    __device__ __forceinline__ void load(const Epilogue& e, int64_t i, bool ok) {
+        if (ok && e.mode != EPI_APPLY) {
+            q = e.scal[i];
+            a = e.marg[i];
+        }
+    }
+};
+
+// epi_point with the scaling value and marginal already loaded.
+__device__ __forceinline__ void epi_point_pre(const Epilogue& e, int64_t i, double t, double q, double a,
+                                              double& sq, double& bad, double& dot) {
+    if (e.mode == EPI_APPLY) {
+        e.out[e.perm[i]] = t;
+        return;
+    }
+    const double r = fma(q, t, -a);
+    sq = fma(r, r, sq);
+    if (e.mode == EPI_UPDATE) {
+        const float tf = float(t);
+        if (!(tf >= 1.17549435e-38f && tf <= 3.0e38f)) bad += 1.0;
+        e.scal[i] = div_newton(a, t);
+    } else {
+        dot = fma(q, t, dot);
+        e.t_store[i] = t;
+    }
+}
+
+// Reduction of the epilogue sums without a block-wide barrier: each warp adds
+// its sums into the block's shared slots; the last warp of the block to
+// arrive writes the block partial and takes part in the grid-wide
+// last-block-done reduction (deterministic order over blocks).
+// `warps_done` is a shared counter the kernel sets to 0 before its first
+// __syncthreads.
+__device__ __forceinline__ void epi_finish_warps(const Epilogue& e, double sq, double bad, double dot,
+                                                 unsigned* warps_done) {
+    if (e.mode == EPI_APPLY) return;
+    __shared__ double wsum[3][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned nw = (blockDim.x + 31) >> 5;
+    sq = warp_sum(sq);
+    bad = warp_sum(bad);
+    dot = warp_sum(dot);
+    bool last_warp = false;
+    if (lane == 0) {
+        wsum[0][wid] = sq;
+        wsum[1][wid] = bad;
+        wsum[2][wid] = dot;
+        __threadfence_block();
+        last_warp = atomicAdd(warps_done, 1u) == nw - 1;
+    }
+    last_warp = __shfl_sync(0xffffffffu, last_warp, 0);
+    if (!last_warp) return;
+    __threadfence_block();
+    double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+    if (lane < int(nw)) {
+        b0 = ((volatile double*)wsum[0])[lane];
+        b1 = ((volatile double*)wsum[1])[lane];
+        b2 = ((volatile double*)wsum[2])[lane];
+    }
+    // block sum in warp order (lanes are warps), then the grid step
+    b0 = warp_sum(b0);
+    b1 = warp_sum(b1);
+    b2 = warp_sum(b2);
+    bool last = false;
+    if (lane == 0) {
+        e.partial[3 * blockIdx.x + 0] = b0;
+        e.partial[3 * blockIdx.x + 1] = b1;
+        e.partial[3 * blockIdx.x + 2] = b2;
+        __threadfence();
+        last = atomicAdd(e.ticket, 1u) == gridDim.x - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (unsigned b = lane; b < gridDim.x; b += 32) {
+        s0 += ((volatile double*)e.partial)[3 * b + 0];
+        s1 += ((volatile double*)e.partial)[3 * b + 1];
+        s2 += ((volatile double*)e.partial)[3 * b + 2];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+        e.result[0] = s0;
+        e.result[1] = s1;
+        e.result[2] = s2;
+        if (s1 > 0.0 && e.status) atomicOr(e.status, 1);
+        *e.ticket = 0u;
     }
 }
 

@@ -441,7 +441,46 @@ __global__ void k_scatter(const double* __restrict__ in, const int* __restrict__
     if (i < n) out[perm[i]] = in[i];
 }
 
+// Smallest and largest cell index per axis over the points (atomics on ints;
+// out[0..2] start at INT_MAX, out[3..5] at INT_MIN).
+template <typename T>
+__global__ void k_cell_bounds(const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
+                              int64_t n, int d, int* __restrict__ out) {
+    const T* u[3] = {u0, u1, u2};
+    int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        for (int t = 0; t < d; ++t) {
+            const int f = int(floor(u[t][i]));
+            mn[t] = min(mn[t], f);
+            mx[t] = max(mx[t], f);
+        }
+    }
+    for (int t = 0; t < d; ++t) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[t] = min(mn[t], __shfl_xor_sync(0xffffffffu, mn[t], o));
+            mx[t] = max(mx[t], __shfl_xor_sync(0xffffffffu, mx[t], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&out[t], mn[t]);
+            atomicMax(&out[3 + t], mx[t]);
+        }
+    }
+}
+
+__global__ void k_init_bounds(int* out) {
+    if (threadIdx.x < 3) out[threadIdx.x] = INT_MAX;
+    else if (threadIdx.x < 6) out[threadIdx.x] = INT_MIN;
+}
+
 // ------------------------------------------------------------ host launchers
+template <typename T>
+void launch_cell_bounds(void* const u[3], int64_t n, int d, int* out, cudaStream_t s) {
+    k_cell_bounds<T><<<256, 256, 0, s>>>(static_cast<const T*>(u[0]), static_cast<const T*>(u[1]),
+                                         static_cast<const T*>(u[2]), n, d, out);
+}
+template void launch_cell_bounds<float>(void* const[3], int64_t, int, int*, cudaStream_t);
+template void launch_cell_bounds<double>(void* const[3], int64_t, int, int*, cudaStream_t);
+
 template <typename T>
 void launch_prepare_points(const double* x, int64_t n, int d, const double c[3], double scale, int n_os,
                            const int B[3], const int nb[3], int m, T* const u[3], int* key, int* count, int* status,

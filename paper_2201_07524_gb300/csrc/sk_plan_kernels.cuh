@@ -40,6 +40,9 @@ void launch_build_mult(T* M, int d, int h, const double* bk, double inv_norm, co
 template <typename T>
 void launch_twiddles(void* tw, int n, cudaStream_t s);
 
+__global__ void k_init_bounds(int* out);
+template <typename T>
+void launch_cell_bounds(void* const u[3], int64_t n, int d, int* out, cudaStream_t s);
 __global__ void k_fill(double* p, int64_t n, double v);
 __global__ void k_scale(double* p, int64_t n, double f);
 __global__ void k_gather(const double* in, const int* perm, int64_t n, double* out);

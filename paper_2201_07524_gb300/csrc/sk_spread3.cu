@@ -27,17 +27,27 @@
 
 namespace sk {
 
-template <int W> struct Col3 {
+template <int W, typename T = float> struct Col3 {
     static constexpr int BX = 4, BY = 4, BZ = 8;
     static constexpr int NCOL = BX * BY;
     static constexpr int SX = BX + W - 1, SY = BY + W - 1, SZ = BZ + W - 1;
     static constexpr int E = SZ;                       // z-cells of a column window
     static constexpr int ROWS = W * W;
     static constexpr int Q = (ROWS + 31) / 32;         // rows per lane
-    static constexpr int WZP = (W + 3) / 4 * 4;        // wz padded to whole 16-byte vectors
-    static constexpr int WZ = 0, WX = WZP, WY = WZP + W;
-    static constexpr int STRIDE = (WZP + 2 * W + 3) / 4 * 4;   // table entries per point
+    // Table row of a point: wz | wx | wy, each padded to whole 16-byte vectors.
+    static constexpr int VEC = 16 / int(sizeof(T));    // entries per 16-byte vector
+    static constexpr int WP = (W + VEC - 1) / VEC * VEC;
+    static constexpr int WZ = 0, WX = WP, WY = 2 * WP;
+    // an odd number of 16-byte vectors per row keeps the vector stores of 8
+    // consecutive lanes on distinct banks
+    static constexpr int NV = (3 * WP) / VEC;
+    static constexpr int STRIDE = (NV % 2 == 1 ? NV : NV + 1) * VEC;
     static constexpr int SUB = SX * SY * SZ;
+    // 16-byte-aligned z-chunks covering a column window: the window starts
+    // LEAD entries into the first chunk
+    static constexpr int ZA = (W / 2 - 1 + VEC - 1) / VEC * VEC;   // window start = z0 - (m-1) = z0 - ZA + LEAD
+    static constexpr int LEAD = ZA - (W / 2 - 1);
+    static constexpr int NCHUNK = (LEAD + E + VEC - 1) / VEC;
 };
 
 constexpr int kWarps = 8;
@@ -72,18 +82,52 @@ __device__ __forceinline__ void window_poly(T u, const WindowPoly& wp, T scale, 
     }
 }
 
-// Weights of point p into the warp's table row; returns the z-offset of its
-// cell inside the column.
+// Weights of a point at grid coordinates (u0, u1, u2) into the warp's table
+// row; returns the z-offset of its cell inside the column.
+template <typename T, int N>
+__device__ __forceinline__ void store_vec(T* dst, const T (&v)[N]) {
+    if (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < N; k += 4)
+            *reinterpret_cast<float4*>(dst + k) = make_float4(float(v[k]), k + 1 < N ? float(v[k + 1]) : 0.f,
+                                                              k + 2 < N ? float(v[k + 2]) : 0.f,
+                                                              k + 3 < N ? float(v[k + 3]) : 0.f);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k += 2)
+            *reinterpret_cast<double2*>(dst + k) = make_double2(double(v[k]), k + 1 < N ? double(v[k + 1]) : 0.0);
+    }
+}
+
 template <int W, typename T>
-__device__ __forceinline__ int fill_row(T* row, const T* c0, const T* c1, const T* c2, int p, T scale,
-                                        const WindowPoly& wp, int z0) {
-    using G = Col3<W>;
+__device__ __forceinline__ int fill_row(T* row, T u0, T u1, T u2, T scale, const WindowPoly& wp, int z0) {
+    using G = Col3<W, T>;
     int f0, f1, f2;
-    window_poly<W, T>(c0[p], wp, T(1), f0, row + G::WX);
-    window_poly<W, T>(c1[p], wp, T(1), f1, row + G::WY);
-    window_poly<W, T>(c2[p], wp, scale, f2, row + G::WZ);
+    T w[W];
+    window_poly<W, T>(u0, wp, T(1), f0, w);
+    store_vec<T, W>(row + G::WX, w);
+    window_poly<W, T>(u1, wp, T(1), f1, w);
+    store_vec<T, W>(row + G::WY, w);
+    window_poly<W, T>(u2, wp, scale, f2, w);
+    store_vec<T, W>(row + G::WZ, w);
     return f2 - z0;
 }
+
+// Coordinates (and weight) of the point a lane will evaluate next, loaded one
+// batch ahead so the global-load latency overlaps the current batch.
+template <typename T>
+struct Prefetch {
+    T u0, u1, u2;
+    double w;
+    __device__ __forceinline__ void load(const T* c0, const T* c1, const T* c2, const double* wv, int p, bool ok) {
+        if (ok) {
+            u0 = c0[p];
+            u1 = c1[p];
+            u2 = c2[p];
+            w = wv ? wv[p] : 1.0;
+        }
+    }
+};
 
 template <int W, typename T>
 __device__ __forceinline__ void load_wz(const T* row, T (&wz)[W]) {
@@ -142,12 +186,54 @@ __device__ __forceinline__ T dot_taps(const T (&win)[Q][E], const T (&a)[Q], con
     T r = T(0);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        T s = T(0);
+        T s0 = T(0), s1 = T(0);     // two independent chains
 #pragma unroll
-        for (int k = 0; k < W; ++k) s = fma(win[q][DZ0 + k], wz[k], s);
-        r = fma(a[q], s, r);
+        for (int k = 0; k < W; k += 2) {
+            s0 = fma(win[q][DZ0 + k], wz[k], s0);
+            if (k + 1 < W) s1 = fma(win[q][DZ0 + k + 1], wz[k + 1], s1);
+        }
+        r = fma(a[q], s0 + s1, r);
     }
     return r;
+}
+
+// The column window of a lane's rows from the grid, as 16-byte vectors: chunk
+// c of row q covers z = zc + VEC c ... zc + VEC c + VEC - 1 (zc is 16-byte
+// aligned); chunks outside [0, n) read as zero (n is a multiple of VEC).
+template <int W, typename T, int Q, int E>
+__device__ __forceinline__ void load_window(T (&win)[Q][E], const T* __restrict__ grid, int n, int gx0, int gy0,
+                                            int zc, const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]) {
+    using G = Col3<W, T>;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const T* grow = grid + (int64_t(gx0 + ri[q]) * n + (gy0 + rj[q])) * n;
+#pragma unroll
+        for (int c = 0; c < G::NCHUNK; ++c) {
+            const int z = zc + c * G::VEC;
+            T v[G::VEC];
+            if (rv[q] && z >= 0 && z < n) {
+                if (sizeof(T) == 4) {
+                    const float4 f = __ldg(reinterpret_cast<const float4*>(grow + z));
+                    v[0] = f.x;
+                    v[1 % G::VEC] = f.y;
+                    v[2 % G::VEC] = f.z;
+                    v[3 % G::VEC] = f.w;
+                } else {
+                    const double2 f = __ldg(reinterpret_cast<const double2*>(grow + z));
+                    v[0] = f.x;
+                    v[1 % G::VEC] = f.y;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < G::VEC; ++k) v[k] = T(0);
+            }
+#pragma unroll
+            for (int k = 0; k < G::VEC; ++k) {
+                const int e = c * G::VEC + k - G::LEAD;
+                if (e >= 0 && e < E) win[q][e] = v[k];
+            }
+        }
+    }
 }
 
 // Lanes owning a row (i, j) of the W x W column window: row lane + 32 q.
@@ -165,48 +251,78 @@ __device__ __forceinline__ void lane_rows(int lane, int (&ri)[Q], int (&rj)[Q], 
 template <int W, int Q, typename T>
 __device__ __forceinline__ void row_products(const T* row, const int (&ri)[Q], const int (&rj)[Q],
                                              const bool (&rv)[Q], T (&av)[Q]) {
-    using G = Col3<W>;
+    using G = Col3<W, T>;
+    if (32 % W == 0 && (W * W) % 32 == 0) {
+        // every row of a lane has the same j (row = lane + 32 q, 32 a multiple of W)
+        const T wy = row[G::WY + rj[0]];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) av[q] = rv[q] ? row[G::WX + ri[q]] * row[G::WY + rj[q]] : T(0);
+        for (int q = 0; q < Q; ++q) av[q] = row[G::WX + ri[0] + q * (32 / W)] * wy;
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) av[q] = rv[q] ? row[G::WX + ri[q]] * row[G::WY + rj[q]] : T(0);
+    }
 }
 
 template <int W, int Q, int E, int DZ0, typename T>
 __device__ __forceinline__ void spread_segment(T (&acc)[Q][E], const T* wt, int mydz, const int (&ri)[Q],
                                                const int (&rj)[Q], const bool (&rv)[Q]) {
-    using G = Col3<W>;
+    using G = Col3<W, T>;
     unsigned mask = __ballot_sync(0xffffffffu, mydz == DZ0);
+    // two points per step: both points' loads issue before either's FMAs
     while (mask) {
-        const int pp = __ffs(mask) - 1;
+        const int p0 = __ffs(mask) - 1;
         mask &= mask - 1;
-        const T* row = wt + pp * G::STRIDE;
-        T av[Q];
-        row_products<W, Q, T>(row, ri, rj, rv, av);
-        T wz[W];
-        load_wz<W, T>(row + G::WZ, wz);
-        add_taps<W, Q, E, DZ0, T>(acc, av, wz);
+        const T* r0 = wt + p0 * G::STRIDE;
+        T av0[Q], wz0[W];
+        row_products<W, Q, T>(r0, ri, rj, rv, av0);
+        load_wz<W, T>(r0 + G::WZ, wz0);
+        if (mask) {
+            const int p1 = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const T* r1 = wt + p1 * G::STRIDE;
+            T av1[Q], wz1[W];
+            row_products<W, Q, T>(r1, ri, rj, rv, av1);
+            load_wz<W, T>(r1 + G::WZ, wz1);
+            add_taps<W, Q, E, DZ0, T>(acc, av0, wz0);
+            add_taps<W, Q, E, DZ0, T>(acc, av1, wz1);
+        } else {
+            add_taps<W, Q, E, DZ0, T>(acc, av0, wz0);
+        }
     }
 }
 
 template <int W, int Q, int E, int DZ0, typename T>
 __device__ __forceinline__ void interp_segment(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
                                                const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]) {
-    using G = Col3<W>;
+    using G = Col3<W, T>;
     unsigned mask = __ballot_sync(0xffffffffu, mydz == DZ0);
     while (mask) {
-        const int pp = __ffs(mask) - 1;
+        const int p0 = __ffs(mask) - 1;
         mask &= mask - 1;
-        const T* row = wt + pp * G::STRIDE;
-        T av[Q];
-        row_products<W, Q, T>(row, ri, rj, rv, av);
-        T wz[W];
-        load_wz<W, T>(row + G::WZ, wz);
-        rd[pp * 33 + lane] = dot_taps<W, Q, E, DZ0, T>(win, av, wz);
+        const T* r0 = wt + p0 * G::STRIDE;
+        T av0[Q], wz0[W];
+        row_products<W, Q, T>(r0, ri, rj, rv, av0);
+        load_wz<W, T>(r0 + G::WZ, wz0);
+        if (mask) {
+            const int p1 = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const T* r1 = wt + p1 * G::STRIDE;
+            T av1[Q], wz1[W];
+            row_products<W, Q, T>(r1, ri, rj, rv, av1);
+            load_wz<W, T>(r1 + G::WZ, wz1);
+            const T d0 = dot_taps<W, Q, E, DZ0, T>(win, av0, wz0);
+            const T d1 = dot_taps<W, Q, E, DZ0, T>(win, av1, wz1);
+            rd[p0 * 33 + lane] = d0;
+            rd[p1 * 33 + lane] = d1;
+        } else {
+            rd[p0 * 33 + lane] = dot_taps<W, Q, E, DZ0, T>(win, av0, wz0);
+        }
     }
 }
 
 template <int W, typename T>
 __global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
-    using G = Col3<W>;
+    using G = Col3<W, T>;
     constexpr int Q = G::Q, E = G::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sub = reinterpret_cast<T*>(smem_raw);
@@ -240,12 +356,13 @@ __global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
             for (int q = 0; q < Q; ++q)
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc[q][e] = T(0);
+            Prefetch<T> pf;
+            pf.load(c0, c1, c2, a.w, start + lane, lane < end - start);
             for (int base = start; base < end; base += 32) {
                 const int cnt = min(32, end - base);
                 int mydz = -1;
-                if (lane < cnt)
-                    mydz = fill_row<W, T>(wt + lane * G::STRIDE, c0, c1, c2, base + lane, T(a.w[base + lane]),
-                                          a.wp, z0);
+                if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp, z0);
+                pf.load(c0, c1, c2, a.w, base + 32 + lane, base + 32 + lane < end);
                 __syncwarp();
                 spread_batch<W, Q, E, T>(acc, wt, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
                 __syncwarp();
@@ -280,20 +397,24 @@ __global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
 }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_interp3_col(InterpArgs a, Epilogue e) {
-    using G = Col3<W>;
+__global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e) {
+    using G = Col3<W, T>;
     constexpr int Q = G::Q, E = G::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* tab = reinterpret_cast<T*>(smem_raw);
     T* red = tab + kWarps * 32 * G::STRIDE;
     __shared__ int col_next;
+    __shared__ unsigned warps_done;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* wt = tab + warp * 32 * G::STRIDE;
     T* rd = red + warp * 32 * 33;
 
     const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
     const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
-    if (threadIdx.x == 0) col_next = col0 + kWarps;
+    if (threadIdx.x == 0) {
+        col_next = col0 + kWarps;
+        warps_done = 0u;
+    }
     __syncthreads();
     const T* c0 = static_cast<const T*>(a.coord[0]);
     const T* c1 = static_cast<const T*>(a.coord[1]);
@@ -304,7 +425,6 @@ __global__ void __launch_bounds__(256) k_interp3_col(InterpArgs a, Epilogue e) {
     bool rv[Q];
     lane_rows<W, Q>(lane, ri, rj, rv);
     const int z0 = bz * G::BZ;
-    const int gz0 = z0 - (W / 2 - 1);
     const int64_t kbase = int64_t(bin) * (G::NCOL * G::BZ);
     double sq = 0.0, bad = 0.0, dot = 0.0;
 
@@ -315,21 +435,19 @@ __global__ void __launch_bounds__(256) k_interp3_col(InterpArgs a, Epilogue e) {
         if (start < end) {
             const int cx = col / G::BY, cy = col % G::BY;
             T win[Q][E];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int gx = bx * G::BX + cx - (W / 2 - 1) + ri[q];
-                const int gy = by * G::BY + cy - (W / 2 - 1) + rj[q];
-                const T* grow = grid + (int64_t(gx) * n + gy) * n;
-#pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    const int gz = gz0 + k;
-                    win[q][k] = (rv[q] && gz >= 0 && gz < n) ? __ldg(grow + gz) : T(0);
-                }
-            }
+            load_window<W, T>(win, grid, n, bx * G::BX + cx - (W / 2 - 1), by * G::BY + cy - (W / 2 - 1),
+                              z0 - G::ZA, ri, rj, rv);
+            Prefetch<T> pf;
+            EpiPrefetch ep;
+            pf.load(c0, c1, c2, nullptr, start + lane, lane < end - start);
+            ep.load(e, start + lane, lane < end - start);
             for (int base = start; base < end; base += 32) {
                 const int cnt = min(32, end - base);
                 int mydz = -1;
-                if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, c0, c1, c2, base + lane, T(1), a.wp, z0);
+                if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, pf.u0, pf.u1, pf.u2, T(1), a.wp, z0);
+                const EpiPrefetch cur = ep;
+                pf.load(c0, c1, c2, nullptr, base + 32 + lane, base + 32 + lane < end);
+                ep.load(e, base + 32 + lane, base + 32 + lane < end);
                 __syncwarp();
                 interp_batch<W, Q, E, T>(win, wt, rd, lane, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
                 __syncwarp();
@@ -337,7 +455,7 @@ __global__ void __launch_bounds__(256) k_interp3_col(InterpArgs a, Epilogue e) {
                     T t = T(0);
 #pragma unroll 8
                     for (int l = 0; l < 32; ++l) t += rd[lane * 33 + l];
-                    epi_point(e, base + lane, double(t), sq, bad, dot);
+                    epi_point_pre(e, base + lane, double(t), cur.q, cur.a, sq, bad, dot);
                 }
                 __syncwarp();
             }
@@ -346,19 +464,19 @@ __global__ void __launch_bounds__(256) k_interp3_col(InterpArgs a, Epilogue e) {
         if (lane == 0) nxt = atomicAdd(&col_next, 1);
         col = __shfl_sync(0xffffffffu, nxt, 0);
     }
-    epi_finish(e, sq, bad, dot);
+    epi_finish_warps(e, sq, bad, dot, &warps_done);
 }
 
 // ------------------------------------------------------------------ dispatch
 template <int W, typename T>
 size_t spread3_smem() {
-    using G = Col3<W>;
+    using G = Col3<W, T>;
     return (size_t((G::SUB + 3) / 4 * 4) + size_t(kWarps) * 32 * G::STRIDE) * sizeof(T);
 }
 
 template <int W, typename T>
 size_t interp3_smem() {
-    using G = Col3<W>;
+    using G = Col3<W, T>;
     return (size_t(kWarps) * 32 * G::STRIDE + size_t(kWarps) * 32 * 33) * sizeof(T);
 }
 
