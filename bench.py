@@ -176,24 +176,41 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ GPU arm
 def algorithmic_counts(w, n_os):
-    """Algorithmic work per launch of each stage for one product over n points
-    (n = m here), as stated in the design notes:
-      spread / interp: 2 W^d flops per point (one multiply forming the tap weight,
-        one add into the grid or the sum), W = 2 m;
-      FFT (all passes of one product): 5 N' log2 N' flops per complex transform of
-        length N' = n_os, over the pencils the pruned pipeline transforms;
-      bytes: spread reads d coords (4 B) and one weight (8 B) per point and writes
-        the n_os^d grid once; interp reads the grid once, d coords, u, a and
-        writes u and t (FP64) per point."""
+    """Algorithmic work per launch of the two point stages of one product over
+    n points (n = m here), as stated in the design notes:
+      flops: 2 W^d per point (one multiply forming each tap weight, one add into
+        the grid or into the sum), W = 2 m;
+      bytes: spreading reads d FP32 coordinates and one FP64 weight per point
+        and writes the n_os^d FP32 grid once; interpolation reads the grid once
+        and, per point, d FP32 coordinates, u and a (FP64), and writes u."""
     d, W = w.d, 2 * w.m_w
     n = w.n
     taps = W ** d
-    f_spread = 2.0 * taps * n
-    f_interp = 2.0 * taps * n
     grid_bytes = 4.0 * n_os ** d
-    b_spread = n * (4 * d + 8) + grid_bytes
-    b_interp = grid_bytes + n * (4 * d + 8 * 3 + 8 * 2)
-    return {"spread": (f_spread, b_spread), "interp": (f_interp, b_interp)}
+    return {"spread": (2.0 * taps * n, n * (4 * d + 8) + grid_bytes),
+            "interp": (2.0 * taps * n, grid_bytes + n * (4 * d + 8 * 3))}
+
+
+def kernel_name(stage, w):
+    return "k_%s3_col<%d, float>" % (stage, 2 * w.m_w) if w.d == 3 else None
+
+
+def measured_traffic(kname):
+    """DRAM bytes per launch of `kname` from the committed ncu record, or None
+    when there is none or the kernel's sources changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kname)
+        if not rec:
+            return None
+        h = hashlib.sha1()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sha1"] else None
+    except Exception:
+        return None
 
 
 def fp32_alu_peak_tflops(pk):
@@ -360,8 +377,9 @@ def run_ours(args, rank, world):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+            "roofline": {"bound": "alu", "kernel": kernel_name(dominant, w) or dominant, "achieved": achieved,
+                         "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                         "traffic": measured_traffic(kernel_name(dominant, w)),
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s peaks file)"
                                         % (float(pk.get("sm_max_mhz", 2070.0)), pk_kind),
                          "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
