@@ -433,6 +433,46 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
     CK(cudaFreeAsync(suboff, P->ps));
 }
 
+// Near-field cell list of one cloud: cubic cells of side 1/nc >= eps_I / 2
+// over the unit torus (so all pairs closer than eps_I lie in the 5^d cells
+// around a point's own), the cloud in that order, and its non-empty cells.
+int near_cells_per_dim(const sk_plan* P) { return std::max(1, int(std::floor(2.0 / P->prm.eps_I))); }
+
+template <typename T>
+void build_near(sk_plan* P, Cloud& c) {
+    const int nc = near_cells_per_dim(P);
+    int ncells = 1;
+    for (int t = 0; t < P->d; ++t) ncells *= nc;
+    const int64_t n = c.n;
+    c.nf_start = static_cast<int*>(dalloc(P, size_t(ncells + 1) * sizeof(int)));
+    c.nf_idx = static_cast<int*>(dalloc(P, size_t(n) * sizeof(int)));
+    for (int t = 0; t < P->d; ++t) c.nf_coord[t] = dalloc(P, size_t(n) * sizeof(T));
+    c.nf_tasks = static_cast<int*>(dalloc(P, size_t(ncells) * sizeof(int)));
+    c.nf_corr = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
+    int *key = nullptr, *count = nullptr, *cursor = nullptr, *ntask = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&key), size_t(n) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&count), size_t(ncells) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&cursor), size_t(ncells) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&ntask), sizeof(int), P->ps));
+    CK(cudaMemsetAsync(count, 0, size_t(ncells) * sizeof(int), P->ps));
+    CK(cudaMemsetAsync(cursor, 0, size_t(ncells) * sizeof(int), P->ps));
+    CK(cudaMemsetAsync(ntask, 0, sizeof(int), P->ps));
+    launch_near_keys<T>(c.coord, n, P->d, double(nc) / P->n_os, nc, key, count, P->ps);
+    CK(cudaGetLastError());
+    scan_ints(P, count, c.nf_start, ncells);
+    launch_near_scatter(key, n, c.nf_start, cursor, c.nf_idx, P->ps);
+    CK(cudaGetLastError());
+    launch_near_gather<T>(c.nf_idx, n, P->d, c.coord, c.nf_coord, P->ps);
+    CK(cudaGetLastError());
+    launch_near_tasks(c.nf_start, ncells, c.nf_tasks, ntask, P->ps);
+    CK(cudaGetLastError());
+    c.nf_ntasks = read_int(P, ntask);
+    CK(cudaFreeAsync(key, P->ps));
+    CK(cudaFreeAsync(count, P->ps));
+    CK(cudaFreeAsync(cursor, P->ps));
+    CK(cudaFreeAsync(ntask, P->ps));
+}
+
 template <typename T>
 void build_tables(sk_plan* P) {
     const int d = P->d, N = P->N, h = P->h;
@@ -628,12 +668,37 @@ void product(sk_plan* P, Cloud& src, const double* w, Cloud& dst, const Epilogue
         stage_end(P, st);
         return;
     }
-    if (P->nearfield) throw Fail{SK_ERR_UNSUPPORTED};
+    Epilogue ee = e;
+    if (P->nearfield) {
+        // direct sums over pairs closer than eps_I, added to t in the epilogue
+        NearArgs na{};
+        for (int t = 0; t < 3; ++t) { na.t_coord[t] = dst.nf_coord[t]; na.s_coord[t] = src.nf_coord[t]; }
+        na.t_start = dst.nf_start;
+        na.t_idx = dst.nf_idx;
+        na.s_start = src.nf_start;
+        na.s_idx = src.nf_idx;
+        na.w = w;
+        na.tasks = dst.nf_tasks;
+        na.nc = near_cells_per_dim(P);
+        const double rg = P->n_os * P->prm.eps_I;
+        na.r2max = rg * rg;
+        na.inv_r2 = 1.0 / (rg * rg);
+        na.kcoef = 1.0 / (P->eps_s * std::pow(double(P->n_os), P->r));
+        na.r = P->r;
+        na.p = P->kp.p;
+        for (int q = 0; q < kMaxP; ++q) na.ki[q] = P->kp.ki[q];
+        na.out = dst.nf_corr;
+        const int st = stage_begin(P, SK_STAGE_NEAR);
+        CK(launch_nearfield<T>(P->d, na, dst.nf_ntasks, P->ps));
+        if (dst.nf_ntasks > 0) ++P->launches;
+        stage_end(P, st);
+        ee.add = dst.nf_corr;
+    }
     spread_into_grid<T>(P, src, w);
     int st = stage_begin(P, SK_STAGE_FFT);
     CK(launch_fft_convolve<T>(P->fft, P->ps, &P->launches));
     stage_end(P, st);
-    interp_from_grid<T>(P, dst, e);
+    interp_from_grid<T>(P, dst, ee);
 }
 
 template <typename T>
@@ -795,7 +860,7 @@ int sk_default_params(sk_nfft_params* prm) {
     prm->m_w = 4;
     prm->p = 8;
     prm->eps_B = 0.1;
-    prm->eps_I = 1.0 / 16.0;
+    prm->eps_I = 0.0;
     prm->precision = SK_FP32;
     prm->user_geometry = 0;
     prm->scale = 1.0;
@@ -838,7 +903,8 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
     int rc = validate_params(d, p, n_os, log2n);
     if (rc != SK_OK) return rc;
     const bool nearfield = !even_integer(r);
-    if (nearfield && !(p.eps_I > 0.0 && p.eps_I < 0.5 - p.eps_B)) return SK_ERR_ARG;
+    if (!(p.eps_I > 0.0)) p.eps_I = 16.0 / (3.0 * p.N);   // automatic near-field radius
+    if (nearfield && !(p.eps_I < 0.5 - p.eps_B)) return SK_ERR_ARG;
 
     sk_plan* P = new (std::nothrow) sk_plan();
     if (!P) return SK_ERR_NOMEM;
@@ -966,11 +1032,19 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         if (P->precision == SK_FP32) {
             build_cloud<float>(P, P->X, xs, as, n);
             build_cloud<float>(P, P->Y, ys, bs, m);
+            if (P->nearfield) {
+                build_near<float>(P, P->X);
+                build_near<float>(P, P->Y);
+            }
             build_tables<float>(P);
             build_grid<float>(P);
         } else {
             build_cloud<double>(P, P->X, xs, as, n);
             build_cloud<double>(P, P->Y, ys, bs, m);
+            if (P->nearfield) {
+                build_near<double>(P, P->X);
+                build_near<double>(P, P->Y);
+            }
             build_tables<double>(P);
             build_grid<double>(P);
         }

@@ -56,6 +56,13 @@ struct Cloud {
     int* bin_start = nullptr;   // CSR over bins, nbins + 1
     int* tasks = nullptr;       // column tasks (3-D)
     int ntasks = 0;
+    // near-field cell list (only when the kernel needs near-field correction)
+    int* nf_start = nullptr;    // CSR over near-field cells
+    int* nf_idx = nullptr;      // near-field position -> sorted index
+    void* nf_coord[3] = {nullptr, nullptr, nullptr};   // T*, coordinates in near-field order
+    int* nf_tasks = nullptr;    // non-empty near-field cells
+    int nf_ntasks = 0;
+    double* nf_corr = nullptr;  // correction of the last product into this cloud (sorted order)
     int* sub_start = nullptr;   // spreading subproblems
     int* sub_count = nullptr;
     int* sub_bin = nullptr;
@@ -73,6 +80,7 @@ struct Epilogue {
     double* t_store = nullptr;   // UPDATE / RESID: t_store[i] = t_i
     const double* marg = nullptr;
     double* scal = nullptr;      // UPDATE: scal[i] = marg[i] / t_i; RESID: read only
+    const double* add = nullptr; // if set, t_i += add[i] before anything else (near-field correction)
     double* partial = nullptr;   // 3 doubles per block
     unsigned* ticket = nullptr;  // zero between launches; the last block resets it
     double* result = nullptr;    // [0] sum (scal_old t - marg)^2, [1] bad count, [2] sum scal_old t
@@ -125,6 +133,25 @@ struct InterpArgs {
     WindowPoly wp;
 };
 
+struct NearArgs {
+    const void* t_coord[3];   // targets in near-field order (T, grid units)
+    const int* t_start;       // CSR over near-field cells of the targets
+    const int* t_idx;         // near-field position -> sorted target index
+    const void* s_coord[3];   // sources in near-field order
+    const int* s_start;
+    const int* s_idx;
+    const double* w;          // source weights in sorted order
+    const int* tasks;         // non-empty target cells
+    int nc;                   // near-field cells per dimension
+    double r2max;             // (n_os eps_I)^2: squared near-field radius in grid units
+    double inv_r2;            // 1 / r2max
+    double kcoef;             // K = exp(-kcoef |du|^r) with kcoef = 1 / (eps_s n_os^r)
+    double r;
+    int p;
+    double ki[kMaxP];         // K_I = sum_q ki[q] (|du|^2 / r2max)^q
+    double* out;              // correction per target, sorted order
+};
+
 struct DirectArgs {
     const void* tcoord[3];   // targets (sorted grid coordinates)
     int64_t nt;
@@ -167,6 +194,13 @@ template <typename T> cudaError_t launch_fft_adjoint(const FftPlan& f, double* f
                                                      int64_t* launches);
 template <typename T> cudaError_t launch_fft_forward(const FftPlan& f, const double* fhat, cudaStream_t s,
                                                      int64_t* launches);
+template <typename T> void launch_near_keys(void* const u[3], int64_t n, int d, double inv_cell, int nc, int* key,
+                                            int* count, cudaStream_t s);
+void launch_near_scatter(const int* key, int64_t n, const int* start, int* cursor, int* idx, cudaStream_t s);
+template <typename T> void launch_near_gather(const int* idx, int64_t n, int d, void* const u[3], void* const o[3],
+                                              cudaStream_t s);
+void launch_near_tasks(const int* start, int ncells, int* tasks, int* ntasks, cudaStream_t s);
+template <typename T> cudaError_t launch_nearfield(int d, const NearArgs& a, int ntasks, cudaStream_t s);
 template <typename T> cudaError_t launch_direct(int d, const DirectArgs& a, const Epilogue& e,
                                                 int64_t* launches, cudaStream_t s);
 template <typename T> int direct_blocks(int64_t nt);
@@ -224,6 +258,7 @@ __device__ __forceinline__ double div_newton(double a, double t) {
 // iteration).  RESID: sq, dot += u t, and t itself, for the final report.
 __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t,
                                           double& sq, double& bad, double& dot) {
+    if (e.add) t += e.add[i];
     if (e.mode == EPI_APPLY) {
         e.out[e.perm[i]] = t;
         return;
@@ -257,6 +292,7 @@ struct EpiPrefetch {
 // epi_point with the scaling value and marginal already loaded.
 __device__ __forceinline__ void epi_point_pre(const Epilogue& e, int64_t i, double t, double q, double a,
                                               double& sq, double& bad, double& dot) {
+    if (e.add) t += e.add[i];
     if (e.mode == EPI_APPLY) {
         e.out[e.perm[i]] = t;
         return;

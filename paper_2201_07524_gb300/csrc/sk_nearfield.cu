@@ -1,0 +1,224 @@
+// Near-field correction for kernels that are not smooth at y = 0 (r not an
+// even integer; Remark "Arithmetic complexity": r = 1 needs near-field
+// regularization).  The fast summation uses the regularized kernel K_R, which
+// equals the even polynomial K_I for rho < eps_I; adding
+//     t_i += sum_{j : |x_i - y_j| < eps_I} v_j (K(rho_ij) - K_I(rho_ij))
+// restores the exact kernel near 0.
+//
+// Both clouds carry a second cell list at plan time: cubic cells of side
+// eps_I / 2 over the unit torus, so every neighbour of a point lies in the 5^d
+// cells around its own.  One block takes one non-empty target cell; the
+// sources of the surrounding cells are staged through shared memory in tiles;
+// each thread owns up to kNearPerThread targets.  Partial sums are FP32 per
+// tile and FP64 across tiles.
+#include <type_traits>
+
+#include "sk_internal.cuh"
+
+namespace sk {
+
+constexpr int kNearTile = 512;   // sources staged per tile
+constexpr int kNearPerThread = 2;   // 512 target slots per block: a cell holds a few hundred
+constexpr int kNearThreads = 256;
+
+// Cell of each point in the near-field cell list (coordinates in grid units).
+template <typename T>
+__global__ void k_near_keys(const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2, int64_t n,
+                            int d, double inv_cell, int nc, int* __restrict__ key, int* __restrict__ count) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T* u[3] = {u0, u1, u2};
+    int k = 0;
+    for (int t = 0; t < d; ++t) {
+        int c = int(floor(double(u[t][i]) * inv_cell));
+        c = c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+        k = k * nc + c;
+    }
+    key[i] = k;
+    atomicAdd(&count[k], 1);
+}
+
+// Near-field order: idx[pos] = the point's index in the NFFT sort order, and
+// its coordinates copied into near-field order.
+template <typename T>
+__global__ void k_near_scatter(const int* __restrict__ key, int64_t n, const int* __restrict__ start,
+                               int* __restrict__ cursor, int* __restrict__ idx) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = key[i];
+    idx[start[k] + atomicAdd(&cursor[k], 1)] = int(i);
+}
+
+template <typename T>
+__global__ void k_near_gather(const int* __restrict__ idx, int64_t n, int d, const T* __restrict__ u0,
+                              const T* __restrict__ u1, const T* __restrict__ u2, T* __restrict__ o0,
+                              T* __restrict__ o1, T* __restrict__ o2) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = idx[i];
+    o0[i] = u0[p];
+    if (d > 1) o1[i] = u1[p];
+    if (d > 2) o2[i] = u2[p];
+}
+
+// Non-empty cells of the list (one block task each).
+__global__ void k_near_tasks(const int* __restrict__ start, int ncells, int* __restrict__ tasks,
+                             int* __restrict__ ntasks) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    if (start[c + 1] > start[c]) tasks[atomicAdd(ntasks, 1)] = c;
+}
+
+// Per-pair correction v (K(rho) - K_I(rho)) for |du|^2 = d2 < r2max (else 0).
+// Everything here is FP32 (or FP64 for FP64 plans); the parameters were
+// converted once per thread.  For r = 1 the distance is d2 * rsqrt(d2).
+template <typename T, bool R1, int NP>
+__device__ __forceinline__ T pair_term(T d2, T w, T r2max, T inv_r2, T kc, T half_r, const T (&ki)[kMaxP]) {
+    T rho_r;
+    if (R1) {
+        rho_r = d2 > T(0) ? d2 * rsqrt(d2) : T(0);
+    } else {
+        rho_r = pow(d2, half_r);
+    }
+    const T kv = exp2(-kc * rho_r);
+    const T s = d2 * inv_r2;
+    T kin = ki[NP - 1];
+#pragma unroll
+    for (int k = NP - 2; k >= 0; --k) kin = fma(kin, s, ki[k]);
+    return d2 < r2max ? w * (kv - kin) : T(0);
+}
+
+// NP: polynomial length of K_I (the plan's p; kMaxP covers every p with zero padding).
+template <int D, typename T, bool R1, int NP>
+__global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
+    using V = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+    __shared__ V src[kNearTile];   // (x, y, z, w) of the staged sources
+    const int cell = a.tasks[blockIdx.x];
+    int cc[3] = {0, 0, 0};
+    {
+        int rem = cell;
+        for (int t = D - 1; t >= 0; --t) { cc[t] = rem % a.nc; rem /= a.nc; }
+    }
+    const int ts = a.t_start[cell], te = a.t_start[cell + 1];
+    const T* tc[3] = {static_cast<const T*>(a.t_coord[0]), static_cast<const T*>(a.t_coord[1]),
+                      static_cast<const T*>(a.t_coord[2])};
+    const T* scd[3] = {static_cast<const T*>(a.s_coord[0]), static_cast<const T*>(a.s_coord[1]),
+                       static_cast<const T*>(a.s_coord[2])};
+    // parameters in the working precision, once
+    const T r2max = T(a.r2max), inv_r2 = T(a.inv_r2), half_r = T(0.5 * a.r);
+    const T kc = T(a.kcoef * 1.4426950408889634);    // exp(-x) = exp2(-x log2 e)
+    T ki[kMaxP];
+#pragma unroll
+    for (int k = 0; k < kMaxP; ++k) ki[k] = k < a.p ? T(a.ki[k]) : T(0);
+    int lo[3], hi[3];
+    for (int t = 0; t < 3; ++t) {
+        lo[t] = t < D ? max(0, cc[t] - 2) : 0;
+        hi[t] = t < D ? min(a.nc - 1, cc[t] + 2) : 0;
+    }
+    for (int tb = ts; tb < te; tb += kNearThreads * kNearPerThread) {
+        T xt[kNearPerThread][3];
+        double acc[kNearPerThread];
+#pragma unroll
+        for (int q = 0; q < kNearPerThread; ++q) {
+            const int i = tb + q * kNearThreads + threadIdx.x;
+            acc[q] = 0.0;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) xt[q][t] = (t < D && i < te) ? tc[t][i] : (t < D ? T(1e18) : T(0));
+        }
+        for (int c0 = lo[0]; c0 <= hi[0]; ++c0)
+            for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
+                for (int c2 = lo[2]; c2 <= hi[2]; ++c2) {
+                    int sc_id = c0;
+                    if (D > 1) sc_id = sc_id * a.nc + c1;
+                    if (D > 2) sc_id = sc_id * a.nc + c2;
+                    const int ss = a.s_start[sc_id], se = a.s_start[sc_id + 1];
+                    for (int s0 = ss; s0 < se; s0 += kNearTile) {
+                        const int cnt = min(kNearTile, se - s0);
+                        __syncthreads();
+                        for (int j = threadIdx.x; j < cnt; j += kNearThreads) {
+                            V v;
+                            v.x = scd[0][s0 + j];
+                            v.y = D > 1 ? scd[1][s0 + j] : T(0);
+                            v.z = D > 2 ? scd[2][s0 + j] : T(0);
+                            v.w = T(a.w[a.s_idx[s0 + j]]);
+                            src[j] = v;
+                        }
+                        __syncthreads();
+                        T part[kNearPerThread];
+#pragma unroll
+                        for (int q = 0; q < kNearPerThread; ++q) part[q] = T(0);
+#pragma unroll 2
+                        for (int j = 0; j < cnt; ++j) {
+                            const V s = src[j];
+#pragma unroll
+                            for (int q = 0; q < kNearPerThread; ++q) {
+                                const T dx = xt[q][0] - s.x, dy = xt[q][1] - s.y, dz = xt[q][2] - s.z;
+                                const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                                part[q] += pair_term<T, R1, NP>(d2, s.w, r2max, inv_r2, kc, half_r, ki);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < kNearPerThread; ++q) acc[q] += double(part[q]);
+                    }
+                }
+#pragma unroll
+        for (int q = 0; q < kNearPerThread; ++q) {
+            const int i = tb + q * kNearThreads + threadIdx.x;
+            if (i < te) a.out[a.t_idx[i]] = acc[q];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+void launch_near_keys(void* const u[3], int64_t n, int d, double inv_cell, int nc, int* key, int* count,
+                      cudaStream_t s) {
+    k_near_keys<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(static_cast<const T*>(u[0]), static_cast<const T*>(u[1]),
+                                                             static_cast<const T*>(u[2]), n, d, inv_cell, nc, key,
+                                                             count);
+}
+
+void launch_near_scatter(const int* key, int64_t n, const int* start, int* cursor, int* idx, cudaStream_t s) {
+    k_near_scatter<float><<<unsigned((n + 255) / 256), 256, 0, s>>>(key, n, start, cursor, idx);
+}
+
+template <typename T>
+void launch_near_gather(const int* idx, int64_t n, int d, void* const u[3], void* const o[3], cudaStream_t s) {
+    k_near_gather<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(
+        idx, n, d, static_cast<const T*>(u[0]), static_cast<const T*>(u[1]), static_cast<const T*>(u[2]),
+        static_cast<T*>(o[0]), static_cast<T*>(o[1]), static_cast<T*>(o[2]));
+}
+
+void launch_near_tasks(const int* start, int ncells, int* tasks, int* ntasks, cudaStream_t s) {
+    k_near_tasks<<<unsigned((ncells + 255) / 256), 256, 0, s>>>(start, ncells, tasks, ntasks);
+}
+
+template <typename T>
+cudaError_t launch_nearfield(int d, const NearArgs& a, int ntasks, cudaStream_t s) {
+    if (ntasks == 0) return cudaSuccess;
+    const bool r1 = a.r == 1.0;
+    const bool p8 = a.p == 8;
+#define SK_NF(DD, R, NP) k_nearfield<DD, T, R, NP><<<ntasks, kNearThreads, 0, s>>>(a)
+#define SK_NF_D(DD)                                  \
+    if (r1 && p8) SK_NF(DD, true, 8);                 \
+    else if (r1) SK_NF(DD, true, kMaxP);              \
+    else if (p8) SK_NF(DD, false, 8);                 \
+    else SK_NF(DD, false, kMaxP);
+    switch (d) {
+        case 1: SK_NF_D(1); break;
+        case 2: SK_NF_D(2); break;
+        default: SK_NF_D(3); break;
+    }
+#undef SK_NF_D
+#undef SK_NF
+    return cudaGetLastError();
+}
+
+template void launch_near_keys<float>(void* const[3], int64_t, int, double, int, int*, int*, cudaStream_t);
+template void launch_near_keys<double>(void* const[3], int64_t, int, double, int, int*, int*, cudaStream_t);
+template void launch_near_gather<float>(const int*, int64_t, int, void* const[3], void* const[3], cudaStream_t);
+template void launch_near_gather<double>(const int*, int64_t, int, void* const[3], void* const[3], cudaStream_t);
+template cudaError_t launch_nearfield<float>(int, const NearArgs&, int, cudaStream_t);
+template cudaError_t launch_nearfield<double>(int, const NearArgs&, int, cudaStream_t);
+
+}  // namespace sk

@@ -25,8 +25,9 @@ SK_ERR_TOO_LARGE = 10
 SK_FP32, SK_FP64 = 0, 1
 SK_METHOD_NFFT, SK_METHOD_DIRECT = 0, 1
 SK_SET_X, SK_SET_Y = 0, 1
-SK_STAGE_SPREAD, SK_STAGE_FFT, SK_STAGE_INTERP, SK_STAGE_OTHER, SK_STAGE_DIRECT, SK_NSTAGES = 0, 1, 2, 3, 4, 5
-STAGE_NAMES = ("spread", "fft", "interp", "other", "direct")
+SK_STAGE_SPREAD, SK_STAGE_FFT, SK_STAGE_INTERP, SK_STAGE_OTHER, SK_STAGE_DIRECT, SK_STAGE_NEAR = 0, 1, 2, 3, 4, 5
+SK_NSTAGES = 6
+STAGE_NAMES = ("spread", "fft", "interp", "other", "direct", "near")
 
 
 class sk_nfft_params(ctypes.Structure):

@@ -95,4 +95,4 @@ HEADLINE_3D = Workload("ball3d_n1e6_eps0.02_fp32", d=3, n=1_000_000, m=1_000_000
 GMM_2D = Workload("gmm2d_n1e6_eps0.01_fp32", d=2, n=1_000_000, m=1_000_000, eps=0.01, r=2.0,
                   iters=100, N=512, m_w=6, precision="fp32", source="gmm", weights="dirichlet")
 BALL3D_R1 = Workload("ball3d_n4e6_r1_eps0.02_fp32", d=3, n=4_000_000, m=4_000_000, eps=0.02,
-                     r=1.0, iters=100, N=128, m_w=4, precision="fp32")
+                     r=1.0, iters=100, N=128, m_w=4, precision="fp32", extra={"eps_I": 1.0 / 32})

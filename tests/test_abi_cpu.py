@@ -48,7 +48,7 @@ def test_default_params_and_error_strings():
     from paper_2201_07524_gb300 import sk
     p = sk.sk_default_params()
     assert (p.N, p.sigma, p.m_w, p.p, p.precision) == (64, 2.0, 4, 8, sk.SK_FP32)
-    assert p.eps_B == 0.1 and p.eps_I == 1.0 / 16
+    assert p.eps_B == 0.1 and p.eps_I == 0.0
     for code in range(10):
         assert sk.sk_error_string(code)
     assert sk.sk_error_string(999) == "unknown status"

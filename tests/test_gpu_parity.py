@@ -347,3 +347,65 @@ def test_full_size_solve_marginal_property():
         marg[k] = v[j] * np.dot(u, np.exp(-d2 / work.eps))
     np.testing.assert_allclose(marg, b[cols], rtol=1e-4)
     assert res["err_col"] < 1e-4 * np.linalg.norm(b)
+
+
+# --------------------------------------------------------- near field (r not an even integer)
+@pytest.mark.parametrize("d,N,r,eps,eps_I,precision", [
+    (1, 256, 1.0, 0.05, 0.0, sk.SK_FP64),
+    (2, 64, 1.0, 0.05, 0.0, sk.SK_FP64),
+    (2, 64, 1.0, 0.05, 0.0, sk.SK_FP32),
+    (2, 64, 1.5, 0.05, 0.0, sk.SK_FP32),
+    (3, 64, 1.0, 0.02, 0.0, sk.SK_FP32),
+    (3, 64, 1.0, 0.02, 1.0 / 8, sk.SK_FP64),
+])
+def test_nearfield_kernel_apply_matches_exact_sums(d, N, r, eps, eps_I, precision):
+    n, m = 1500, 1301
+    x = wl.uniform_ball(n, d, 0.2, 41)
+    y = wl.uniform_ball(m, d, 0.2, 42)
+    plan = plan_for(x, y, eps=eps, r=r, N=N, precision=precision, user_geometry=False, eps_I=eps_I)
+    assert sk.sk_plan_info(plan)["nearfield"] == 1
+    v = wl.positive_vector(m, 43)
+    u = wl.positive_vector(n, 44)
+    t = np.zeros(n)
+    tt = np.zeros(m)
+    sk.sk_kernel_apply(plan, 0, v, t)
+    sk.sk_kernel_apply(plan, 1, u, tt)
+    assert efs(t, osk.kernel_apply(x, y, v, eps, r)) <= TOL_FS[precision]
+    assert efs(tt, osk.kernel_apply_T(x, y, u, eps, r)) <= TOL_FS[precision]
+
+
+def test_nearfield_solve_matches_dense_oracle():
+    d, n, m, eps, iters = 2, 1200, 1000, 0.05, 30
+    x = wl.uniform_ball(n, d, 0.2, 45)
+    y = wl.uniform_ball(m, d, 0.2, 46)
+    a, b = wl.dirichlet_weights(n, 47), wl.dirichlet_weights(m, 48)
+    ref = osk.sinkhorn_dense(x, a, y, b, eps, 1.0, iters)
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), eps, 1.0, sk.sk_default_params(precision=sk.SK_FP64))
+    st, res = sk.sk_solve(plan, iters)
+    assert st == sk.SK_OK
+    assert abs(res["s"] - ref["s"]) / abs(ref["s"]) <= 1e-5
+
+
+def test_nearfield_stage_timing_counts():
+    x = wl.uniform_ball(2000, 3, 0.2, 49)
+    y = wl.uniform_ball(2000, 3, 0.2, 50)
+    plan = plan_for(x, y, r=1.0, eps=0.02, precision=sk.SK_FP32, user_geometry=False)
+    sk.sk_stage_times(plan, 1)
+    sk.sk_solve(plan, 2, result=False)
+    times = sk.sk_stage_times(plan, 0)
+    assert times["near"][1] == 4 and times["near"][0] > 0
+
+
+def test_full_size_r1_kernel_apply_sampled_rows():
+    work = wl.BALL3D_R1
+    x, y = work.points()
+    a, b = work.marginals()
+    prm = sk.sk_default_params(N=work.N, m_w=work.m_w, precision=sk.SK_FP32, eps_I=work.extra["eps_I"])
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), work.eps, work.r, prm)
+    v = wl.positive_vector(work.m, 51)
+    t = torch.zeros(work.n, dtype=torch.float64, device=DEV)
+    sk.sk_kernel_apply(plan, 0, cuda(v), t)
+    rows = np.random.default_rng(52).choice(work.n, 24, replace=False)
+    exact = _sampled_rows(x, y, v, work.eps, work.r, rows)
+    got = t.cpu().numpy()[rows]
+    assert np.max(np.abs(got - exact)) / np.max(np.abs(exact)) <= 1e-5
