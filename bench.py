@@ -213,6 +213,30 @@ def measured_traffic(kname):
         return None
 
 
+def reduce_max_ms(ms, world, device="cpu"):
+    """The timed region's length as the maximum over ranks (ranks run
+    independent problems; the job ends when the slowest rank does)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ms_max, steps, world):
+    """Iterations per second of the whole job: every rank ran `steps`
+    iterations of its own problem within ms_max milliseconds."""
+    return world * steps / (ms_max / 1e3)
+
+
+def replica_workload(w, rank):
+    """Rank r solves its own problem: the same workload with seeds shifted by 1000 r."""
+    from paper_2201_07524_gb300 import workloads as wl
+    return wl.Workload(w.name, w.d, w.n, w.m, w.eps, w.r, w.iters, w.N, w.m_w, w.sigma, w.precision,
+                       seed_x=w.seed_x + 1000 * rank, seed_y=w.seed_y + 1000 * rank)
+
+
 def fp32_alu_peak_tflops(pk):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
     mhz = float(pk.get("sm_max_mhz", 2070.0))
@@ -229,10 +253,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    w = wl.HEADLINE_3D
     # each rank solves its own independent problem (replicas; seeds offset by rank)
-    w = wl.Workload(w.name, w.d, w.n, w.m, w.eps, w.r, w.iters, w.N, w.m_w, w.sigma, w.precision,
-                    seed_x=w.seed_x + 1000 * rank, seed_y=w.seed_y + 1000 * rank)
+    w = replica_workload(wl.HEADLINE_3D, rank)
     x, y = w.points()
     a, b = w.marginals()
     T = lambda z: torch.as_tensor(z, dtype=torch.float64, device=dev)
@@ -269,11 +291,8 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     launches = sk.sk_launch_count(plan) - launches0
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = reduce_max_ms(ms, world, dev)
+    value = whole_job_rate(ms_max, args.steps, world)
 
     # per-stage times over the same number of steps (instrumented pass, no graph replay)
     sk.sk_stage_times(plan, 1)

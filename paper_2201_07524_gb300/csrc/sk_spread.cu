@@ -73,7 +73,15 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
     const T* c0 = static_cast<const T*>(a.coord[0]);
     const T* c1 = static_cast<const T*>(a.coord[1]);
     const T* c2 = static_cast<const T*>(a.coord[2]);
-    for (int p = start + threadIdx.x; p < start + cnt; p += blockDim.x) {
+    // Points of a bin are sorted by cell, so neighbouring points share taps.
+    // Interleave: slot q (lane q % 32 of group q / 32) takes point
+    // (q % 32) * G + q / 32, so the 32 lanes of a warp add into cells far apart
+    // instead of serializing on the same shared-memory addresses.
+    const int G = (cnt + 31) / 32;
+    for (int q = threadIdx.x; q < 32 * G; q += blockDim.x) {
+        const int qi = (q & 31) * G + (q >> 5);
+        if (qi >= cnt) continue;
+        const int p = start + qi;
         const T val = T(a.w[p]);
         T w0[W], w1[W], w2[W];
         int f0 = 0, f1 = 0, f2 = 0;
