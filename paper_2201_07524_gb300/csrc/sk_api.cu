@@ -422,6 +422,29 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
             for (int k = 0; k < 3; ++k) sorted[3 * i + k] = tk[3 * order[i] + k];
         CK(cudaMemcpyAsync(c.tasks, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
         CK(cudaStreamSynchronize(P->ps));
+
+        // the interpolation's column queue: every non-empty (bin, column)
+        // pair, most points first, so the warps that take the last entries
+        // take short ones
+        const int64_t npairs = int64_t(P->nbins) * ncol;
+        int* cnt_d = nullptr;
+        CK(cudaMallocAsync(reinterpret_cast<void**>(&cnt_d), size_t(npairs) * sizeof(int), P->ps));
+        k_col_counts<<<unsigned((npairs + 255) / 256), 256, 0, P->ps>>>(c.key_start, P->nbins, P->bvol, ncol,
+                                                                        P->B[2], cnt_d);
+        CK(cudaGetLastError());
+        std::vector<int> cnt(static_cast<size_t>(npairs));
+        CK(cudaMemcpyAsync(cnt.data(), cnt_d, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+        CK(cudaFreeAsync(cnt_d, P->ps));
+        std::vector<int> cols;
+        for (int64_t i = 0; i < npairs; ++i)
+            if (cnt[i] > 0) cols.push_back(int(i));
+        std::stable_sort(cols.begin(), cols.end(), [&](int p, int q) { return cnt[p] > cnt[q]; });
+        c.ncols = int(cols.size());
+        c.cols = static_cast<int*>(dalloc(P, size_t(std::max(c.ncols, 1)) * sizeof(int)));
+        if (c.ncols > 0)
+            CK(cudaMemcpyAsync(c.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
     }
     k_fill<<<nblk(n), 256, 0, P->ps>>>(c.scal, n, 1.0);
     CK(cudaGetLastError());
@@ -585,7 +608,7 @@ void prepare_kernels(sk_plan* P) {
     CK(launch_spread<T>(P->d, P->W, a, P->ps));
     if (column_kernels(P->d, P->W)) {
         InterpArgs ia{};
-        ia.ntasks = 0;
+        ia.ncols = 0;
         CK(launch_interp3<T>(P->W, ia, Epilogue{}, P->ps));
     }
     CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
@@ -645,6 +668,9 @@ void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
     a.n_os = P->n_os;
     a.beta = P->beta;
     a.knorm = P->knorm;
+    a.cols = dst.cols;
+    a.ncols = dst.ncols;
+    a.queue = P->ticket + 2;
     a.grid = P->fft.grid_out;
     a.wp = P->wp;
     int st = stage_begin(P, SK_STAGE_INTERP);
@@ -945,7 +971,7 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         const int64_t nmax = std::max(n, m);
         P->partial_blocks = std::max<int64_t>(interp_blocks<double>(nmax), kRedBlocks);
         P->partial = static_cast<double*>(dalloc(P, size_t(P->partial_blocks) * 8 * sizeof(double)));
-        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 4));
+        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 4));   // [0] reductions, [2..3] column queue
         P->stats = static_cast<double*>(dalloc(P, sizeof(double) * (3 * NSLOTS + 8)));
         P->status = static_cast<int*>(dalloc(P, sizeof(int) * 4));
         CK(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned) * 4, P->ps));
@@ -1049,18 +1075,23 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
             build_grid<double>(P);
         }
         for (void* t : tmps) CK(cudaFreeAsync(t, P->ps));
-        // the column kernels reduce one partial per task
-        const int need = std::max(P->X.ntasks, P->Y.ntasks);
-        if (need > P->partial_blocks) {
-            P->partial_blocks = need;
-            P->partial = static_cast<double*>(dalloc(P, size_t(need) * 8 * sizeof(double)));
-        }
         // opt the kernels this plan uses into their shared-memory sizes now, so
         // no attribute call happens while an iteration is being captured
         if (P->precision == SK_FP32)
             prepare_kernels<float>(P);
         else
             prepare_kernels<double>(P);
+        // the column kernels reduce one partial per block
+        if (column_kernels(P->d, P->W)) {
+            const int ncols = std::max(P->X.ncols, P->Y.ncols);
+            const int need = std::max(std::max(P->X.ntasks, P->Y.ntasks),
+                                      P->precision == SK_FP32 ? interp3_blocks<float>(P->W, ncols)
+                                                              : interp3_blocks<double>(P->W, ncols));
+            if (need > P->partial_blocks) {
+                P->partial_blocks = need;
+                P->partial = static_cast<double*>(dalloc(P, size_t(need) * 8 * sizeof(double)));
+            }
+        }
         const int st = read_status(P);
         if (st & 2) throw Fail{SK_ERR_DOMAIN};
         leave(P, stream);

@@ -56,6 +56,8 @@ struct Cloud {
     int* bin_start = nullptr;   // CSR over bins, nbins + 1
     int* tasks = nullptr;       // column tasks (3-D)
     int ntasks = 0;
+    int* cols = nullptr;        // non-empty (bin, column) pairs, bin * columns + column, most points first (3-D)
+    int ncols = 0;
     // near-field cell list (only when the kernel needs near-field correction)
     int* nf_start = nullptr;    // CSR over near-field cells
     int* nf_idx = nullptr;      // near-field position -> sorted index
@@ -126,6 +128,9 @@ struct InterpArgs {
     const int* key_start;
     const int* tasks;
     int ntasks;
+    const int* cols;       // 3-D column queue: (bin, column) codes, most points first
+    int ncols;
+    unsigned* queue;       // [0] next queue entry, [1] warps finished; zero between launches
     int nb[3];
     int n_os;
     double beta, knorm;
@@ -187,6 +192,7 @@ template <typename T> cudaError_t launch_interp(int d, int W, const InterpArgs& 
 template <typename T> int interp_blocks(int64_t n);
 template <typename T> cudaError_t launch_spread3(int W, const SpreadArgs& a, cudaStream_t s);
 template <typename T> cudaError_t launch_interp3(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s);
+template <typename T> int interp3_blocks(int W, int ncols);
 bool column_kernels(int d, int W);
 void bin_shape(int d, int W, int B[3]);
 template <typename T> cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches);

@@ -300,6 +300,16 @@ __global__ void k_fill_tasks(const int* __restrict__ ntask_off, int nbins, int n
     }
 }
 
+// Points in each (bin, column) pair of the 3-D column kernels: a column is the
+// bz cells of one (x, y) cell position inside a bin, consecutive sort keys.
+__global__ void k_col_counts(const int* __restrict__ key_start, int nbins, int bvol, int ncol, int bz,
+                             int* __restrict__ count) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(nbins) * ncol) return;
+    const int64_t k0 = (i / ncol) * bvol + (i % ncol) * bz;
+    count[i] = key_start[k0 + bz] - key_start[k0];
+}
+
 // ------------------------------------------------------------ coefficient table
 // K_R(l/N) for l in {-N/2..N/2-1}^d, stored at index l + N/2 per dimension.
 __global__ void k_sample_kernel(double* __restrict__ out, int N, int d, KernelParams kp) {

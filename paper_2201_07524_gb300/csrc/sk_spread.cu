@@ -265,7 +265,7 @@ template <typename T>
 cudaError_t launch_interp(int d, int W, const InterpArgs& a, const Epilogue& e, int64_t* launches,
                           cudaStream_t s) {
     if (column_kernels(d, W)) {
-        if (launches && a.ntasks > 0) ++*launches;
+        if (launches && a.ncols > 0) ++*launches;
         return launch_interp3<T>(W, a, e, s);
     }
     switch (d) {

@@ -21,6 +21,7 @@
 //   * interpolation loads the column's window from the grid once, reduces each
 //     point's 32 lane partials through shared memory, and runs the FP64
 //     epilogue with one lane per point.
+#include <algorithm>
 #include <utility>
 
 #include "sk_internal.cuh"
@@ -51,6 +52,9 @@ template <int W, typename T = float> struct Col3 {
 };
 
 constexpr int kWarps = 8;
+// Row stride of the per-warp table of lane partials (a multiple of 4 floats, so
+// a point's row is read with 16-byte loads; 36 keeps those loads conflict-free).
+constexpr int kRedStride = 36;
 
 template <typename T> struct PolyDeg;
 template <> struct PolyDeg<float> { static constexpr int D = kPolyDeg32; };
@@ -312,10 +316,10 @@ __device__ __forceinline__ void interp_segment(const T (&win)[Q][E], const T* wt
             load_wz<W, T>(r1 + G::WZ, wz1);
             const T d0 = dot_taps<W, Q, E, DZ0, T>(win, av0, wz0);
             const T d1 = dot_taps<W, Q, E, DZ0, T>(win, av1, wz1);
-            rd[p0 * 33 + lane] = d0;
-            rd[p1 * 33 + lane] = d1;
+            rd[p0 * kRedStride + lane] = d0;
+            rd[p1 * kRedStride + lane] = d1;
         } else {
-            rd[p0 * 33 + lane] = dot_taps<W, Q, E, DZ0, T>(win, av0, wz0);
+            rd[p0 * kRedStride + lane] = dot_taps<W, Q, E, DZ0, T>(win, av0, wz0);
         }
     }
 }
@@ -396,6 +400,55 @@ __global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
     }
 }
 
+// Next entry of the interpolation's column queue for this warp (lane 0 takes
+// it; every lane gets it).
+__device__ __forceinline__ int queue_take(unsigned* q, int lane) {
+    unsigned c = 0u;
+    if (lane == 0) c = atomicAdd(q, 1u);
+    return int(__shfl_sync(0xffffffffu, c, 0));
+}
+
+// A warp that has left the queue loop signs off; the last warp of the grid
+// resets the queue for the next launch (every other warp has already taken
+// its last entry, which precedes its sign-off).
+__device__ __forceinline__ void queue_leave(unsigned* q, int lane) {
+    if (lane == 0) {
+        __threadfence();
+        const unsigned total = gridDim.x * (blockDim.x >> 5);
+        if (atomicAdd(q + 1, 1u) == total - 1u) {
+            q[0] = 0u;
+            q[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// A queue entry: the column's points [start, end) and its cell offsets.
+struct ColumnRef {
+    int start = 0, end = 0, gx0 = 0, gy0 = 0, z0 = 0;
+};
+
+template <int W, typename T>
+__device__ __forceinline__ ColumnRef column_ref(const InterpArgs& a, int c) {
+    using G = Col3<W, T>;
+    ColumnRef r;
+    if (c >= a.ncols) return r;
+    const int code = a.cols[c];
+    const int bin = code / G::NCOL, col = code % G::NCOL;
+    const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
+    const int64_t k0 = int64_t(bin) * (G::NCOL * G::BZ) + col * G::BZ;
+    r.start = a.key_start[k0];
+    r.end = a.key_start[k0 + G::BZ];
+    r.gx0 = bx * G::BX + col / G::BY - (W / 2 - 1);
+    r.gy0 = by * G::BY + col % G::BY - (W / 2 - 1);
+    r.z0 = bz * G::BZ;
+    return r;
+}
+
+// Interpolation with a persistent grid: each warp takes columns from a global
+// queue (most points first), so the load balances at column granularity
+// whatever the number of bins.  The next entry is taken, and its first batch
+// of coordinates requested, while the current column is processed.
 template <int W, typename T>
 __global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e) {
     using G = Col3<W, T>;
@@ -403,18 +456,12 @@ __global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* tab = reinterpret_cast<T*>(smem_raw);
     T* red = tab + kWarps * 32 * G::STRIDE;
-    __shared__ int col_next;
     __shared__ unsigned warps_done;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* wt = tab + warp * 32 * G::STRIDE;
-    T* rd = red + warp * 32 * 33;
+    T* rd = red + warp * 32 * kRedStride;
 
-    const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
-    const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
-    if (threadIdx.x == 0) {
-        col_next = col0 + kWarps;
-        warps_done = 0u;
-    }
+    if (threadIdx.x == 0) warps_done = 0u;
     __syncthreads();
     const T* c0 = static_cast<const T*>(a.coord[0]);
     const T* c1 = static_cast<const T*>(a.coord[1]);
@@ -424,46 +471,60 @@ __global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e
     int ri[Q], rj[Q];
     bool rv[Q];
     lane_rows<W, Q>(lane, ri, rj, rv);
-    const int z0 = bz * G::BZ;
-    const int64_t kbase = int64_t(bin) * (G::NCOL * G::BZ);
     double sq = 0.0, bad = 0.0, dot = 0.0;
 
-    int col = col0 + warp;
-    while (col < col1) {
-        const int start = a.key_start[kbase + col * G::BZ];
-        const int end = a.key_start[kbase + (col + 1) * G::BZ];
-        if (start < end) {
-            const int cx = col / G::BY, cy = col % G::BY;
-            T win[Q][E];
-            load_window<W, T>(win, grid, n, bx * G::BX + cx - (W / 2 - 1), by * G::BY + cy - (W / 2 - 1),
-                              z0 - G::ZA, ri, rj, rv);
-            Prefetch<T> pf;
-            EpiPrefetch ep;
-            pf.load(c0, c1, c2, nullptr, start + lane, lane < end - start);
-            ep.load(e, start + lane, lane < end - start);
-            for (int base = start; base < end; base += 32) {
-                const int cnt = min(32, end - base);
-                int mydz = -1;
-                if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, pf.u0, pf.u1, pf.u2, T(1), a.wp, z0);
-                const EpiPrefetch cur = ep;
-                pf.load(c0, c1, c2, nullptr, base + 32 + lane, base + 32 + lane < end);
-                ep.load(e, base + 32 + lane, base + 32 + lane < end);
-                __syncwarp();
-                interp_batch<W, Q, E, T>(win, wt, rd, lane, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
-                __syncwarp();
-                if (lane < cnt) {
+    int c = queue_take(a.queue, lane);
+    ColumnRef cur = column_ref<W, T>(a, c);
+    Prefetch<T> pf;
+    EpiPrefetch ep;
+    pf.load(c0, c1, c2, nullptr, cur.start + lane, lane < cur.end - cur.start);
+    ep.load(e, cur.start + lane, lane < cur.end - cur.start);
+    while (c < a.ncols) {
+        const int cn = queue_take(a.queue, lane);
+        const ColumnRef nxt = column_ref<W, T>(a, cn);
+        T win[Q][E];
+        load_window<W, T>(win, grid, n, cur.gx0, cur.gy0, cur.z0 - G::ZA, ri, rj, rv);
+        for (int base = cur.start; base < cur.end; base += 32) {
+            const int cnt = min(32, cur.end - base);
+            int mydz = -1;
+            if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, pf.u0, pf.u1, pf.u2, T(1), a.wp, cur.z0);
+            const EpiPrefetch epc = ep;
+            // the next batch: this column's, else the next column's first
+            const bool more = base + 32 < cur.end;
+            const int nb = more ? base + 32 : nxt.start;
+            const int ne = more ? cur.end : nxt.end;
+            pf.load(c0, c1, c2, nullptr, nb + lane, nb + lane < ne);
+            ep.load(e, nb + lane, nb + lane < ne);
+            __syncwarp();
+            interp_batch<W, Q, E, T>(win, wt, rd, lane, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
+            __syncwarp();
+            if (lane < cnt) {
+                // the point's 32 lane partials, four at a time
+                if constexpr (sizeof(T) == 4) {
+                    const float4* row = reinterpret_cast<const float4*>(rd + lane * kRedStride);
+                    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) {
+                        const float4 v = row[l];
+                        t0 += v.x;
+                        t1 += v.y;
+                        t2 += v.z;
+                        t3 += v.w;
+                    }
+                    epi_point_pre(e, base + lane, double((t0 + t1) + (t2 + t3)), epc.q, epc.a, sq, bad, dot);
+                } else {
                     T t = T(0);
 #pragma unroll 8
-                    for (int l = 0; l < 32; ++l) t += rd[lane * 33 + l];
-                    epi_point_pre(e, base + lane, double(t), cur.q, cur.a, sq, bad, dot);
+                    for (int l = 0; l < 32; ++l) t += rd[lane * kRedStride + l];
+                    epi_point_pre(e, base + lane, double(t), epc.q, epc.a, sq, bad, dot);
                 }
-                __syncwarp();
             }
+            __syncwarp();
         }
-        int nxt = 0;
-        if (lane == 0) nxt = atomicAdd(&col_next, 1);
-        col = __shfl_sync(0xffffffffu, nxt, 0);
+        c = cn;
+        cur = nxt;
     }
+    queue_leave(a.queue, lane);
     epi_finish_warps(e, sq, bad, dot, &warps_done);
 }
 
@@ -477,7 +538,7 @@ size_t spread3_smem() {
 template <int W, typename T>
 size_t interp3_smem() {
     using G = Col3<W, T>;
-    return (size_t(kWarps) * 32 * G::STRIDE + size_t(kWarps) * 32 * 33) * sizeof(T);
+    return (size_t(kWarps) * 32 * G::STRIDE + size_t(kWarps) * 32 * kRedStride) * sizeof(T);
 }
 
 template <auto K>
@@ -502,13 +563,38 @@ static cudaError_t spread3_one(const SpreadArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Blocks of the persistent interpolation grid: as many as fit on the GPU at
+// once, but no more than the queue can keep busy.
+template <int W, typename T>
+static int interp3_grid(int ncols) {
+    static int resident[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& r = resident[dev & 63];
+    if (r == 0) {
+        int per_sm = 0, sms = 0;
+        if (opt_in<k_interp3_col<W, T>>(interp3_smem<W, T>()) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp3_col<W, T>, 256, interp3_smem<W, T>()) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        r = std::max(1, per_sm) * sms;
+    }
+    return std::max(1, std::min(r, (ncols + kWarps - 1) / kWarps));
+}
+
 template <int W, typename T>
 static cudaError_t interp3_one(const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
     const size_t bytes = interp3_smem<W, T>();
     cudaError_t err = opt_in<k_interp3_col<W, T>>(bytes);
     if (err != cudaSuccess) return err;
-    if (a.ntasks == 0) return cudaSuccess;
-    k_interp3_col<W, T><<<a.ntasks, 256, bytes, s>>>(a, e);
+    const int blocks = interp3_grid<W, T>(a.ncols);
+    if (blocks == 0) {
+        const cudaError_t last = cudaGetLastError();
+        return last != cudaSuccess ? last : cudaErrorInvalidValue;
+    }
+    if (a.ncols == 0) return cudaSuccess;
+    k_interp3_col<W, T><<<blocks, 256, bytes, s>>>(a, e);
     return cudaGetLastError();
 }
 
@@ -536,6 +622,19 @@ cudaError_t launch_interp3(int W, const InterpArgs& a, const Epilogue& e, cudaSt
     }
 }
 
+template <typename T>
+int interp3_blocks(int W, int ncols) {
+    switch (W) {
+        case 4: return interp3_grid<4, T>(ncols);
+        case 6: return interp3_grid<6, T>(ncols);
+        case 8: return interp3_grid<8, T>(ncols);
+        case 10: return interp3_grid<10, T>(ncols);
+        default: return 0;
+    }
+}
+
+template int interp3_blocks<float>(int, int);
+template int interp3_blocks<double>(int, int);
 template cudaError_t launch_spread3<float>(int, const SpreadArgs&, cudaStream_t);
 template cudaError_t launch_spread3<double>(int, const SpreadArgs&, cudaStream_t);
 template cudaError_t launch_interp3<float>(int, const InterpArgs&, const Epilogue&, cudaStream_t);
