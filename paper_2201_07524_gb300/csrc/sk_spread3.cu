@@ -8,18 +8,20 @@
 // window, so a warp keeps the column's whole window -- W^2 rows by (8 + W - 1)
 // z-cells -- in registers, two rows per lane for W = 8:
 //
-//   * one lane per point evaluates that point's 3W window weights and writes
-//     them to a per-warp table in shared memory;
-//   * for each point, every lane forms wx[i] wy[j] for its rows and adds
-//     (or, when interpolating, gathers) the W z-taps with plain FMAs; the
-//     points of a batch are sorted by their z-offset inside the column, so the
-//     batch is walked in segments of equal offset (found with a warp ballot)
-//     and the register indices are compile-time constants in each segment;
+//   * each batch of 32 points is first ordered by the z-offset of the points'
+//     cells inside the column (warp ballots), then one lane per point
+//     evaluates that point's 3W window weights into its row of a per-warp
+//     table in shared memory, so the points of equal offset are consecutive
+//     rows and every segment of equal offset has compile-time register
+//     indices;
+//   * for each point, every lane scales its rows by the x (and y) weights and
+//     adds (or, when interpolating, gathers) the W z-taps with plain FMAs;
 //   * spreading flushes a finished column into the bin's shared-memory
 //     sub-grid with shared-memory atomics (one per register, not one per tap),
 //     and the block adds the sub-grid to the global grid once;
-//   * interpolation loads the column's window from the grid once, reduces each
-//     point's 32 lane partials through shared memory, and runs the FP64
+//   * interpolation runs a persistent grid whose warps take columns from a
+//     global queue, loads each column's window from the grid once, reduces
+//     each point's 32 lane partials through shared memory, and runs the FP64
 //     epilogue with one lane per point.
 #include <algorithm>
 #include <utility>
@@ -51,7 +53,8 @@ template <int W, typename T = float> struct Col3 {
     static constexpr int NCHUNK = (LEAD + E + VEC - 1) / VEC;
 };
 
-constexpr int kWarps = 8;
+constexpr int kWarps = 8;         // warps per interpolation block
+constexpr int kSpreadWarps = 8;   // warps per spreading block (one block per bin task)
 // Row stride of the per-warp table of lane partials (a multiple of 4 floats, so
 // a point's row is read with 16-byte loads; 36 keeps those loads conflict-free).
 constexpr int kRedStride = 36;
@@ -86,8 +89,7 @@ __device__ __forceinline__ void window_poly(T u, const WindowPoly& wp, T scale, 
     }
 }
 
-// Weights of a point at grid coordinates (u0, u1, u2) into the warp's table
-// row; returns the z-offset of its cell inside the column.
+// N values to 16-byte aligned shared memory with vector stores.
 template <typename T, int N>
 __device__ __forceinline__ void store_vec(T* dst, const T (&v)[N]) {
     if (sizeof(T) == 4) {
@@ -101,20 +103,6 @@ __device__ __forceinline__ void store_vec(T* dst, const T (&v)[N]) {
         for (int k = 0; k < N; k += 2)
             *reinterpret_cast<double2*>(dst + k) = make_double2(double(v[k]), k + 1 < N ? double(v[k + 1]) : 0.0);
     }
-}
-
-template <int W, typename T>
-__device__ __forceinline__ int fill_row(T* row, T u0, T u1, T u2, T scale, const WindowPoly& wp, int z0) {
-    using G = Col3<W, T>;
-    int f0, f1, f2;
-    T w[W];
-    window_poly<W, T>(u0, wp, T(1), f0, w);
-    store_vec<T, W>(row + G::WX, w);
-    window_poly<W, T>(u1, wp, T(1), f1, w);
-    store_vec<T, W>(row + G::WY, w);
-    window_poly<W, T>(u2, wp, scale, f2, w);
-    store_vec<T, W>(row + G::WZ, w);
-    return f2 - z0;
 }
 
 // Coordinates (and weight) of the point a lane will evaluate next, loaded one
@@ -154,28 +142,6 @@ __device__ __forceinline__ void load_wz(const T* row, T (&wz)[W]) {
     }
 }
 
-// One segment of a batch: the points whose cell has z-offset DZ0 in the column.
-template <int W, int Q, int E, int DZ0, typename T>
-__device__ __forceinline__ void spread_segment(T (&acc)[Q][E], const T* wt, int mydz, const int (&ri)[Q],
-                                               const int (&rj)[Q], const bool (&rv)[Q]);
-template <int W, int Q, int E, int DZ0, typename T>
-__device__ __forceinline__ void interp_segment(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
-                                               const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]);
-
-template <int W, int Q, int E, typename T, int... DZ>
-__device__ __forceinline__ void spread_batch(T (&acc)[Q][E], const T* wt, int mydz, const int (&ri)[Q],
-                                             const int (&rj)[Q], const bool (&rv)[Q],
-                                             std::integer_sequence<int, DZ...>) {
-    (spread_segment<W, Q, E, DZ, T>(acc, wt, mydz, ri, rj, rv), ...);
-}
-
-template <int W, int Q, int E, typename T, int... DZ>
-__device__ __forceinline__ void interp_batch(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
-                                             const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q],
-                                             std::integer_sequence<int, DZ...>) {
-    (interp_segment<W, Q, E, DZ, T>(win, wt, rd, lane, mydz, ri, rj, rv), ...);
-}
-
 template <int W, int Q, int E, int DZ0, typename T>
 __device__ __forceinline__ void add_taps(T (&acc)[Q][E], const T (&a)[Q], const T (&wz)[W]) {
 #pragma unroll
@@ -183,22 +149,6 @@ __device__ __forceinline__ void add_taps(T (&acc)[Q][E], const T (&a)[Q], const 
 #pragma unroll
         for (int q = 0; q < Q; ++q) acc[q][DZ0 + k] = fma(a[q], wz[k], acc[q][DZ0 + k]);
     }
-}
-
-template <int W, int Q, int E, int DZ0, typename T>
-__device__ __forceinline__ T dot_taps(const T (&win)[Q][E], const T (&a)[Q], const T (&wz)[W]) {
-    T r = T(0);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        T s0 = T(0), s1 = T(0);     // two independent chains
-#pragma unroll
-        for (int k = 0; k < W; k += 2) {
-            s0 = fma(win[q][DZ0 + k], wz[k], s0);
-            if (k + 1 < W) s1 = fma(win[q][DZ0 + k + 1], wz[k + 1], s1);
-        }
-        r = fma(a[q], s0 + s1, r);
-    }
-    return r;
 }
 
 // The column window of a lane's rows from the grid, as 16-byte vectors: chunk
@@ -267,65 +217,243 @@ __device__ __forceinline__ void row_products(const T* row, const int (&ri)[Q], c
     }
 }
 
-template <int W, int Q, int E, int DZ0, typename T>
-__device__ __forceinline__ void spread_segment(T (&acc)[Q][E], const T* wt, int mydz, const int (&ri)[Q],
-                                               const int (&rj)[Q], const bool (&rv)[Q]) {
+// ------------------------------------------------------------ sorted batches
+// A batch of 32 points is ordered by the z-offset of the
+// points' cells inside the column before the weights are written, so the
+// points of equal offset are consecutive table rows.  Returns this lane's row
+// (lanes with mydz < 0 have none).
+template <int BZ>
+__device__ __forceinline__ int sort_batch(int mydz, int lane) {
+    const unsigned below = (1u << lane) - 1u;
+    int pos = 0, acc = 0;
+#pragma unroll
+    for (int d = 0; d < BZ; ++d) {
+        const unsigned m = __ballot_sync(0xffffffffu, mydz == d);
+        if (mydz == d) pos = acc + __popc(m & below);
+        acc += __popc(m);
+    }
+    return pos;
+}
+
+// With 32 a multiple of W and W^2 a multiple of 32, all rows of a lane share
+// j = lane % W, and its x-taps are i = lane / W + q (32 / W), q < Q.  The
+// lane then leaves wy[j] out of its partial (the batch reduction applies
+// it), and the table stores wx permuted so that a lane's Q values are
+// adjacent: position (i % (32 / W)) Q + i / (32 / W) holds wx[i].
+template <int W>
+struct SharedJ {
+    static constexpr bool value = (32 % W == 0) && ((W * W) % 32 == 0);
+};
+
+template <int W, int Q>
+__host__ __device__ constexpr int wx_slot(int i) {
+    return (i % (32 / W)) * Q + i / (32 / W);
+}
+
+// Table row of a point of a sorted batch: wz (times `scale`), wx (permuted
+// when SharedJ), wy.
+template <int W, typename T>
+__device__ __forceinline__ void fill_row_sorted(T* row, T u0, T u1, T u2, T scale, const WindowPoly& wp) {
     using G = Col3<W, T>;
-    unsigned mask = __ballot_sync(0xffffffffu, mydz == DZ0);
-    // two points per step: both points' loads issue before either's FMAs
-    while (mask) {
-        const int p0 = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const T* r0 = wt + p0 * G::STRIDE;
-        T av0[Q], wz0[W];
-        row_products<W, Q, T>(r0, ri, rj, rv, av0);
-        load_wz<W, T>(r0 + G::WZ, wz0);
-        if (mask) {
-            const int p1 = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const T* r1 = wt + p1 * G::STRIDE;
-            T av1[Q], wz1[W];
-            row_products<W, Q, T>(r1, ri, rj, rv, av1);
-            load_wz<W, T>(r1 + G::WZ, wz1);
-            add_taps<W, Q, E, DZ0, T>(acc, av0, wz0);
-            add_taps<W, Q, E, DZ0, T>(acc, av1, wz1);
-        } else {
-            add_taps<W, Q, E, DZ0, T>(acc, av0, wz0);
-        }
+    int f;
+    T w[W];
+    window_poly<W, T>(u0, wp, T(1), f, w);
+    if constexpr (SharedJ<W>::value) {
+        T wpm[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) wpm[wx_slot<W, G::Q>(i)] = w[i];
+        store_vec<T, W>(row + G::WX, wpm);
+    } else {
+        store_vec<T, W>(row + G::WX, w);
+    }
+    window_poly<W, T>(u1, wp, T(1), f, w);
+    store_vec<T, W>(row + G::WY, w);
+    window_poly<W, T>(u2, wp, scale, f, w);
+    store_vec<T, W>(row + G::WZ, w);
+}
+
+// A lane's Q adjacent (permuted) x-weights.
+template <int Q, typename T>
+__device__ __forceinline__ void load_wx(const T* src, T (&x)[Q]) {
+    if constexpr (Q == 2 && sizeof(T) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(src);
+        x[0] = v.x;
+        x[1] = v.y;
+    } else if constexpr (Q == 2 && sizeof(T) == 8) {
+        const double2 v = *reinterpret_cast<const double2*>(src);
+        x[0] = v.x;
+        x[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) x[q] = src[q];
+    }
+}
+
+// The W z-taps of one row from the point's window offset DZ0.
+template <int W, int E, int DZ0, typename T>
+__device__ __forceinline__ T row_taps(const T (&w)[E], const T (&wz)[W]) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < W; ++k) s = fma(w[DZ0 + k], wz[k], s);
+    return s;
+}
+
+// One point's lane partial: sum over the lane's rows of (x or x*y weight) times its z-taps.
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ T point_partial(const T (&win)[Q][E], const T* row, int i0, const int (&ri)[Q],
+                                           const int (&rj)[Q], const bool (&rv)[Q]) {
+    using G = Col3<W, T>;
+    T wz[W];
+    load_wz<W, T>(row + G::WZ, wz);
+    T av[Q];
+    if constexpr (SharedJ<W>::value) {
+        load_wx<Q, T>(row + G::WX + i0 * Q, av);
+    } else {
+        row_products<W, Q, T>(row, ri, rj, rv, av);
+    }
+    T r = T(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) r = fma(av[q], row_taps<W, E, DZ0, T>(win[q], wz), r);
+    return r;
+}
+
+// Rows [p, pe) of the sorted batch, all at z-offset DZ0, two at a time.
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void interp_rows(const T (&win)[Q][E], const T* wt, T* rd, int lane, int p, int pe, int i0,
+                                            const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]) {
+    using G = Col3<W, T>;
+    for (; p + 1 < pe; p += 2) {
+        const T d0 = point_partial<W, Q, E, DZ0, T>(win, wt + p * G::STRIDE, i0, ri, rj, rv);
+        const T d1 = point_partial<W, Q, E, DZ0, T>(win, wt + (p + 1) * G::STRIDE, i0, ri, rj, rv);
+        rd[p * kRedStride + lane] = d0;
+        rd[(p + 1) * kRedStride + lane] = d1;
+    }
+    if (p < pe) rd[p * kRedStride + lane] = point_partial<W, Q, E, DZ0, T>(win, wt + p * G::STRIDE, i0, ri, rj, rv);
+}
+
+// Segment DZ0 of a sorted batch: its rows start at `first`, which advances
+// past them.
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void interp_segment_sorted(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
+                                                      int& first, int i0, const int (&ri)[Q], const int (&rj)[Q],
+                                                      const bool (&rv)[Q]) {
+    const int cnt = __popc(__ballot_sync(0xffffffffu, mydz == DZ0));
+    interp_rows<W, Q, E, DZ0, T>(win, wt, rd, lane, first, first + cnt, i0, ri, rj, rv);
+    first += cnt;
+}
+
+template <int W, int Q, int E, typename T, int... DZ>
+__device__ __forceinline__ void interp_sorted(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz, int i0,
+                                              const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q],
+                                              std::integer_sequence<int, DZ...>) {
+    int first = 0;
+    (interp_segment_sorted<W, Q, E, DZ, T>(win, wt, rd, lane, mydz, first, i0, ri, rj, rv), ...);
+}
+
+// Spreading of rows [p, pe) of a sorted batch, all at z-offset DZ0: the
+// lane's rows get (x y weight) times the point's scaled z-taps.
+template <int W, int Q, typename T>
+__device__ __forceinline__ void row_weights_sorted(const T* row, int i0, int j0, const int (&ri)[Q], const int (&rj)[Q],
+                                                   const bool (&rv)[Q], T (&av)[Q]) {
+    using G = Col3<W, T>;
+    if constexpr (SharedJ<W>::value) {
+        load_wx<Q, T>(row + G::WX + i0 * Q, av);
+        const T wy = row[G::WY + j0];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) av[q] *= wy;
+    } else {
+        row_products<W, Q, T>(row, ri, rj, rv, av);
     }
 }
 
 template <int W, int Q, int E, int DZ0, typename T>
-__device__ __forceinline__ void interp_segment(const T (&win)[Q][E], const T* wt, T* rd, int lane, int mydz,
-                                               const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]) {
+__device__ __forceinline__ void spread_rows(T (&acc)[Q][E], const T* wt, int p, int pe, int i0, int j0,
+                                            const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q]) {
     using G = Col3<W, T>;
-    unsigned mask = __ballot_sync(0xffffffffu, mydz == DZ0);
-    while (mask) {
-        const int p0 = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const T* r0 = wt + p0 * G::STRIDE;
-        T av0[Q], wz0[W];
-        row_products<W, Q, T>(r0, ri, rj, rv, av0);
+    for (; p + 1 < pe; p += 2) {
+        const T* r0 = wt + p * G::STRIDE;
+        const T* r1 = r0 + G::STRIDE;
+        T av0[Q], av1[Q], wz0[W], wz1[W];
+        row_weights_sorted<W, Q, T>(r0, i0, j0, ri, rj, rv, av0);
         load_wz<W, T>(r0 + G::WZ, wz0);
-        if (mask) {
-            const int p1 = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const T* r1 = wt + p1 * G::STRIDE;
-            T av1[Q], wz1[W];
-            row_products<W, Q, T>(r1, ri, rj, rv, av1);
-            load_wz<W, T>(r1 + G::WZ, wz1);
-            const T d0 = dot_taps<W, Q, E, DZ0, T>(win, av0, wz0);
-            const T d1 = dot_taps<W, Q, E, DZ0, T>(win, av1, wz1);
-            rd[p0 * kRedStride + lane] = d0;
-            rd[p1 * kRedStride + lane] = d1;
+        row_weights_sorted<W, Q, T>(r1, i0, j0, ri, rj, rv, av1);
+        load_wz<W, T>(r1 + G::WZ, wz1);
+        add_taps<W, Q, E, DZ0, T>(acc, av0, wz0);
+        add_taps<W, Q, E, DZ0, T>(acc, av1, wz1);
+    }
+    if (p < pe) {
+        const T* r0 = wt + p * G::STRIDE;
+        T av0[Q], wz0[W];
+        row_weights_sorted<W, Q, T>(r0, i0, j0, ri, rj, rv, av0);
+        load_wz<W, T>(r0 + G::WZ, wz0);
+        add_taps<W, Q, E, DZ0, T>(acc, av0, wz0);
+    }
+}
+
+template <int W, int Q, int E, int DZ0, typename T>
+__device__ __forceinline__ void spread_segment_sorted(T (&acc)[Q][E], const T* wt, int mydz, int& first, int i0,
+                                                      int j0, const int (&ri)[Q], const int (&rj)[Q],
+                                                      const bool (&rv)[Q]) {
+    const int cnt = __popc(__ballot_sync(0xffffffffu, mydz == DZ0));
+    spread_rows<W, Q, E, DZ0, T>(acc, wt, first, first + cnt, i0, j0, ri, rj, rv);
+    first += cnt;
+}
+
+template <int W, int Q, int E, typename T, int... DZ>
+__device__ __forceinline__ void spread_sorted(T (&acc)[Q][E], const T* wt, int mydz, int i0, int j0,
+                                              const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q],
+                                              std::integer_sequence<int, DZ...>) {
+    int first = 0;
+    (spread_segment_sorted<W, Q, E, DZ, T>(acc, wt, mydz, first, i0, j0, ri, rj, rv), ...);
+}
+
+// Kernel sum of the point in table row `pos`: its 32 lane partials, times
+// wy[j] per lane group when the lanes left it out.
+template <int W, typename T>
+__device__ __forceinline__ T batch_sum(const T* rd, const T* row, int pos) {
+    using G = Col3<W, T>;
+    const T* pr = rd + pos * kRedStride;
+    if constexpr (SharedJ<W>::value) {
+        T g[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) g[j] = T(0);
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int l = 0; l < 32; l += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(pr + l);
+                g[(l + 0) % W] += v.x;
+                g[(l + 1) % W] += v.y;
+                g[(l + 2) % W] += v.z;
+                g[(l + 3) % W] += v.w;
+            }
         } else {
-            rd[p0 * kRedStride + lane] = dot_taps<W, Q, E, DZ0, T>(win, av0, wz0);
+#pragma unroll
+            for (int l = 0; l < 32; l += 2) {
+                const double2 v = *reinterpret_cast<const double2*>(pr + l);
+                g[(l + 0) % W] += v.x;
+                g[(l + 1) % W] += v.y;
+            }
         }
+        T wy[W];
+        load_wz<W, T>(row + G::WY, wy);
+        T t = T(0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) t = fma(wy[j], g[j], t);
+        return t;
+    } else {
+        T t0 = T(0), t1 = T(0);
+#pragma unroll
+        for (int l = 0; l < 32; l += 2) {
+            t0 += pr[l];
+            t1 += pr[l + 1];
+        }
+        return t0 + t1;
     }
 }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
+__global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 4 : 2) : (W <= 6 ? 2 : 1))
+    k_spread3_col(SpreadArgs a) {
     using G = Col3<W, T>;
     constexpr int Q = G::Q, E = G::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -338,7 +466,7 @@ __global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
     const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
     const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
     for (int c = threadIdx.x; c < G::SUB; c += blockDim.x) sub[c] = T(0);
-    if (threadIdx.x == 0) col_next = col0 + kWarps;
+    if (threadIdx.x == 0) col_next = col0 + kSpreadWarps;
     __syncthreads();
 
     const T* c0 = static_cast<const T*>(a.coord[0]);
@@ -364,11 +492,13 @@ __global__ void __launch_bounds__(256) k_spread3_col(SpreadArgs a) {
             pf.load(c0, c1, c2, a.w, start + lane, lane < end - start);
             for (int base = start; base < end; base += 32) {
                 const int cnt = min(32, end - base);
-                int mydz = -1;
-                if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp, z0);
+                const int mydz = lane < cnt ? int(floor(pf.u2)) - z0 : -1;
+                const int pos = sort_batch<G::BZ>(mydz, lane);
+                if (lane < cnt) fill_row_sorted<W, T>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp);
                 pf.load(c0, c1, c2, a.w, base + 32 + lane, base + 32 + lane < end);
                 __syncwarp();
-                spread_batch<W, Q, E, T>(acc, wt, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
+                spread_sorted<W, Q, E, T>(acc, wt, mydz, lane / W, lane % W, ri, rj, rv,
+                                          std::make_integer_sequence<int, G::BZ>{});
                 __syncwarp();
             }
             const int cx = col / G::BY, cy = col % G::BY;
@@ -423,9 +553,9 @@ __device__ __forceinline__ void queue_leave(unsigned* q, int lane) {
     }
 }
 
-// A queue entry: the column's points [start, end) and its cell offsets.
+// A queue entry: its (bin, column) code and the column's points [start, end).
 struct ColumnRef {
-    int start = 0, end = 0, gx0 = 0, gy0 = 0, z0 = 0;
+    int code = 0, start = 0, end = 0;
 };
 
 template <int W, typename T>
@@ -433,15 +563,10 @@ __device__ __forceinline__ ColumnRef column_ref(const InterpArgs& a, int c) {
     using G = Col3<W, T>;
     ColumnRef r;
     if (c >= a.ncols) return r;
-    const int code = a.cols[c];
-    const int bin = code / G::NCOL, col = code % G::NCOL;
-    const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
-    const int64_t k0 = int64_t(bin) * (G::NCOL * G::BZ) + col * G::BZ;
+    r.code = a.cols[c];
+    const int64_t k0 = int64_t(r.code / G::NCOL) * (G::NCOL * G::BZ) + (r.code % G::NCOL) * G::BZ;
     r.start = a.key_start[k0];
     r.end = a.key_start[k0 + G::BZ];
-    r.gx0 = bx * G::BX + col / G::BY - (W / 2 - 1);
-    r.gy0 = by * G::BY + col % G::BY - (W / 2 - 1);
-    r.z0 = bz * G::BZ;
     return r;
 }
 
@@ -450,7 +575,8 @@ __device__ __forceinline__ ColumnRef column_ref(const InterpArgs& a, int c) {
 // whatever the number of bins.  The next entry is taken, and its first batch
 // of coordinates requested, while the current column is processed.
 template <int W, typename T>
-__global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (W <= 8 ? 3 : 2) : (W <= 6 ? 2 : 1))
+    k_interp3_col(InterpArgs a, Epilogue e) {
     using G = Col3<W, T>;
     constexpr int Q = G::Q, E = G::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -482,12 +608,18 @@ __global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e
     while (c < a.ncols) {
         const int cn = queue_take(a.queue, lane);
         const ColumnRef nxt = column_ref<W, T>(a, cn);
+        // the column's cell offsets: bin (bx, by, bz), column (cx, cy) inside it
+        const int bin = cur.code / G::NCOL, col = cur.code % G::NCOL;
+        const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
+        const int z0 = bz * G::BZ;
         T win[Q][E];
-        load_window<W, T>(win, grid, n, cur.gx0, cur.gy0, cur.z0 - G::ZA, ri, rj, rv);
+        load_window<W, T>(win, grid, n, bx * G::BX + col / G::BY - (W / 2 - 1), by * G::BY + col % G::BY - (W / 2 - 1),
+                          z0 - G::ZA, ri, rj, rv);
         for (int base = cur.start; base < cur.end; base += 32) {
             const int cnt = min(32, cur.end - base);
-            int mydz = -1;
-            if (lane < cnt) mydz = fill_row<W, T>(wt + lane * G::STRIDE, pf.u0, pf.u1, pf.u2, T(1), a.wp, cur.z0);
+            const int mydz = lane < cnt ? int(floor(pf.u2)) - z0 : -1;
+            const int pos = sort_batch<G::BZ>(mydz, lane);
+            if (lane < cnt) fill_row_sorted<W, T>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, T(1), a.wp);
             const EpiPrefetch epc = ep;
             // the next batch: this column's, else the next column's first
             const bool more = base + 32 < cur.end;
@@ -496,29 +628,12 @@ __global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e
             pf.load(c0, c1, c2, nullptr, nb + lane, nb + lane < ne);
             ep.load(e, nb + lane, nb + lane < ne);
             __syncwarp();
-            interp_batch<W, Q, E, T>(win, wt, rd, lane, mydz, ri, rj, rv, std::make_integer_sequence<int, G::BZ>{});
+            interp_sorted<W, Q, E, T>(win, wt, rd, lane, mydz, lane / W, ri, rj, rv,
+                                      std::make_integer_sequence<int, G::BZ>{});
             __syncwarp();
-            if (lane < cnt) {
-                // the point's 32 lane partials, four at a time
-                if constexpr (sizeof(T) == 4) {
-                    const float4* row = reinterpret_cast<const float4*>(rd + lane * kRedStride);
-                    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-#pragma unroll
-                    for (int l = 0; l < 8; ++l) {
-                        const float4 v = row[l];
-                        t0 += v.x;
-                        t1 += v.y;
-                        t2 += v.z;
-                        t3 += v.w;
-                    }
-                    epi_point_pre(e, base + lane, double((t0 + t1) + (t2 + t3)), epc.q, epc.a, sq, bad, dot);
-                } else {
-                    T t = T(0);
-#pragma unroll 8
-                    for (int l = 0; l < 32; ++l) t += rd[lane * kRedStride + l];
-                    epi_point_pre(e, base + lane, double(t), epc.q, epc.a, sq, bad, dot);
-                }
-            }
+            if (lane < cnt)
+                epi_point_pre(e, base + lane, double(batch_sum<W, T>(rd, wt + pos * G::STRIDE, pos)), epc.q, epc.a, sq,
+                              bad, dot);
             __syncwarp();
         }
         c = cn;
@@ -532,7 +647,7 @@ __global__ void __launch_bounds__(256, 3) k_interp3_col(InterpArgs a, Epilogue e
 template <int W, typename T>
 size_t spread3_smem() {
     using G = Col3<W, T>;
-    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kWarps) * 32 * G::STRIDE) * sizeof(T);
+    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kSpreadWarps) * 32 * G::STRIDE) * sizeof(T);
 }
 
 template <int W, typename T>
@@ -559,7 +674,7 @@ static cudaError_t spread3_one(const SpreadArgs& a, cudaStream_t s) {
     cudaError_t err = opt_in<k_spread3_col<W, T>>(bytes);
     if (err != cudaSuccess) return err;
     if (a.ntasks == 0) return cudaSuccess;
-    k_spread3_col<W, T><<<a.ntasks, 256, bytes, s>>>(a);
+    k_spread3_col<W, T><<<a.ntasks, kSpreadWarps * 32, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
