@@ -43,9 +43,17 @@ struct sk_plan {
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_kernels = 0;
     bool timing = false;
-    std::vector<cudaEvent_t> tev;      // pairs
-    std::vector<int> tev_stage;
-    size_t tev_used = 0;
+    // stage timing: pairs of events around each stage, either recorded as
+    // the stages are launched (eager) or captured into the timed graph
+    struct EventPool {
+        std::vector<cudaEvent_t> ev;   // pairs
+        std::vector<int> stage;
+        size_t used = 0;
+    };
+    EventPool eager, graph_ev;
+    EventPool* pool = &eager;
+    cudaGraphExec_t gexec_timed = nullptr;   // one iteration with its stage events
+    int64_t graph_kernels_timed = 0;
     double stage_ms[SK_NSTAGES] = {0};
     int64_t stage_cnt[SK_NSTAGES] = {0};
     int iters = 0;
@@ -122,38 +130,48 @@ void leave(sk_plan* P, void* stream) {
 }
 
 // ------------------------------------------------------------ stage timing
+// Inside a capture the stage events become event-record nodes of the graph
+// (external records), so they are recorded, with timestamps, on every replay.
+unsigned stage_record_flags(const sk_plan* P) {
+    return P->pool == &P->graph_ev ? cudaEventRecordExternal : cudaEventRecordDefault;
+}
+
 int stage_begin(sk_plan* P, int stage) {
     if (!P->timing) return -1;
-    if (P->tev_used * 2 + 2 > P->tev.size()) {
-        for (int k = 0; k < 256; ++k) {
+    sk_plan::EventPool& q = *P->pool;
+    if (q.used * 2 + 2 > q.ev.size()) {
+        for (int k = 0; k < 64; ++k) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e));
-            P->tev.push_back(e);
+            q.ev.push_back(e);
         }
-        P->tev_stage.resize(P->tev.size() / 2);
+        q.stage.resize(q.ev.size() / 2);
     }
-    const int idx = int(P->tev_used++);
-    P->tev_stage[idx] = stage;
-    CK(cudaEventRecord(P->tev[2 * idx], P->ps));
+    const int idx = int(q.used++);
+    q.stage[idx] = stage;
+    CK(cudaEventRecordWithFlags(q.ev[2 * idx], P->ps, stage_record_flags(P)));
     return idx;
 }
 
 void stage_end(sk_plan* P, int idx) {
     if (idx < 0) return;
-    CK(cudaEventRecord(P->tev[2 * idx + 1], P->ps));
+    CK(cudaEventRecordWithFlags(P->pool->ev[2 * idx + 1], P->ps, stage_record_flags(P)));
 }
 
-void stage_resolve(sk_plan* P) {
-    if (P->tev_used == 0) return;
+// Adds the recorded stage intervals of a pool to the totals.
+void pool_resolve(sk_plan* P, sk_plan::EventPool& q, bool keep) {
+    if (q.used == 0) return;
     CK(cudaStreamSynchronize(P->ps));
-    for (size_t k = 0; k < P->tev_used; ++k) {
+    for (size_t k = 0; k < q.used; ++k) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, P->tev[2 * k], P->tev[2 * k + 1]));
-        P->stage_ms[P->tev_stage[k]] += ms;
-        P->stage_cnt[P->tev_stage[k]] += 1;
+        CK(cudaEventElapsedTime(&ms, q.ev[2 * k], q.ev[2 * k + 1]));
+        P->stage_ms[q.stage[k]] += ms;
+        P->stage_cnt[q.stage[k]] += 1;
     }
-    P->tev_used = 0;
+    if (!keep) q.used = 0;
 }
+
+void stage_resolve(sk_plan* P) { pool_resolve(P, P->eager, false); }
 
 // ------------------------------------------------------------ host math
 // Derivatives 0..p-1 of K(rho) = exp(g(rho)), g = -rho^r / eps, at rho0, from
@@ -747,11 +765,20 @@ void destroy_graph(sk_plan* P) {
         cudaGraphExecDestroy(P->gexec);
         P->gexec = nullptr;
     }
+    if (P->gexec_timed) {
+        cudaGraphExecDestroy(P->gexec_timed);
+        P->gexec_timed = nullptr;
+    }
 }
 
-void ensure_graph(sk_plan* P) {
-    if (P->gexec) return;
+// One iteration captured into a graph; with stage timing on, the stage events
+// are captured too (as event-record nodes of their own pool).
+void capture_iteration(sk_plan* P, cudaGraphExec_t* out, int64_t* kernels) {
     const int64_t before = P->launches;
+    if (P->timing) {
+        P->graph_ev.used = 0;
+        P->pool = &P->graph_ev;
+    }
     CK(cudaStreamBeginCapture(P->ps, cudaStreamCaptureModeThreadLocal));
     cudaGraph_t g = nullptr;
     try {
@@ -760,22 +787,29 @@ void ensure_graph(sk_plan* P) {
         cudaStreamEndCapture(P->ps, &g);
         if (g) cudaGraphDestroy(g);
         P->launches = before;
+        P->pool = &P->eager;
         throw;
     }
+    P->pool = &P->eager;
     CK(cudaStreamEndCapture(P->ps, &g));
-    P->graph_kernels = P->launches - before;
+    *kernels = P->launches - before;
     P->launches = before;
-    cudaError_t e = cudaGraphInstantiate(&P->gexec, g, 0);
+    cudaError_t e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     CK(e);
 }
 
+// Iterations by graph replay.  With stage timing on, the replayed graph
+// holds the stage events, which are read after every replay.
 void iterate(sk_plan* P, int k) {
     for (int i = 0; i < k; ++i) {
         if (P->timing) {
-            run_iteration(P);
+            if (!P->gexec_timed) capture_iteration(P, &P->gexec_timed, &P->graph_kernels_timed);
+            CK(cudaGraphLaunch(P->gexec_timed, P->ps));
+            P->launches += P->graph_kernels_timed;
+            pool_resolve(P, P->graph_ev, true);
         } else {
-            ensure_graph(P);
+            if (!P->gexec) capture_iteration(P, &P->gexec, &P->graph_kernels);
             CK(cudaGraphLaunch(P->gexec, P->ps));
             P->launches += P->graph_kernels;
         }
@@ -1112,7 +1146,8 @@ void sk_destroy(sk_plan* P) {
     if (P->ps) cudaStreamSynchronize(P->ps);
     destroy_graph(P);
     for (void* p : P->allocs) cudaFree(p);
-    for (cudaEvent_t e : P->tev) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->eager.ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->graph_ev.ev) cudaEventDestroy(e);
     if (P->pinned) cudaFreeHost(P->pinned);
     if (P->ev_in) cudaEventDestroy(P->ev_in);
     if (P->ev_out) cudaEventDestroy(P->ev_out);

@@ -4,7 +4,9 @@
 //
 //   * Every block loads P pencils of length n (P * n = kFftBlockElems complex
 //     values, or one pencil when n is larger) into shared memory, runs a
-//     radix-2 FFT there and writes back.
+//     radix-2 FFT there and writes back.  Blocks are small (two butterflies
+//     per thread and stage), so a launch has many of them and their load,
+//     barrier and store latencies overlap on every SM.
 //     Pencils are padded to n+1 elements so that the loads, which walk the
 //     pencils in parallel, do not collide in shared-memory banks.
 //   * The grid is real, so the first pass packs two real rows into one complex
@@ -33,9 +35,15 @@ namespace sk {
 
 enum { FULL = 0, CENTERED = 1 };
 
-constexpr int kFftBlockElems = 1024;
+constexpr int kFftBlockElems = 256;
 
 __host__ __device__ __forceinline__ int fft_pencils(int n) { return n >= kFftBlockElems ? 1 : kFftBlockElems / n; }
+
+// Threads of an FFT block: two butterflies per thread and stage, 32 to 256.
+__host__ __device__ __forceinline__ int fft_threads(int n) {
+    const int t = fft_pencils(n) * n / 4;
+    return t < 32 ? 32 : (t > 256 ? 256 : t);
+}
 
 // Row pairs of the real passes: pair q covers rows r0 = o * ostride + y and
 // r0 + 1 with o = olo + q / npo and y = ylo + 2 (q % npo).
@@ -61,9 +69,10 @@ __device__ __forceinline__ C cmul(C a, C b) {
 __device__ __forceinline__ int bitrev(int v, int log2n) { return int(__brev(unsigned(v)) >> (32 - log2n)); }
 
 // Decimation in time: input in bit-reversed order, output in natural order.
+// `tw` is the block's shared-memory copy of the n/2 twiddles.
 template <typename T, bool INV>
 __device__ void fft_dit(typename Cplx<T>::type* buf, int ns, int n, int log2n, int P,
-                        const typename Cplx<T>::type* __restrict__ tw) {
+                        const typename Cplx<T>::type* tw) {
     using C = typename Cplx<T>::type;
     const int half = n >> 1;
     const int total = P * half;
@@ -93,7 +102,7 @@ __device__ void fft_dit(typename Cplx<T>::type* buf, int ns, int n, int log2n, i
 // Decimation in frequency: input in natural order, output in bit-reversed order.
 template <typename T, bool INV>
 __device__ void fft_dif(typename Cplx<T>::type* buf, int ns, int n, int log2n, int P,
-                        const typename Cplx<T>::type* __restrict__ tw) {
+                        const typename Cplx<T>::type* tw) {
     using C = typename Cplx<T>::type;
     const int half = n >> 1;
     const int total = P * half;
@@ -122,33 +131,68 @@ __device__ void fft_dif(typename Cplx<T>::type* buf, int ns, int n, int log2n, i
     __syncthreads();
 }
 
+// Shared memory of an FFT block: the n/2 twiddles, then P pencils of n + 1.
+template <typename T>
+struct FftSmem {
+    using C = typename Cplx<T>::type;
+    C* tw;
+    C* buf;
+    __device__ __forceinline__ explicit FftSmem(int n) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        tw = reinterpret_cast<C*>(smem_raw);
+        buf = tw + n / 2;
+    }
+};
+
+template <typename C>
+__device__ __forceinline__ void load_twiddles(C* dst, const C* __restrict__ src, int n) {
+    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) dst[k] = src[k];
+}
+
+// Elements a thread loads per round; a round's loads are all issued before
+// any of them is stored, so their latencies overlap.
+constexpr int kFftLoadsPerRound = 4;
+
 // Two real rows of length n -> two half spectra of length h+1 (output rows
 // are the same row indices in A1).  The input rows are zeroed after reading.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
                                                       RowPairs rp, int n, int log2n, int h,
-                                                      const typename Cplx<T>::type* __restrict__ tw) {
+                                                      const typename Cplx<T>::type* __restrict__ twg) {
     using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    const FftSmem<T> sm(n);
+    C* buf = sm.buf;
+    const C* tw = sm.tw;
+    load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
     const int ns = n + 1;
     const int64_t q0 = int64_t(blockIdx.x) * P;
-    for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-        const int p = e >> log2n;
-        const int l = e & (n - 1);
-        const int64_t q = q0 + p;
-        C z;
-        z.x = T(0);
-        z.y = T(0);
-        if (q < rp.npairs) {
-            const int64_t r0 = pair_row(rp, q);
-            z.x = g[r0 * n + l];
-            z.y = g[(r0 + 1) * n + l];
-            g[r0 * n + l] = T(0);
-            g[(r0 + 1) * n + l] = T(0);
+    for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * blockDim.x) {
+        C z[kFftLoadsPerRound];
+        int64_t at[kFftLoadsPerRound];
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            const int64_t q = q0 + (e >> log2n);
+            z[j].x = T(0);
+            z[j].y = T(0);
+            at[j] = -1;
+            if (e < P * n && q < rp.npairs) {
+                at[j] = pair_row(rp, q) * n + (e & (n - 1));
+                z[j].x = g[at[j]];
+                z[j].y = g[at[j] + n];
+            }
         }
-        buf[p * ns + bitrev(l, log2n)] = z;
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            if (e >= P * n) continue;
+            if (at[j] >= 0) {
+                g[at[j]] = T(0);
+                g[at[j] + n] = T(0);
+            }
+            buf[(e >> log2n) * ns + bitrev(e & (n - 1), log2n)] = z[j];
+        }
     }
     fft_dit<T, false>(buf, ns, n, log2n, P, tw);
     const int H = h + 1;
@@ -174,38 +218,57 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typenam
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
                                                       RowPairs rp, int n, int log2n, int h,
-                                                      const typename Cplx<T>::type* __restrict__ tw) {
+                                                      const typename Cplx<T>::type* __restrict__ twg) {
     using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    const FftSmem<T> sm(n);
+    C* buf = sm.buf;
+    const C* tw = sm.tw;
+    load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
     const int ns = n + 1;
     const int H = h + 1;
     const int64_t q0 = int64_t(blockIdx.x) * P;
-    for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-        const int p = e >> log2n;
-        const int pos = e & (n - 1);
-        const int64_t q = q0 + p;
-        C z;
-        z.x = T(0);
-        z.y = T(0);
-        if (q < rp.npairs) {
-            const int64_t r0 = pair_row(rp, q);
+    for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * blockDim.x) {
+        C A[kFftLoadsPerRound], Bv[kFftLoadsPerRound];
+        int sgn[kFftLoadsPerRound];   // +1: k in 0..h, -1: -k in 1..h, 0: outside (zero)
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            const int pos = e & (n - 1);
+            const int64_t q = q0 + (e >> log2n);
             const int k = pos <= (n >> 1) ? pos : pos - n;
-            if (k >= 0 && k <= h) {
-                C A = in[r0 * H + k];
-                C Bv = in[(r0 + 1) * H + k];
-                if (k == 0) { A.y = T(0); Bv.y = T(0); }
-                z.x = A.x - Bv.y;
-                z.y = A.y + Bv.x;
-            } else if (k < 0 && -k <= h) {
-                const C A = in[r0 * H - k];
-                const C Bv = in[(r0 + 1) * H - k];
-                z.x = A.x + Bv.y;
-                z.y = Bv.x - A.y;
+            sgn[j] = 0;
+            A[j].x = A[j].y = Bv[j].x = Bv[j].y = T(0);
+            if (e < P * n && q < rp.npairs && k >= -h && k <= h) {
+                const int64_t r0 = pair_row(rp, q);
+                const int ka = k >= 0 ? k : -k;
+                sgn[j] = k >= 0 ? 1 : -1;
+                A[j] = in[r0 * H + ka];
+                Bv[j] = in[(r0 + 1) * H + ka];
             }
         }
-        buf[p * ns + pos] = z;
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            if (e >= P * n) continue;
+            const int pos = e & (n - 1);
+            C z;
+            if (sgn[j] > 0) {
+                if (pos == 0) {
+                    A[j].y = T(0);
+                    Bv[j].y = T(0);
+                }
+                z.x = A[j].x - Bv[j].y;
+                z.y = A[j].y + Bv[j].x;
+            } else if (sgn[j] < 0) {
+                z.x = A[j].x + Bv[j].y;
+                z.y = Bv[j].x - A[j].y;
+            } else {
+                z.x = T(0);
+                z.y = T(0);
+            }
+            buf[(e >> log2n) * ns + pos] = z;
+        }
     }
     fft_dif<T, true>(buf, ns, n, log2n, P, tw);
     for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
@@ -229,10 +292,12 @@ template <typename T, int INM, int OUTM, bool INV>
 __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* __restrict__ in,
                                                   typename Cplx<T>::type* __restrict__ out, int64_t olo, int64_t ocnt,
                                                   int64_t I, int klo, int kcnt, int n, int log2n, int h,
-                                                  const typename Cplx<T>::type* __restrict__ tw) {
+                                                  const typename Cplx<T>::type* __restrict__ twg) {
     using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    const FftSmem<T> sm(n);
+    C* buf = sm.buf;
+    const C* tw = sm.tw;
+    load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
     const int ns = n + 1;
     const int64_t Q = ocnt * I;
@@ -248,14 +313,25 @@ __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* 
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < P * Lin; e += blockDim.x) {
-        const int k = e / P;
-        const int pl = e - k * P;
-        const int64_t q = q0 + pl;
-        if (q >= Q) continue;
-        const int64_t o = olo + q / I, i = q % I;
-        const int pos = INM == FULL ? k : ((k - h) & (n - 1));
-        buf[pl * ns + bitrev(pos, log2n)] = in[(o * Lin + k) * I + i];
+    for (int e0 = 0; e0 < P * Lin; e0 += kFftLoadsPerRound * blockDim.x) {
+        C v[kFftLoadsPerRound];
+        bool ok[kFftLoadsPerRound];
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            const int k = e / P;
+            const int64_t q = q0 + (e - k * P);
+            ok[j] = e < P * Lin && q < Q;
+            if (ok[j]) v[j] = in[((olo + q / I) * Lin + k) * I + q % I];
+        }
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            if (!ok[j]) continue;
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            const int k = e / P;
+            const int pos = INM == FULL ? k : ((k - h) & (n - 1));
+            buf[(e - k * P) * ns + bitrev(pos, log2n)] = v[j];
+        }
     }
     fft_dit<T, INV>(buf, ns, n, log2n, P, tw);
     for (int e = threadIdx.x; e < P * kn; e += blockDim.x) {
@@ -278,37 +354,73 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::type* __restrict__ data, int64_t I,
                                                             int xlo, int xcnt, int n, int log2n, int h,
                                                             const T* __restrict__ mult,
-                                                            const typename Cplx<T>::type* __restrict__ tw) {
+                                                            const typename Cplx<T>::type* __restrict__ twg) {
     using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    const FftSmem<T> sm(n);
+    C* buf = sm.buf;
+    const C* tw = sm.tw;
+    load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
     const int ns = n + 1;
     const int64_t q0 = int64_t(blockIdx.x) * P;
-    for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-        const int k = e / P;
-        const int pl = e - k * P;
-        const int64_t q = q0 + pl;
-        C v;
-        v.x = T(0);
-        v.y = T(0);
-        if (q < I && k >= xlo && k < xlo + xcnt) v = data[int64_t(k) * I + q];
-        buf[pl * ns + bitrev(k, log2n)] = v;
+    for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * blockDim.x) {
+        C v[kFftLoadsPerRound];
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            const int k = e / P;
+            const int64_t q = q0 + (e - k * P);
+            v[j].x = T(0);
+            v[j].y = T(0);
+            if (e < P * n && q < I && k >= xlo && k < xlo + xcnt) v[j] = data[int64_t(k) * I + q];
+        }
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = e0 + j * blockDim.x + threadIdx.x;
+            if (e >= P * n) continue;
+            const int k = e / P;
+            buf[(e - k * P) * ns + bitrev(k, log2n)] = v[j];
+        }
+    }
+    // when one round covers the block, the multiplier of each element this
+    // thread scales is loaded before the forward transform, so its latency
+    // hides behind it
+    const bool one_round = P * n <= kFftLoadsPerRound * int(blockDim.x);
+    T mv[kFftLoadsPerRound];
+#pragma unroll
+    for (int j = 0; j < kFftLoadsPerRound; ++j) {
+        const int e = j * blockDim.x + threadIdx.x;
+        const int pos = e / P;
+        const int64_t q = q0 + (e - pos * P);
+        const int k = pos <= (n >> 1) ? pos : pos - n;
+        mv[j] = (one_round && e < P * n && q < I && k >= -h && k <= h) ? mult[int64_t(k + h) * I + q] : T(0);
     }
     fft_dit<T, false>(buf, ns, n, log2n, P, tw);
-    for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-        const int pos = e / P;
-        const int pl = e - pos * P;
-        const int64_t q = q0 + pl;
-        const int k = pos <= (n >> 1) ? pos : pos - n;
-        C& v = buf[pl * ns + pos];
-        if (q < I && k >= -h && k <= h) {
-            const T mv = mult[int64_t(k + h) * I + q];
-            v.x *= mv;
-            v.y *= mv;
-        } else {
-            v.x = T(0);
-            v.y = T(0);
+    if (one_round) {
+#pragma unroll
+        for (int j = 0; j < kFftLoadsPerRound; ++j) {
+            const int e = j * blockDim.x + threadIdx.x;
+            if (e >= P * n) continue;
+            const int pos = e / P;
+            C& v = buf[(e - pos * P) * ns + pos];
+            v.x *= mv[j];
+            v.y *= mv[j];
+        }
+    } else {
+        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+            const int pos = e / P;
+            const int pl = e - pos * P;
+            const int64_t q = q0 + pl;
+            const int k = pos <= (n >> 1) ? pos : pos - n;
+            C& v = buf[pl * ns + pos];
+            if (q < I && k >= -h && k <= h) {
+                const T m = mult[int64_t(k + h) * I + q];
+                v.x *= m;
+                v.y *= m;
+            } else {
+                v.x = T(0);
+                v.y = T(0);
+            }
         }
     }
     fft_dif<T, true>(buf, ns, n, log2n, P, tw);
@@ -386,14 +498,14 @@ __global__ void k_fill_forward(const double* __restrict__ fhat, int d, int h, co
 
 template <typename T>
 static size_t fft_smem_bytes(int n) {
-    return size_t(fft_pencils(n)) * size_t(n + 1) * sizeof(typename Cplx<T>::type);
+    return (size_t(n / 2) + size_t(fft_pencils(n)) * size_t(n + 1)) * sizeof(typename Cplx<T>::type);
 }
 
 // Largest dynamic shared memory any FFT launch of this precision can use:
-// one pencil of the largest length, 4096 (P (n + 1) is largest there).
+// one pencil of the largest length, 4096, and its twiddles.
 template <typename T>
 static size_t fft_smem_max() {
-    return size_t(4096 + 1) * sizeof(typename Cplx<T>::type);
+    return size_t(2048 + 4096 + 1) * sizeof(typename Cplx<T>::type);
 }
 
 // Opt a kernel into its largest shared-memory size once per device (the cache
@@ -445,7 +557,7 @@ static cudaError_t run_r2c(const FftPlan& f, int64_t* launches, cudaStream_t s) 
     SK_TRY((ensure_smem<T, k_fft_r2c_rows<T>>()));
     const RowPairs rp = row_pairs(f);
     const int P = fft_pencils(f.n);
-    k_fft_r2c_rows<T><<<unsigned((rp.npairs + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_r2c_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<T*>(f.grid), static_cast<C*>(f.A1), rp, f.n, f.log2n, f.h, static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
@@ -457,7 +569,7 @@ static cudaError_t run_c2r(const FftPlan& f, int64_t* launches, cudaStream_t s) 
     SK_TRY((ensure_smem<T, k_fft_c2r_rows<T>>()));
     const RowPairs rp = row_pairs(f);
     const int P = fft_pencils(f.n);
-    k_fft_c2r_rows<T><<<unsigned((rp.npairs + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_c2r_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<const C*>(f.A1), static_cast<T*>(f.grid_out), rp, f.n, f.log2n, f.h,
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
@@ -471,7 +583,7 @@ static cudaError_t run_axis(const FftPlan& f, const void* in, void* out, int64_t
     SK_TRY((ensure_smem<T, k_fft_axis<T, INM, OUTM, INV>>()));
     const int P = fft_pencils(f.n);
     const int64_t Q = ocnt * I;
-    k_fft_axis<T, INM, OUTM, INV><<<unsigned((Q + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_axis<T, INM, OUTM, INV><<<unsigned((Q + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<const C*>(in), static_cast<C*>(out), olo, ocnt, I, klo, kcnt, f.n, f.log2n, f.h,
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
@@ -497,7 +609,7 @@ static cudaError_t run_axis0_convolve(const FftPlan& f, void* data, int64_t I, i
     const int P = fft_pencils(f.n);
     int xlo, xcnt;
     axis0_range(f, xlo, xcnt);
-    k_fft_axis0_convolve<T><<<unsigned((I + P - 1) / P), 256, fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_axis0_convolve<T><<<unsigned((I + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<C*>(data), I, xlo, xcnt, f.n, f.log2n, f.h, static_cast<const T*>(f.mult),
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
