@@ -165,3 +165,52 @@ def objective_f(u, v, a, b, K):
     """f(u, v) = u^T K v - sum a log u - sum b log v (Eq. (objfunc)), here with
     the unnormalized K that Alg. 1 iterates with."""
     return float(u @ K @ v - np.sum(a * np.log(u)) - np.sum(b * np.log(v)))
+
+
+def cost_gradient(x, y, r):
+    """dC_ij / dx_i for C_ij = ||x_i - y_j||^r: r ||x_i - y_j||^(r-2) (x_i - y_j),
+    shape (n, m, d).  Where x_i = y_j the cost is not differentiable for r < 2;
+    there the value 0 (a subgradient) is taken."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    diff = x[:, None, :] - y[None, :, :]
+    dist = np.sqrt(np.sum(diff * diff, axis=-1))
+    scale = np.zeros_like(dist)
+    nz = dist > 0
+    scale[nz] = r * dist[nz] ** (r - 2.0)
+    return scale[:, :, None] * diff
+
+
+def dual_gradient(x, y, a, b, u, v, eps, r):
+    """Gradient of the dual function Eq. (27) at fixed scaling vectors (u, v)
+    with respect to the weights and the positions.
+
+    Eq. (27) is d = eps sum_i a_i (1/2 + log u_i) + eps sum_j b_j (1/2 + log v_j)
+    - eps sum_ij u_i k_ij v_j with k_ij = exp(-C_ij / eps), so
+      d/da_i = eps (1/2 + log u_i)   (the dual variable beta_i of Eq. (13))
+      d/db_j = eps (1/2 + log v_j)   (gamma_j)
+      d/dx_i = sum_j pi_ij dC_ij/dx_i,  pi = diag(u) K diag(v)  (Eq. (pi*))
+      d/dy_j = sum_i pi_ij dC_ij/dy_j = -sum_i pi_ij dC_ij/dx_i.
+    At the maximizer of Eq. (14) this is the gradient of the value s
+    (envelope theorem: the first-order conditions Eq. (S1) hold there).
+    Returns (grad_a, grad_b, grad_x, grad_y)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    K = gibbs_kernel(x, y, eps, r)
+    pi = transport_plan(np.asarray(u, dtype=np.float64), np.asarray(v, dtype=np.float64), K)
+    G = cost_gradient(x, y, r)
+    grad_x = np.einsum("ij,ijk->ik", pi, G)
+    grad_y = -np.einsum("ij,ijk->jk", pi, G)
+    grad_a = eps * (0.5 + np.log(u))
+    grad_b = eps * (0.5 + np.log(v))
+    return grad_a, grad_b, grad_x, grad_y
+
+
+def sinkhorn_divergence(x, a, y, b, eps, r, iters):
+    """Sinkhorn divergence sd(P, P~) = s(P, P~) - (s(P, P) + s(P~, P~)) / 2
+    (Remark "Entropy bias and Sinkhorn divergence"), each term the Alg. 1
+    result after ``iters`` iterations from u = v = 1."""
+    sxy = sinkhorn_dense(x, a, y, b, eps, r, iters)["s"]
+    sxx = sinkhorn_dense(x, a, x, a, eps, r, iters)["s"]
+    syy = sinkhorn_dense(y, b, y, b, eps, r, iters)["s"]
+    return sxy - 0.5 * (sxx + syy)
