@@ -174,8 +174,25 @@ int sk_kernel_apply(sk_plan* plan, int transpose, const double* in, double* out,
 int sk_solve(sk_plan* plan, int max_iter, double tol, int check_every,
              double* u_out, double* v_out, sk_result* res, void* stream);
 
-/* Gradient of the value with respect to weights and positions: not built yet,
- * always returns SK_ERR_UNSUPPORTED. */
+/*
+ * Gradient of the value with respect to the weights and the positions, at the
+ * plan's current scaling vectors (Prop. "dual representation", Eqs. (13),
+ * (27)): the gradient of the dual function Eq. (27) with u, v held fixed,
+ *   grad_a[i] = eps (1/2 + log u_i)           (the dual variable beta_i)
+ *   grad_b[j] = eps (1/2 + log v_j)           (gamma_j)
+ *   grad_x[i] = sum_j pi_ij dC_ij/dx_i,  grad_y[j] = sum_i pi_ij dC_ij/dy_j,
+ * with pi = diag(u) K diag(v) (Eq. (pi*)) and C_ij = ||x_i - y_j||^r.  After
+ * Sinkhorn has converged (u, v maximize Eq. (14)) this is the gradient of the
+ * value s returned by sk_solve (envelope theorem).  The weight gradient is
+ * defined up to adding c to grad_a and -c to grad_b (sum a = sum b).
+ * For r = 2 the position gradients use d + 1 fast summations per side:
+ *   grad_x[i] = 2 u_i (x_i (K v)_i - (K (v y))_i), with the plan's method.
+ * Layout: grad_a (n), grad_b (m), grad_x (n x d row-major), grad_y (m x d),
+ * caller point order, host or device memory; any may be NULL (skipped).
+ * Errors: SK_ERR_ARG for a NULL plan; SK_ERR_UNSUPPORTED if grad_x or grad_y
+ * is requested and r != 2 (other r need the fast summation of a different
+ * kernel); nothing is written then.  Synchronizes the plan's stream.
+ */
 int sk_grad(sk_plan* plan, double* grad_a, double* grad_b, double* grad_x, double* grad_y,
             void* stream);
 

@@ -863,6 +863,60 @@ void final_report(sk_plan* P, sk_result* res) {
     res->total_iters = P->iters;
 }
 
+// The dual variables of one cloud's marginal constraint, eps (1/2 + log u),
+// into a caller buffer (host or device) in caller order.
+void dual_variable_out(sk_plan* P, const Cloud& c, double* out) {
+    const bool host = !is_device_ptr(out);
+    k_dual_variable<<<nblk(c.n), 256, 0, P->ps>>>(c.scal, c.perm, c.n, P->eps, host ? c.stage : out);
+    CK(cudaGetLastError());
+    ++P->launches;
+    if (host) {
+        CK(cudaMemcpyAsync(out, c.stage, size_t(c.n) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+    }
+}
+
+// Gradient of the dual function Eq. (27) with respect to the positions of
+// cloud `dst` for r = 2, at the plan's current scaling vectors:
+//   grad_i = sum_j pi_ij 2 (x_i - y_j) = 2 u_i (x_i (K v)_i - (K (v y))_i),
+// with coordinates taken relative to the plan's centre.  d + 1 products
+// from `src` (weights v and v (y_t - c_t)); out is n x d row-major, caller order.
+template <typename T>
+void position_gradient(sk_plan* P, Cloud& src, Cloud& dst, double* out) {
+    const int d = P->d;
+    const int64_t n = dst.n;
+    const bool host = !is_device_ptr(out);
+    double *t0 = nullptr, *tt = nullptr, *w = nullptr, *g = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&t0), size_t(n) * sizeof(double), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&tt), size_t(n) * sizeof(double), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&w), size_t(src.n) * sizeof(double), P->ps));
+    if (host) CK(cudaMallocAsync(reinterpret_cast<void**>(&g), size_t(n) * d * sizeof(double), P->ps));
+    double* gdst = host ? g : out;
+    const double inv_nos = 1.0 / P->n_os, inv_s = 1.0 / P->scale;
+    Epilogue e = make_epilogue(P, EPI_APPLY, dst, 0, t0);
+    e.perm = nullptr;   // sorted order
+    product<T>(P, src, src.scal, dst, e);
+    for (int t = 0; t < d; ++t) {
+        launch_weighted_coord<T>(src.scal, src.coord[t], src.n, inv_nos, inv_s, w, P->ps);
+        CK(cudaGetLastError());
+        ++P->launches;
+        Epilogue et = make_epilogue(P, EPI_APPLY, dst, 0, tt);
+        et.perm = nullptr;
+        product<T>(P, src, w, dst, et);
+        launch_position_gradient<T>(dst.scal, dst.coord[t], t0, tt, dst.perm, n, d, t, inv_nos, inv_s, gdst, P->ps);
+        CK(cudaGetLastError());
+        ++P->launches;
+    }
+    if (host) {
+        CK(cudaMemcpyAsync(out, g, size_t(n) * d * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+    }
+    CK(cudaFreeAsync(t0, P->ps));
+    CK(cudaFreeAsync(tt, P->ps));
+    CK(cudaFreeAsync(w, P->ps));
+    if (g) CK(cudaFreeAsync(g, P->ps));
+}
+
 void write_out(sk_plan* P, const Cloud& c, const double* sorted, double* out) {
     if (!out) return;
     if (is_device_ptr(out)) {
@@ -1235,9 +1289,26 @@ int sk_solve(sk_plan* P, int max_iter, double tol, int check_every, double* u_ou
     return rc;
 }
 
-int sk_grad(sk_plan* P, double*, double*, double*, double*, void*) {
+int sk_grad(sk_plan* P, double* grad_a, double* grad_b, double* grad_x, double* grad_y, void* stream) {
     if (!P) return SK_ERR_ARG;
-    return SK_ERR_UNSUPPORTED;
+    if ((grad_x || grad_y) && P->r != 2.0) return SK_ERR_UNSUPPORTED;
+    try {
+        enter(P, stream);
+        if (grad_a) dual_variable_out(P, P->X, grad_a);
+        if (grad_b) dual_variable_out(P, P->Y, grad_b);
+        if (P->precision == SK_FP32) {
+            if (grad_x) position_gradient<float>(P, P->Y, P->X, grad_x);
+            if (grad_y) position_gradient<float>(P, P->X, P->Y, grad_y);
+        } else {
+            if (grad_x) position_gradient<double>(P, P->Y, P->X, grad_x);
+            if (grad_y) position_gradient<double>(P, P->X, P->Y, grad_y);
+        }
+        leave(P, stream);
+        CK(cudaStreamSynchronize(P->ps));
+    } catch (const Fail& f) {
+        return fail_code(f);
+    }
+    return SK_OK;
 }
 
 int sk_get_state(sk_plan* P, double* u, double* v, int* iters) {

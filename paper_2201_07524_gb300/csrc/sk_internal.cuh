@@ -77,7 +77,7 @@ enum EpiMode { EPI_APPLY = 0, EPI_UPDATE = 1, EPI_RESID = 2 };
 struct Epilogue {
     int mode = EPI_APPLY;
     int64_t n = 0;
-    const int* perm = nullptr;   // APPLY: out[perm[i]] = t_i
+    const int* perm = nullptr;   // APPLY: out[perm[i]] = t_i (out[i] = t_i when null)
     double* out = nullptr;
     double* t_store = nullptr;   // UPDATE / RESID: t_store[i] = t_i
     const double* marg = nullptr;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t
                                           double& sq, double& bad, double& dot) {
     if (e.add) t += e.add[i];
     if (e.mode == EPI_APPLY) {
-        e.out[e.perm[i]] = t;
+        e.out[e.perm ? e.perm[i] : i] = t;
         return;
     }
     const double q = e.scal[i];
@@ -300,7 +300,7 @@ __device__ __forceinline__ void epi_point_pre(const Epilogue& e, int64_t i, doub
                                               double& sq, double& bad, double& dot) {
     if (e.add) t += e.add[i];
     if (e.mode == EPI_APPLY) {
-        e.out[e.perm[i]] = t;
+        e.out[e.perm ? e.perm[i] : i] = t;
         return;
     }
     const double r = fma(q, t, -a);

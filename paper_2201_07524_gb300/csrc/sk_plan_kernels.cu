@@ -532,4 +532,58 @@ template void launch_build_mult<double>(double*, int, int, const double*, double
 template void launch_twiddles<float>(void*, int, cudaStream_t);
 template void launch_twiddles<double>(void*, int, cudaStream_t);
 
+// ------------------------------------------------------------ gradient
+// Dual variable of a marginal constraint from its scaling vector, in caller
+// order: beta_i = eps (1/2 + log u_i), the substitution alpha_i =
+// exp(lambda beta_i - 1/2) of Eq. (27) inverted (lambda = 1 / eps).
+__global__ void k_dual_variable(const double* __restrict__ scal, const int* __restrict__ perm, int64_t n, double eps,
+                                double* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = eps * (0.5 + log(scal[i]));
+}
+
+// w_j = v_j (y_jt - c_t): a scaling vector times one coordinate relative to
+// the plan's centre, from grid units u = n_os (s (y - c) + 1/2).
+template <typename T>
+__global__ void k_weighted_coord(const double* __restrict__ scal, const T* __restrict__ coord, int64_t n,
+                                 double inv_nos, double inv_s, double* __restrict__ w) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = scal[i] * ((double(coord[i]) * inv_nos - 0.5) * inv_s);
+}
+
+// Position gradient for r = 2, coordinate t, in caller order (row-major n x d):
+// sum_j pi_ij 2 (x_it - y_jt) = 2 u_i ((x_it - c_t) (K v)_i - (K (v (y_t - c_t)))_i).
+template <typename T>
+__global__ void k_position_gradient(const double* __restrict__ scal, const T* __restrict__ coord,
+                                    const double* __restrict__ t0, const double* __restrict__ tt,
+                                    const int* __restrict__ perm, int64_t n, int d, int t, double inv_nos,
+                                    double inv_s, double* __restrict__ grad) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xc = (double(coord[i]) * inv_nos - 0.5) * inv_s;
+    grad[int64_t(perm[i]) * d + t] = 2.0 * scal[i] * (xc * t0[i] - tt[i]);
+}
+
+template <typename T>
+void launch_weighted_coord(const double* scal, const void* coord, int64_t n, double inv_nos, double inv_s, double* w,
+                           cudaStream_t s) {
+    k_weighted_coord<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(scal, static_cast<const T*>(coord), n, inv_nos, inv_s,
+                                                                  w);
+}
+
+template <typename T>
+void launch_position_gradient(const double* scal, const void* coord, const double* t0, const double* tt,
+                              const int* perm, int64_t n, int d, int t, double inv_nos, double inv_s, double* grad,
+                              cudaStream_t s) {
+    k_position_gradient<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(scal, static_cast<const T*>(coord), t0, tt, perm,
+                                                                     n, d, t, inv_nos, inv_s, grad);
+}
+
+template void launch_weighted_coord<float>(const double*, const void*, int64_t, double, double, double*, cudaStream_t);
+template void launch_weighted_coord<double>(const double*, const void*, int64_t, double, double, double*, cudaStream_t);
+template void launch_position_gradient<float>(const double*, const void*, const double*, const double*, const int*,
+                                              int64_t, int, int, double, double, double*, cudaStream_t);
+template void launch_position_gradient<double>(const double*, const void*, const double*, const double*, const int*,
+                                               int64_t, int, int, double, double, double*, cudaStream_t);
+
 }  // namespace sk

@@ -25,6 +25,14 @@ template <typename T>
 void launch_gather_points(const int* perm, int64_t n, int d, T* const in[3], T* const out[3], cudaStream_t s);
 __global__ void k_bin_starts(const int* key_start, int nbins, int bvol, int* bin_start);
 __global__ void k_count_tasks(const int* bin_start, int nbins, int maxpts, int ncol, int* ntask);
+__global__ void k_dual_variable(const double* scal, const int* perm, int64_t n, double eps, double* out);
+template <typename T>
+void launch_weighted_coord(const double* scal, const void* coord, int64_t n, double inv_nos, double inv_s, double* w,
+                           cudaStream_t s);
+template <typename T>
+void launch_position_gradient(const double* scal, const void* coord, const double* t0, const double* tt,
+                              const int* perm, int64_t n, int d, int t, double inv_nos, double inv_s, double* grad,
+                              cudaStream_t s);
 __global__ void k_col_counts(const int* key_start, int nbins, int bvol, int ncol, int bz, int* count);
 __global__ void k_fill_tasks(const int* ntask_off, int nbins, int ncol, int* task);
 __global__ void k_count_subs(const int* bin_start, int nbins, int maxpts, int* nsub);

@@ -217,7 +217,11 @@ def sk_solve(plan, max_iter, tol=0.0, check_every=10, u_out=None, v_out=None, re
 
 
 def sk_grad(plan, grad_a=None, grad_b=None, grad_x=None, grad_y=None, stream=None):
-    return _lib.sk_grad(plan.handle, _ptr(grad_a), _ptr(grad_b), _ptr(grad_x), _ptr(grad_y), _stream(stream))
+    """Gradient of the value at the plan's current state (see include/sk.h);
+    grad_x / grad_y are n x d / m x d row-major."""
+    _check(_lib.sk_grad(plan.handle, _ptr(grad_a, plan.n, "grad_a"), _ptr(grad_b, plan.m, "grad_b"),
+                        _ptr(grad_x, plan.n * plan.d, "grad_x"), _ptr(grad_y, plan.m * plan.d, "grad_y"),
+                        _stream(stream)), "sk_grad")
 
 
 def sk_get_state(plan, u=None, v=None):

@@ -283,12 +283,6 @@ def test_input_errors_are_reported():
     assert e.value.status == sk.SK_ERR_WEIGHTS
 
 
-def test_grad_reports_unsupported():
-    x = wl.uniform_ball(20, 2, 0.2, 33)
-    plan = plan_for(x, x)
-    assert sk.sk_grad(plan) == sk.SK_ERR_UNSUPPORTED
-
-
 def test_launch_count_and_stage_timing():
     x = wl.uniform_ball(3000, 3, 0.2, 34)
     y = wl.uniform_ball(3000, 3, 0.2, 35)
