@@ -196,6 +196,20 @@ int sk_solve(sk_plan* plan, int max_iter, double tol, int check_every,
 int sk_grad(sk_plan* plan, double* grad_a, double* grad_b, double* grad_x, double* grad_y,
             void* stream);
 
+/*
+ * Sinkhorn divergence (Remark "Entropy bias and Sinkhorn divergence"; its
+ * NFFT form after Alg. 3): sd = s(P, P~) - s(P, P) / 2 - s(P~, P~) / 2.
+ * Builds and solves three plans with the arguments of sk_init and sk_solve
+ * (the same params, max_iter and tol for each), then destroys them.
+ * host_out[4] (host memory) receives sd, s(P, P~), s(P, P), s(P~, P~).
+ * Returns the first error of sk_init / sk_solve (nothing written then), or
+ * SK_ERR_NOT_CONVERGED if a solve with tol > 0 reached max_iter (values
+ * written), else SK_OK.  Synchronizes `stream`.
+ */
+int sk_divergence(int d, int64_t n, const double* x, const double* a, int64_t m, const double* y,
+                  const double* b, double eps, double r, const sk_nfft_params* prm, int max_iter,
+                  double tol, double* host_out, void* stream);
+
 /* Copy the scaling vectors out (caller order; either pointer may be NULL) and the
  * iteration count. Synchronizes. */
 int sk_get_state(sk_plan* plan, double* u, double* v, int* iters);

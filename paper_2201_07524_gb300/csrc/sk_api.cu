@@ -1311,6 +1311,36 @@ int sk_grad(sk_plan* P, double* grad_a, double* grad_b, double* grad_x, double* 
     return SK_OK;
 }
 
+int sk_divergence(int d, int64_t n, const double* x, const double* a, int64_t m, const double* y, const double* b,
+                  double eps, double r, const sk_nfft_params* prm, int max_iter, double tol, double* host_out,
+                  void* stream) {
+    if (!host_out || max_iter < 0) return SK_ERR_ARG;
+    // s(P, P~), s(P, P), s(P~, P~): three plans, each solved like sk_solve
+    const double* cx[3] = {x, x, y};
+    const double* ca[3] = {a, a, b};
+    const double* cy[3] = {y, x, y};
+    const double* cb[3] = {b, a, b};
+    const int64_t cn[3] = {n, n, m}, cm[3] = {m, n, m};
+    double val[3] = {0.0, 0.0, 0.0};
+    int worst = SK_OK;
+    for (int k = 0; k < 3; ++k) {
+        sk_plan* P = nullptr;
+        int st = sk_init(&P, d, cn[k], cx[k], ca[k], cm[k], cy[k], cb[k], eps, r, prm, stream);
+        if (st != SK_OK) return st;
+        sk_result res{};
+        st = sk_solve(P, max_iter, tol, 0, nullptr, nullptr, &res, stream);
+        sk_destroy(P);
+        if (st != SK_OK && st != SK_ERR_NOT_CONVERGED) return st;
+        if (st == SK_ERR_NOT_CONVERGED) worst = st;
+        val[k] = res.s;
+    }
+    host_out[0] = val[0] - 0.5 * (val[1] + val[2]);
+    host_out[1] = val[0];
+    host_out[2] = val[1];
+    host_out[3] = val[2];
+    return worst;
+}
+
 int sk_get_state(sk_plan* P, double* u, double* v, int* iters) {
     if (!P) return SK_ERR_ARG;
     try {

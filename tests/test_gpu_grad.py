@@ -120,3 +120,34 @@ def test_grad_positions_need_r2_weights_do_not():
     u = np.ones(n)
     assert np.allclose(ga.cpu().numpy(), 0.05 * (0.5 + np.log(u)), rtol=0, atol=1e-15)
     sk.sk_grad(plan)    # nothing requested: a no-op
+
+
+# ------------------------------------------------------------ divergence
+def test_divergence_matches_oracle():
+    # FP64 fast summation: each value to 1e-5 relative (the Sinkhorn-value
+    # target), the divergence to 1e-5 of the largest of them
+    n, m, d, eps, iters = 600, 450, 2, 0.05, 100
+    x = wl.uniform_ball(n, d, 0.2, 101)
+    y = wl.gaussian_mixture(m, d, 4, 0.05, 0.1, 102)
+    a, b = wl.dirichlet_weights(n, 103), wl.dirichlet_weights(m, 104)
+    prm = sk.sk_default_params(precision=sk.SK_FP64)
+    sd, sxy, sxx, syy = sk.sk_divergence(cuda(x), cuda(a), cuda(y), cuda(b), eps, 2.0, iters, params=prm)
+    ref = [osk.sinkhorn_dense(p, wp, q, wq, eps, 2.0, iters)["s"]
+           for p, wp, q, wq in ((x, a, y, b), (x, a, x, a), (y, b, y, b))]
+    for got, want in zip((sxy, sxx, syy), ref):
+        assert abs(got - want) <= 1e-5 * abs(want)
+    scale = max(abs(v) for v in ref)
+    assert abs(sd - osk.sinkhorn_divergence(x, a, y, b, eps, 2.0, iters)) <= 1e-5 * scale
+    assert sd > 0.0
+
+
+def test_divergence_of_a_measure_with_itself_is_zero():
+    n, d = 800, 3
+    x = wl.uniform_ball(n, d, 0.2, 111)
+    a = wl.dirichlet_weights(n, 112)
+    sd, sxy, sxx, syy = sk.sk_divergence(cuda(x), cuda(a), cuda(x), cuda(a), 0.05, 2.0, 50,
+                                         params=sk.sk_default_params(precision=sk.SK_FP32, N=32))
+    # the three plans see the same inputs; spreading adds with atomics, so
+    # the values agree to FP32 rounding, not bit for bit
+    assert abs(sxy - sxx) <= 1e-6 * abs(sxx) and abs(sxx - syy) <= 1e-6 * abs(sxx)
+    assert abs(sd) <= 1e-6 * abs(sxx)
