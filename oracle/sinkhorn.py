@@ -214,3 +214,23 @@ def sinkhorn_divergence(x, a, y, b, eps, r, iters):
     sxx = sinkhorn_dense(x, a, x, a, eps, r, iters)["s"]
     syy = sinkhorn_dense(y, b, y, b, eps, r, iters)["s"]
     return sxy - 0.5 * (sxx + syy)
+
+
+def sinkhorn_divergence_gradient(x, a, y, b, eps, r, iters):
+    """Gradient of sd(P, P~) (Remark "Entropy bias and Sinkhorn divergence")
+    with respect to a, b, x, y, from the dual gradients of its three terms at
+    their Alg. 1 states after ``iters`` iterations.  In s(P, P) every point is
+    both a source and a target, so its gradient is the sum of the two sides'.
+    Returns (grad_a, grad_b, grad_x, grad_y)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    o = sinkhorn_dense(x, a, y, b, eps, r, iters)
+    ga, gb, gx, gy = dual_gradient(x, y, a, b, o["u"], o["v"], eps, r)
+    ox = sinkhorn_dense(x, a, x, a, eps, r, iters)
+    xa1, xa2, xx1, xx2 = dual_gradient(x, x, a, a, ox["u"], ox["v"], eps, r)
+    oy = sinkhorn_dense(y, b, y, b, eps, r, iters)
+    yb1, yb2, yy1, yy2 = dual_gradient(y, y, b, b, oy["u"], oy["v"], eps, r)
+    return (ga - 0.5 * (xa1 + xa2), gb - 0.5 * (yb1 + yb2),
+            gx - 0.5 * (xx1 + xx2), gy - 0.5 * (yy1 + yy2))

@@ -137,3 +137,38 @@ def test_divergence_single_points_and_symmetry():
 def test_divergence_is_nonnegative(seed):
     x, y, a, b = _problem(6, 5, 2, seed)
     assert osk.sinkhorn_divergence(x, a, y, b, 0.05, 2.0, 500) > 0.0
+
+
+def test_divergence_gradient_matches_differences_at_convergence():
+    x, y, a, b = _problem(4, 3, 2, 71)
+    eps, r, h, it = 0.3, 2.0, 1e-5, 3000
+    ga, gb, gx, gy = osk.sinkhorn_divergence_gradient(x, a, y, b, eps, r, it)
+    for arr, g in ((x, gx), (y, gy)):
+        for idx in np.ndindex(arr.shape):
+            old = arr[idx]
+            arr[idx] = old + h
+            sp = osk.sinkhorn_divergence(x, a, y, b, eps, r, it)
+            arr[idx] = old - h
+            sm = osk.sinkhorn_divergence(x, a, y, b, eps, r, it)
+            arr[idx] = old
+            assert abs((sp - sm) / (2 * h) - g[idx]) < 1e-7
+    rng = np.random.default_rng(72)
+    for w, g, first in ((a, ga, True), (b, gb, False)):
+        dlt = rng.standard_normal(len(w))
+        dlt -= dlt.mean()
+        if first:
+            sp = osk.sinkhorn_divergence(x, w + h * dlt, y, b, eps, r, it)
+            sm = osk.sinkhorn_divergence(x, w - h * dlt, y, b, eps, r, it)
+        else:
+            sp = osk.sinkhorn_divergence(x, a, y, w + h * dlt, eps, r, it)
+            sm = osk.sinkhorn_divergence(x, a, y, w - h * dlt, eps, r, it)
+        assert abs((sp - sm) / (2 * h) - float(g @ dlt)) < 1e-7
+
+
+def test_divergence_gradient_vanishes_at_equal_measures():
+    # sd(P, P~) >= 0 with equality at P~ = P: a minimum, so the position
+    # gradient with respect to y vanishes there
+    x, _, a, _ = _problem(5, 5, 2, 81)
+    _, gb, gx, gy = osk.sinkhorn_divergence_gradient(x, a, x.copy(), a.copy(), 0.2, 2.0, 2000)
+    assert np.max(np.abs(gy)) < 1e-12 and np.max(np.abs(gx)) < 1e-12
+    assert np.max(np.abs(gb - gb.mean())) < 1e-12
