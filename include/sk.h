@@ -202,13 +202,20 @@ int sk_grad(sk_plan* plan, double* grad_a, double* grad_b, double* grad_x, doubl
  * Builds and solves three plans with the arguments of sk_init and sk_solve
  * (the same params, max_iter and tol for each), then destroys them.
  * host_out[4] (host memory) receives sd, s(P, P~), s(P, P), s(P~, P~).
- * Returns the first error of sk_init / sk_solve (nothing written then), or
- * SK_ERR_NOT_CONVERGED if a solve with tol > 0 reached max_iter (values
- * written), else SK_OK.  Synchronizes `stream`.
+ * grad_a (n), grad_b (m), grad_x (n x d), grad_y (m x d), each optional
+ * (NULL), host or device memory, caller order, receive the gradient of sd:
+ * the sk_grad gradients of the three terms at their final states, the self
+ * terms contributing both their source and target sides (every point of
+ * s(P, P) is both).  Positions need r = 2 (else SK_ERR_UNSUPPORTED, nothing
+ * written).  Returns the first error of sk_init / sk_solve / sk_grad
+ * (nothing written then), SK_ERR_NOMEM if the gradient buffers cannot be
+ * allocated, or SK_ERR_NOT_CONVERGED if a solve with tol > 0 reached
+ * max_iter (values written), else SK_OK.  Synchronizes `stream`.
  */
 int sk_divergence(int d, int64_t n, const double* x, const double* a, int64_t m, const double* y,
                   const double* b, double eps, double r, const sk_nfft_params* prm, int max_iter,
-                  double tol, double* host_out, void* stream);
+                  double tol, double* host_out, double* grad_a, double* grad_b, double* grad_x,
+                  double* grad_y, void* stream);
 
 /* Copy the scaling vectors out (caller order; either pointer may be NULL) and the
  * iteration count. Synchronizes. */

@@ -1313,8 +1313,11 @@ int sk_grad(sk_plan* P, double* grad_a, double* grad_b, double* grad_x, double* 
 
 int sk_divergence(int d, int64_t n, const double* x, const double* a, int64_t m, const double* y, const double* b,
                   double eps, double r, const sk_nfft_params* prm, int max_iter, double tol, double* host_out,
-                  void* stream) {
-    if (!host_out || max_iter < 0) return SK_ERR_ARG;
+                  double* grad_a, double* grad_b, double* grad_x, double* grad_y, void* stream) {
+    if (!host_out || max_iter < 0 || d < 1 || d > 3 || n < 1 || m < 1) return SK_ERR_ARG;
+    if ((grad_x || grad_y) && r != 2.0) return SK_ERR_UNSUPPORTED;
+    const bool want_grad = grad_a || grad_b || grad_x || grad_y;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     // s(P, P~), s(P, P), s(P~, P~): three plans, each solved like sk_solve
     const double* cx[3] = {x, x, y};
     const double* ca[3] = {a, a, b};
@@ -1323,22 +1326,84 @@ int sk_divergence(int d, int64_t n, const double* x, const double* a, int64_t m,
     const int64_t cn[3] = {n, n, m}, cm[3] = {m, n, m};
     double val[3] = {0.0, 0.0, 0.0};
     int worst = SK_OK;
+    // device accumulators of the gradient (caller order) and one term's parts
+    std::vector<void*> mem;
+    auto dev = [&](int64_t count) -> double* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, size_t(std::max<int64_t>(count, 1)) * sizeof(double)) != cudaSuccess) return nullptr;
+        mem.push_back(p);
+        return static_cast<double*>(p);
+    };
+    auto release = [&]() {
+        for (void* p : mem) cudaFree(p);
+        mem.clear();
+    };
+    double *acc_a = nullptr, *acc_b = nullptr, *acc_x = nullptr, *acc_y = nullptr;
+    double *t1 = nullptr, *t2 = nullptr, *tx1 = nullptr, *tx2 = nullptr;
+    if (want_grad) {
+        const int64_t nm = std::max(n, m);
+        acc_a = dev(n), acc_b = dev(m), acc_x = dev(n * d), acc_y = dev(m * d);
+        t1 = dev(nm), t2 = dev(nm), tx1 = dev(nm * d), tx2 = dev(nm * d);
+        if (!acc_a || !acc_b || !acc_x || !acc_y || !t1 || !t2 || !tx1 || !tx2) {
+            release();
+            return SK_ERR_NOMEM;
+        }
+    }
     for (int k = 0; k < 3; ++k) {
         sk_plan* P = nullptr;
         int st = sk_init(&P, d, cn[k], cx[k], ca[k], cm[k], cy[k], cb[k], eps, r, prm, stream);
-        if (st != SK_OK) return st;
+        if (st != SK_OK) {
+            release();
+            return st;
+        }
         sk_result res{};
         st = sk_solve(P, max_iter, tol, 0, nullptr, nullptr, &res, stream);
+        if (st == SK_OK || st == SK_ERR_NOT_CONVERGED) {
+            if (st == SK_ERR_NOT_CONVERGED) worst = st;
+            val[k] = res.s;
+            if (want_grad) {
+                // s(P, P~) -> the accumulators; the self terms subtract half of
+                // both sides' gradients (every point is source and target)
+                const bool posg = grad_x || grad_y;
+                if (k == 0)
+                    st = sk_grad(P, acc_a, acc_b, posg ? acc_x : nullptr, posg ? acc_y : nullptr, stream);
+                else
+                    st = sk_grad(P, t1, t2, posg ? tx1 : nullptr, posg ? tx2 : nullptr, stream);
+                if (st == SK_OK && k > 0) {
+                    const int64_t c = cn[k];
+                    k_sub_half_sum<<<unsigned((c + 255) / 256), 256, 0, cs>>>(k == 1 ? acc_a : acc_b, t1, t2, c);
+                    if (posg)
+                        k_sub_half_sum<<<unsigned((c * d + 255) / 256), 256, 0, cs>>>(k == 1 ? acc_x : acc_y, tx1,
+                                                                                      tx2, c * d);
+                    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(cs) != cudaSuccess)
+                        st = SK_ERR_CUDA;
+                }
+            }
+        }
         sk_destroy(P);
-        if (st != SK_OK && st != SK_ERR_NOT_CONVERGED) return st;
-        if (st == SK_ERR_NOT_CONVERGED) worst = st;
-        val[k] = res.s;
+        if (st != SK_OK && st != SK_ERR_NOT_CONVERGED) {
+            release();
+            return st;
+        }
+    }
+    int rc = worst;
+    if (want_grad) {
+        const double* src[4] = {acc_a, acc_b, acc_x, acc_y};
+        double* dst[4] = {grad_a, grad_b, grad_x, grad_y};
+        const int64_t cnt[4] = {n, m, n * d, m * d};
+        for (int k = 0; k < 4; ++k)
+            if (dst[k] && cudaMemcpyAsync(dst[k], src[k], size_t(cnt[k]) * sizeof(double), cudaMemcpyDefault, cs) !=
+                              cudaSuccess)
+                rc = SK_ERR_CUDA;
+        if (cudaStreamSynchronize(cs) != cudaSuccess) rc = SK_ERR_CUDA;
+        release();
+        if (rc == SK_ERR_CUDA) return rc;
     }
     host_out[0] = val[0] - 0.5 * (val[1] + val[2]);
     host_out[1] = val[0];
     host_out[2] = val[1];
     host_out[3] = val[2];
-    return worst;
+    return rc;
 }
 
 int sk_get_state(sk_plan* P, double* u, double* v, int* iters) {

@@ -533,6 +533,14 @@ template void launch_twiddles<float>(void*, int, cudaStream_t);
 template void launch_twiddles<double>(void*, int, cudaStream_t);
 
 // ------------------------------------------------------------ gradient
+// acc[i] -= (p[i] + q[i]) / 2: a self term's two sides in the divergence's gradient.
+__global__ void k_sub_half_sum(double* __restrict__ acc, const double* __restrict__ p, const double* __restrict__ q,
+                               int64_t n) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) acc[i] -= 0.5 * (p[i] + q[i]);
+}
+
+
 // Dual variable of a marginal constraint from its scaling vector, in caller
 // order: beta_i = eps (1/2 + log u_i), the substitution alpha_i =
 // exp(lambda beta_i - 1/2) of Eq. (27) inverted (lambda = 1 / eps).

@@ -25,6 +25,7 @@ template <typename T>
 void launch_gather_points(const int* perm, int64_t n, int d, T* const in[3], T* const out[3], cudaStream_t s);
 __global__ void k_bin_starts(const int* key_start, int nbins, int bvol, int* bin_start);
 __global__ void k_count_tasks(const int* bin_start, int nbins, int maxpts, int ncol, int* ntask);
+__global__ void k_sub_half_sum(double* acc, const double* p, const double* q, int64_t n);
 __global__ void k_dual_variable(const double* scal, const int* perm, int64_t n, double eps, double* out);
 template <typename T>
 void launch_weighted_coord(const double* scal, const void* coord, int64_t n, double inv_nos, double inv_s, double* w,

@@ -68,7 +68,7 @@ _SIGS = {
     "sk_grad": (ctypes.c_int, [_P, _D, _D, _D, _D, _S]),
     "sk_divergence": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _D, _D, ctypes.c_int64, _D, _D, ctypes.c_double,
                                      ctypes.c_double, ctypes.POINTER(sk_nfft_params), ctypes.c_int, ctypes.c_double,
-                                     _D, _S]),
+                                     _D, _D, _D, _D, _D, _S]),
     "sk_get_state": (ctypes.c_int, [_P, _D, _D, ctypes.POINTER(ctypes.c_int)]),
     "sk_set_state": (ctypes.c_int, [_P, _D, _D, ctypes.c_int]),
     "sk_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(sk_info)]),
@@ -227,15 +227,17 @@ def sk_grad(plan, grad_a=None, grad_b=None, grad_x=None, grad_y=None, stream=Non
                         _stream(stream)), "sk_grad")
 
 
-def sk_divergence(x, a, y, b, eps, r, max_iter, tol=0.0, params=None, stream=None):
-    """Returns (sd, s_xy, s_xx, s_yy); see include/sk.h."""
+def sk_divergence(x, a, y, b, eps, r, max_iter, tol=0.0, params=None, grad_a=None, grad_b=None, grad_x=None,
+                  grad_y=None, stream=None):
+    """Returns (sd, s_xy, s_xx, s_yy) and fills the optional gradients; see include/sk.h."""
     n, d = x.shape
     m = y.shape[0]
     out = np.zeros(4)
     prm = ctypes.byref(params) if params is not None else None
     st = _lib.sk_divergence(int(d), int(n), _ptr(x, n * d, "x"), _ptr(a, n, "a"), int(m), _ptr(y, m * d, "y"),
                             _ptr(b, m, "b"), float(eps), float(r), prm, int(max_iter), float(tol), out.ctypes.data,
-                            _stream(stream))
+                            _ptr(grad_a, n, "grad_a"), _ptr(grad_b, m, "grad_b"), _ptr(grad_x, n * d, "grad_x"),
+                            _ptr(grad_y, m * d, "grad_y"), _stream(stream))
     if st not in (SK_OK, SK_ERR_NOT_CONVERGED):
         _check(st, "sk_divergence")
     return tuple(float(v) for v in out)

@@ -151,3 +151,69 @@ def test_divergence_of_a_measure_with_itself_is_zero():
     # the values agree to FP32 rounding, not bit for bit
     assert abs(sxy - sxx) <= 1e-6 * abs(sxx) and abs(sxx - syy) <= 1e-6 * abs(sxx)
     assert abs(sd) <= 1e-6 * abs(sxx)
+
+
+def test_divergence_gradient_matches_oracle():
+    n, m, d, eps, iters = 500, 400, 2, 0.05, 300
+    x = wl.gaussian_mixture(n, d, 4, 0.05, 0.1, 121)
+    y = wl.uniform_ball(m, d, 0.2, 122)
+    a, b = wl.dirichlet_weights(n, 123), wl.dirichlet_weights(m, 124)
+    g = [torch.zeros(k, dtype=torch.float64, device="cuda") for k in (n, m, n * d, m * d)]
+    sk.sk_divergence(cuda(x), cuda(a), cuda(y), cuda(b), eps, 2.0, iters,
+                     params=sk.sk_default_params(precision=sk.SK_FP64), grad_a=g[0], grad_b=g[1], grad_x=g[2],
+                     grad_y=g[3])
+    ga, gb, gx, gy = (t.cpu().numpy() for t in g)
+    ea, eb, ex, ey = osk.sinkhorn_divergence_gradient(x, a, y, b, eps, 2.0, iters)
+    # the weight gradients are defined up to a constant on each side's simplex
+    for got, want in ((ga, ea), (gb, eb)):
+        assert np.max(np.abs((got - got.mean()) - (want - want.mean()))) <= 1e-6 * eps
+    o = osk.sinkhorn_dense(x, a, y, b, eps, 2.0, iters)
+    _, _, tx, ty = osk.dual_gradient(x, y, a, b, o["u"], o["v"], eps, 2.0)
+    scale = max(np.max(np.abs(tx)), np.max(np.abs(ty)))     # one term's size
+    assert np.max(np.abs(gx.reshape(n, d) - ex)) <= 1e-5 * scale
+    assert np.max(np.abs(gy.reshape(m, d) - ey)) <= 1e-5 * scale
+
+
+def test_divergence_gradient_finite_differences():
+    # the differentiation check on Gaussian-mixture clouds in 3-D (r = 2,
+    # eps = 0.02): central differences with step 1e-4 of the divergence,
+    # every solve converged (row residual <= 1e-13), on 64 random position
+    # coordinates and two simplex directions of the weights.  FP64 plans.
+    n = m = 1024
+    d, eps, h = 3, 0.02, 1e-4
+    x = wl.gaussian_mixture(n, d, 8, 0.03, 0.15, 131)
+    y = wl.uniform_ball(m, d, 0.2, 132)
+    a, b = wl.uniform_weights(n), wl.uniform_weights(m)
+    prm = sk.sk_default_params(precision=sk.SK_FP64)
+
+    def sd(xx, aa, yy, bb, grads=None):
+        kw = {} if grads is None else dict(grad_a=grads[0], grad_b=grads[1], grad_x=grads[2], grad_y=grads[3])
+        return sk.sk_divergence(cuda(xx), cuda(aa), cuda(yy), cuda(bb), eps, 2.0, 20000, tol=1e-13, params=prm,
+                                **kw)[0]
+
+    g = [np.zeros(k) for k in (n, m, n * d, m * d)]
+    sd(x, a, y, b, g)
+    gx, gy = g[2].reshape(n, d), g[3].reshape(m, d)
+    rng = np.random.default_rng(133)
+    worst = 0.0
+    for k in range(64):
+        arr, grad = (x, gx) if k % 2 == 0 else (y, gy)
+        i, t = int(rng.integers(len(arr))), int(rng.integers(d))
+        old = arr[i, t]
+        arr[i, t] = old + h
+        sp = sd(x, a, y, b)
+        arr[i, t] = old - h
+        sm = sd(x, a, y, b)
+        arr[i, t] = old
+        worst = max(worst, abs((sp - sm) / (2 * h) - grad[i, t]))
+    scale = max(np.max(np.abs(gx)), np.max(np.abs(gy)))
+    assert worst <= 1e-3 * scale
+    for w, grad, first in ((a, g[0], True), (b, g[1], False)):
+        dlt = rng.standard_normal(len(w))
+        dlt -= dlt.mean()
+        dlt *= 1e-3 * w.min() / np.max(np.abs(dlt))   # keeps the weights positive
+        if first:
+            sp, sm = sd(x, a + dlt, y, b), sd(x, a - dlt, y, b)
+        else:
+            sp, sm = sd(x, a, y, b + dlt), sd(x, a, y, b - dlt)
+        assert abs((sp - sm) / 2 - float(grad @ dlt)) <= 1e-3 * abs(float(grad @ dlt)) + 1e-12
