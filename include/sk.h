@@ -60,11 +60,16 @@ typedef struct sk_plan sk_plan;
  * Parameters of the fast summation (Sec. 4.1).  The paper leaves all of them
  * open; sk_default_params() fills in the values this library is tested with.
  *   N        bandwidth: Fourier coefficients b_k for k in I_N = {-N/2..N/2-1}^d
- *            (Eq. (ansatz_NFFT)); even, >= 8.
+ *            (Eq. (ansatz_NFFT)); even, >= 8.  N <= 0: chosen by sk_init once
+ *            the geometry is known, as the smallest power of two >= 16 whose
+ *            Fourier tail of the regularized kernel (one-dimensional slice) is
+ *            below 1e-6 / d (SK_FP32) or 1e-10 / d (SK_FP64) of K(0).
  *   sigma    oversampling; the FFT grid has n_os = sigma*N points per dimension,
  *            which must be a power of two, 16 <= n_os <= 1024 (4096 for d = 1).
  *   m_w      Kaiser-Bessel window cutoff: 2*m_w taps per dimension, 2 <= m_w <= 8,
- *            n_os >= 4*(m_w+1).
+ *            n_os >= 4*(m_w+1).  m_w <= 0: the smallest m whose window error
+ *            estimate 4 pi (1-1/sigma)^(1/4) exp(-2 pi m sqrt(1-1/sigma)) meets
+ *            the same target (at most 5 in 3-D).
  *   p        smoothness of the regularized kernel: the boundary polynomial K_B and
  *            the near-field polynomial K_I match p-1 derivatives, 2 <= p <= 12.
  *   eps_B    width of the boundary region (torus units): L = 1/2 - eps_B, 0 < eps_B < 1/2.
@@ -173,6 +178,21 @@ int sk_kernel_apply(sk_plan* plan, int transpose, const double* in, double* out,
  */
 int sk_solve(sk_plan* plan, int max_iter, double tol, int check_every,
              double* u_out, double* v_out, sk_result* res, void* stream);
+
+/*
+ * Solve `count` independent plans together: one Sinkhorn iteration (Alg. 3)
+ * of every plan is captured once into a single CUDA graph, the plans'
+ * iterations as parallel branches (they share no memory), and the graph is
+ * replayed max_iter times, so the kernels of small problems run side by side
+ * on the GPU.  Each plan's state, iteration count and results then are those
+ * of sk_solve(plan, max_iter, 0, ...).  results[count] (host) may be NULL;
+ * if given, each plan's final residuals and value are computed as sk_solve
+ * does.  Fixed iteration count (no tolerance).  All plans on one device,
+ * none twice, none with stage timing on (else SK_ERR_ARG, nothing run).
+ * Returns SK_ERR_UNDERFLOW if results were requested and a plan saw a
+ * non-positive kernel sum.  Synchronizes `stream`.
+ */
+int sk_solve_batch(sk_plan* const* plans, int count, int max_iter, sk_result* results, void* stream);
 
 /*
  * Gradient of the value with respect to the weights and the positions, at the

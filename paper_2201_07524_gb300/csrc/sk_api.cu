@@ -981,6 +981,61 @@ int sk_default_params(sk_nfft_params* prm) {
     return SK_OK;
 }
 
+// ------------------------------------------------------------ parameter choice
+// Accuracy targets of the automatic choices, relative to K(0) = 1: below the
+// rounding of the kernel sums in each precision.
+double auto_target(int precision) { return precision == SK_FP32 ? 1e-6 : 1e-10; }
+
+// Window cutoff m for the target: the Kaiser-Bessel window's error with
+// oversampling sigma decays like 4 pi (1 - 1/sigma)^(1/4) exp(-2 pi m sqrt(1 - 1/sigma))
+// (the window's error estimate, Plonka et al. Ch. 7).  3-D plans stop at m = 5,
+// the widest window of the column kernels.
+int choose_cutoff(int d, double sigma, int precision) {
+    const double q = 1.0 - 1.0 / sigma;
+    const double m = std::log(4.0 * M_PI * std::pow(q, 0.25) / auto_target(precision)) / (2.0 * M_PI * std::sqrt(q));
+    return std::max(2, std::min(d == 3 ? 5 : 8, int(std::ceil(m))));
+}
+
+// Bandwidth N: the smallest power of two from 16 for which the Fourier tail of
+// the regularized kernel, sum over |k| >= N/2 of |c_k| for its slice
+// rho -> K_R(|rho|) along one axis (Eq. (ansatz_NFFT)'s coefficients in one
+// dimension, from 2048 samples), stays below target / d.
+int choose_bandwidth(double eps_s, double r, int d, const sk_nfft_params& p, bool auto_I, bool nearfield) {
+    KernelParams kp{};
+    kp.eps_s = eps_s;
+    kp.r = r;
+    kp.L = 0.5 - p.eps_B;
+    kp.p = p.p;
+    kp.nearfield = nearfield ? 1 : 0;
+    kp.eps_I = p.eps_I;
+    const int nmax = d == 1 ? 2048 : 512;
+    if (!boundary_coefficients(kp)) return 64;
+    const int M = 2048;
+    std::vector<double> ct(M), f(M), c(M / 2 + 1);
+    for (int l = 0; l < M; ++l) ct[l] = std::cos(2.0 * M_PI * l / M);
+    const double target = auto_target(p.precision) / d;
+    int spectrum_for = -1;   // the N whose eps_I the spectrum was computed with (near field only)
+    for (int N = 16; N <= nmax; N *= 2) {
+        if (spectrum_for < 0 || (nearfield && auto_I)) {
+            if (nearfield) {
+                if (auto_I) kp.eps_I = 16.0 / (3.0 * N);
+                if (!(kp.eps_I < kp.L) || !nearfield_coefficients(kp)) continue;
+            }
+            for (int l = 0; l < M; ++l) f[l] = kr_value(std::fabs(double(l - M / 2) / M), kp);
+            for (int k = 0; k <= M / 2; ++k) {
+                double acc = 0.0;
+                for (int l = 0; l < M; ++l) acc += f[l] * ct[(int64_t(k) * l) % M];
+                c[k] = acc / M;
+            }
+            spectrum_for = N;
+        }
+        double tail = 0.0;
+        for (int k = N / 2; k <= M / 2; ++k) tail += 2.0 * std::fabs(c[k]);
+        if (tail <= target) return N;
+    }
+    return nmax;
+}
+
 static int validate_params(int d, const sk_nfft_params& p, int& n_os, int& log2n) {
     if (p.N < 8 || (p.N % 2) != 0) return SK_ERR_ARG;
     if (!(p.sigma > 1.0) || !std::isfinite(p.sigma)) return SK_ERR_ARG;
@@ -1013,11 +1068,16 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         p = *prm;
     else
         sk_default_params(&p);
+    // N <= 0 or m_w <= 0: chosen once the geometry is known (choose_bandwidth,
+    // choose_cutoff); placeholders let every other parameter be checked now
+    const bool auto_N = p.N <= 0, auto_m = p.m_w <= 0, auto_I = !(p.eps_I > 0.0);
+    if (auto_N) p.N = 64;
+    if (auto_m) p.m_w = 4;
     int n_os = 0, log2n = 0;
     int rc = validate_params(d, p, n_os, log2n);
     if (rc != SK_OK) return rc;
     const bool nearfield = !even_integer(r);
-    if (!(p.eps_I > 0.0)) p.eps_I = 16.0 / (3.0 * p.N);   // automatic near-field radius
+    if (auto_I) p.eps_I = 16.0 / (3.0 * p.N);   // automatic near-field radius
     if (nearfield && !(p.eps_I < 0.5 - p.eps_B)) return SK_ERR_ARG;
 
     sk_plan* P = new (std::nothrow) sk_plan();
@@ -1029,25 +1089,6 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         P->m = m;
         P->eps = eps;
         P->r = r;
-        P->prm = p;
-        P->precision = p.precision;
-        P->N = p.N;
-        P->h = p.N / 2;
-        P->n_os = n_os;
-        P->log2n = log2n;
-        P->W = 2 * p.m_w;
-        bin_shape(d, P->W, P->B);
-        P->nbins = 1;
-        P->bvol = 1;
-        for (int t = 0; t < 3; ++t) {
-            P->nb[t] = t < d ? (n_os + P->B[t] - 1) / P->B[t] : 1;
-            P->nbins *= P->nb[t];
-            P->bvol *= t < d ? P->B[t] : 1;
-        }
-        P->nkeys = int64_t(P->nbins) * P->bvol;
-        P->beta = M_PI * (2.0 - 1.0 / p.sigma);
-        P->knorm = double(p.m_w) / std::sinh(P->beta * p.m_w);
-        window_polynomials(p.m_w, P->beta, P->knorm, P->wp);
         P->nearfield = nearfield ? 1 : 0;
 
         CK(cudaStreamCreateWithFlags(&P->ps, cudaStreamNonBlocking));
@@ -1132,6 +1173,32 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
             P->scale = R > 0.0 ? (0.25 - 0.5 * p.eps_B) / R : 1.0;
         }
         P->eps_s = eps * std::pow(P->scale, r);
+        if (auto_N || auto_m) {
+            if (auto_m) p.m_w = choose_cutoff(d, p.sigma, p.precision);
+            if (auto_N) p.N = choose_bandwidth(P->eps_s, r, d, p, auto_I, nearfield);
+            if (auto_I) p.eps_I = 16.0 / (3.0 * p.N);
+            if (validate_params(d, p, n_os, log2n) != SK_OK) throw Fail{SK_ERR_ARG};
+            if (nearfield && !(p.eps_I < 0.5 - p.eps_B)) throw Fail{SK_ERR_ARG};
+        }
+        P->prm = p;
+        P->precision = p.precision;
+        P->N = p.N;
+        P->h = p.N / 2;
+        P->n_os = n_os;
+        P->log2n = log2n;
+        P->W = 2 * p.m_w;
+        bin_shape(d, P->W, P->B);
+        P->nbins = 1;
+        P->bvol = 1;
+        for (int t = 0; t < 3; ++t) {
+            P->nb[t] = t < d ? (n_os + P->B[t] - 1) / P->B[t] : 1;
+            P->nbins *= P->nb[t];
+            P->bvol *= t < d ? P->B[t] : 1;
+        }
+        P->nkeys = int64_t(P->nbins) * P->bvol;
+        P->beta = M_PI * (2.0 - 1.0 / p.sigma);
+        P->knorm = double(p.m_w) / std::sinh(P->beta * p.m_w);
+        window_polynomials(p.m_w, P->beta, P->knorm, P->wp);
 
         // kernel parameters in torus coordinates
         P->kp.eps_s = P->eps_s;
@@ -1285,6 +1352,94 @@ int sk_solve(sk_plan* P, int max_iter, double tol, int check_every, double* u_ou
         leave(P, stream);
     } catch (const Fail& f) {
         return fail_code(f);
+    }
+    return rc;
+}
+
+int sk_solve_batch(sk_plan* const* plans, int count, int max_iter, sk_result* results, void* stream) {
+    if (!plans || count < 1 || max_iter < 0) return SK_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || plans[i]->timing) return SK_ERR_ARG;
+        if (plans[i]->device != plans[0]->device) return SK_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return SK_ERR_ARG;
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaStream_t bs = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join(size_t(count), nullptr);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int rc = SK_OK;
+    try {
+        CK(cudaSetDevice(plans[0]->device));
+        CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        for (auto& e : join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // every plan's stream starts after the caller's work; statuses cleared
+        for (int i = 0; i < count; ++i) {
+            enter(plans[i], stream);
+            clear_status(plans[i]);
+        }
+        std::vector<int64_t> kernels(size_t(count), 0);
+        if (max_iter > 0) {
+            // one iteration of every plan as parallel branches of one graph
+            CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+            try {
+                CK(cudaEventRecord(fork, bs));
+                for (int i = 0; i < count; ++i) {
+                    sk_plan* P = plans[i];
+                    CK(cudaStreamWaitEvent(P->ps, fork, 0));
+                    const int64_t before = P->launches;
+                    run_iteration(P);
+                    kernels[size_t(i)] = P->launches - before;
+                    P->launches = before;
+                    CK(cudaEventRecord(join[size_t(i)], P->ps));
+                    CK(cudaStreamWaitEvent(bs, join[size_t(i)], 0));
+                }
+            } catch (...) {
+                cudaStreamEndCapture(bs, &g);
+                throw;
+            }
+            CK(cudaStreamEndCapture(bs, &g));
+            CK(cudaGraphInstantiate(&ge, g, 0));
+            // the replays start after every plan's preparation above
+            for (int i = 0; i < count; ++i) {
+                CK(cudaEventRecord(join[size_t(i)], plans[i]->ps));
+                CK(cudaStreamWaitEvent(bs, join[size_t(i)], 0));
+            }
+            for (int k = 0; k < max_iter; ++k) CK(cudaGraphLaunch(ge, bs));
+            CK(cudaEventRecord(fork, bs));
+        }
+        for (int i = 0; i < count; ++i) {
+            sk_plan* P = plans[i];
+            if (max_iter > 0) CK(cudaStreamWaitEvent(P->ps, fork, 0));
+            P->iters += max_iter;
+            P->launches += kernels[size_t(i)] * max_iter;
+            if (results) {
+                sk_result* res = results + i;
+                std::memset(res, 0, sizeof(*res));
+                if (P->precision == SK_FP32)
+                    final_report<float>(P, res);
+                else
+                    final_report<double>(P, res);
+                res->iters = max_iter;
+                if (read_status(P) & 1) rc = SK_ERR_UNDERFLOW;
+            }
+            leave(P, stream);
+        }
+        CK(cudaStreamSynchronize(cs));
+    } catch (const Fail& f) {
+        rc = fail_code(f);
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    for (auto& e : join)
+        if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (bs) {
+        cudaStreamSynchronize(bs);
+        cudaStreamDestroy(bs);
     }
     return rc;
 }

@@ -43,6 +43,23 @@ struct KernelParams {
     double ki[kMaxP];           // K_I(rho) = sum ki[q] (rho/eps_I)^(2q)
 };
 
+// The regularized kernel K_R at distance rho (torus units): K_I below eps_I
+// when near-field regularization is on, the exact kernel exp(-rho^r / eps_s)
+// up to L, the boundary polynomial K_B beyond (constant past 1/2).
+__host__ __device__ inline double kr_value(double rho, const KernelParams& kp) {
+    double v = 0.0;
+    if (kp.nearfield && rho < kp.eps_I) {
+        const double s2 = (rho * rho) / (kp.eps_I * kp.eps_I);
+        for (int q = kp.p - 1; q >= 0; --q) v = v * s2 + kp.ki[q];
+    } else if (rho <= kp.L) {
+        v = exp(-pow(rho, kp.r) / kp.eps_s);
+    } else {
+        const double tau = (fmin(rho, 0.5) - kp.L) / (0.5 - kp.L);
+        for (int i = 2 * kp.p - 2; i >= 0; --i) v = v * tau + kp.kb[i];
+    }
+    return v;
+}
+
 struct Cloud {
     int64_t n = 0;
     void* coord[3] = {nullptr, nullptr, nullptr};  // T*, sorted grid coordinates

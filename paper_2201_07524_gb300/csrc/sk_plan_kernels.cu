@@ -325,19 +325,7 @@ __global__ void k_sample_kernel(double* __restrict__ out, int N, int d, KernelPa
         const double y = double(l) / double(N);
         rho2 += y * y;
     }
-    const double rho = sqrt(rho2);
-    double v;
-    if (kp.nearfield && rho < kp.eps_I) {
-        const double s2 = rho2 / (kp.eps_I * kp.eps_I);
-        v = 0.0;
-        for (int q = kp.p - 1; q >= 0; --q) v = v * s2 + kp.ki[q];
-    } else if (rho <= kp.L) {
-        v = exp(-pow(rho, kp.r) / kp.eps_s);
-    } else {
-        const double tau = (fmin(rho, 0.5) - kp.L) / (0.5 - kp.L);
-        v = 0.0;
-        for (int i = 2 * kp.p - 2; i >= 0; --i) v = v * tau + kp.kb[i];
-    }
+    const double v = kr_value(sqrt(rho2), kp);
     out[idx] = v;
 }
 

@@ -66,6 +66,7 @@ _SIGS = {
     "sk_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D,
                                 ctypes.POINTER(sk_result), _S]),
     "sk_grad": (ctypes.c_int, [_P, _D, _D, _D, _D, _S]),
+    "sk_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(sk_result), _S]),
     "sk_divergence": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _D, _D, ctypes.c_int64, _D, _D, ctypes.c_double,
                                      ctypes.c_double, ctypes.POINTER(sk_nfft_params), ctypes.c_int, ctypes.c_double,
                                      _D, _D, _D, _D, _D, _S]),
@@ -216,6 +217,19 @@ def sk_solve(plan, max_iter, tol=0.0, check_every=10, u_out=None, v_out=None, re
     out = None
     if res is not None:
         out = {f: getattr(res, f) for f, _ in sk_result._fields_}
+    return st, out
+
+
+def sk_solve_batch(plans, max_iter, result=True, stream=None, raise_on_error=True):
+    """Returns (status, list of result dicts or None); see include/sk.h."""
+    arr = (_P * len(plans))(*[p.handle for p in plans])
+    res = (sk_result * len(plans))() if result else None
+    st = _lib.sk_solve_batch(arr, len(plans), int(max_iter), res, _stream(stream))
+    if raise_on_error and st != SK_OK:
+        raise SkError(st, "sk_solve_batch")
+    out = None
+    if result:
+        out = [{f: getattr(r, f) for f, _ in sk_result._fields_} for r in res]
     return st, out
 
 
