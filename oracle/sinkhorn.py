@@ -234,3 +234,43 @@ def sinkhorn_divergence_gradient(x, a, y, b, eps, r, iters):
     yb1, yb2, yy1, yy2 = dual_gradient(y, y, b, b, oy["u"], oy["v"], eps, r)
     return (ga - 0.5 * (xa1 + xa2), gb - 0.5 * (yb1 + yb2),
             gx - 0.5 * (xx1 + xx2), gy - 0.5 * (yy1 + yy2))
+
+
+def _logsumexp(z, axis):
+    zmax = np.max(z, axis=axis, keepdims=True)
+    zmax = np.where(np.isfinite(zmax), zmax, 0.0)
+    return np.squeeze(zmax, axis=axis) + np.log(np.sum(np.exp(z - zmax), axis=axis))
+
+
+def sinkhorn_log_dense(x, a, y, b, eps, r, iters, beta0=None, gamma0=None):
+    """Alg. 4 (log-domain) in FP64 with the dual variables beta, gamma of
+    Eq. (11), every kernel sum formed by the log-sum-exp trick:
+
+      log t_i  = LSE_j (gamma_j / eps - 1/2 - C_ij / eps),
+      beta_i  <- eps (log a_i - log t_i + 1/2)           (Delta odd)
+      log t~_j = LSE_i (beta_i / eps - 1/2 - C_ij / eps),
+      gamma_j <- eps (log b_j - log t~_j + 1/2)          (Delta even).
+
+    The +1/2 is the first-order condition d/d beta_i of Eq. (11) set to zero
+    (the update as printed in Alg. 4 leaves it out).  Starts from the Set line
+    beta = gamma = 0 unless given.  Returns beta, gamma, the value of Eq. (11)
+    at the final state (Alg. 4 result line: sum a beta + sum b gamma - eps sum_j
+    t~_j exp(gamma_j / eps - 1/2), t~ formed from the final beta) and the
+    Eq. (Error) residuals."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    C = cost_matrix(x, y, r)
+    beta = np.zeros(len(a)) if beta0 is None else np.array(beta0, dtype=np.float64)
+    gamma = np.zeros(len(b)) if gamma0 is None else np.array(gamma0, dtype=np.float64)
+    for _ in range(iters):
+        log_t = _logsumexp(gamma[None, :] / eps - 0.5 - C / eps, axis=1)
+        beta = eps * (np.log(a) - log_t + 0.5)
+        log_tt = _logsumexp(beta[:, None] / eps - 0.5 - C / eps, axis=0)
+        gamma = eps * (np.log(b) - log_tt + 0.5)
+    log_pi = beta[:, None] / eps - 0.5 + gamma[None, :] / eps - 0.5 - C / eps
+    row = np.exp(_logsumexp(log_pi, axis=1)) - a
+    col = np.exp(_logsumexp(log_pi, axis=0)) - b
+    mass = float(np.exp(_logsumexp(log_pi.ravel(), axis=0)))
+    s = float(a @ beta + b @ gamma - eps * mass)
+    return dict(beta=beta, gamma=gamma, s=s, err_row=float(np.linalg.norm(row)),
+                err_col=float(np.linalg.norm(col)))

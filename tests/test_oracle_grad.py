@@ -172,3 +172,39 @@ def test_divergence_gradient_vanishes_at_equal_measures():
     _, gb, gx, gy = osk.sinkhorn_divergence_gradient(x, a, x.copy(), a.copy(), 0.2, 2.0, 2000)
     assert np.max(np.abs(gy)) < 1e-12 and np.max(np.abs(gx)) < 1e-12
     assert np.max(np.abs(gb - gb.mean())) < 1e-12
+
+
+# ------------------------------------------------------------ log domain
+@pytest.mark.parametrize("iters", [1, 2, 7])
+def test_log_domain_is_alg1_up_to_a_gauge(iters):
+    # from beta = gamma = 0 (u = v = e^(-1/2)) against Alg. 1 from u = v = 1:
+    # exp(beta/eps - 1/2) = e^(1/2) u and exp(gamma/eps - 1/2) = e^(-1/2) v,
+    # which leaves pi and the value unchanged
+    x, y, a, b = _problem(6, 5, 2, 91)
+    eps = 0.1
+    lg = osk.sinkhorn_log_dense(x, a, y, b, eps, 2.0, iters)
+    ref = osk.sinkhorn_dense(x, a, y, b, eps, 2.0, iters)
+    assert np.allclose(lg["beta"], eps * (np.log(ref["u"]) + 1.0), rtol=0, atol=1e-13)
+    assert np.allclose(lg["gamma"], eps * np.log(ref["v"]), rtol=0, atol=1e-13)
+    assert abs(lg["s"] - ref["s"]) < 1e-13
+    assert abs(lg["err_row"] - ref["err_row"]) < 1e-13
+
+
+def test_log_domain_survives_where_the_kernel_underflows():
+    # eps small enough that the scaling form's u, v leave the FP64 range: the
+    # log form keeps converging, and its dual value (a lower bound of the
+    # entropic optimum) stays within the sandwich of Lemma "Quality of the
+    # Sinkhorn approximation" around the brute-force optimum,
+    # s <= w_r <= s + eps (H(a) + H(b)).
+    from oracle import lp
+    rng = np.random.default_rng(92)
+    x = rng.uniform(-0.4, 0.4, size=(5, 2))
+    y = rng.uniform(-0.4, 0.4, size=(5, 2))
+    a = np.full(5, 0.2)
+    eps = 1e-4
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        assert not np.all(np.isfinite(osk.sinkhorn_dense(x, a, y, a, eps, 2.0, 50)["u"]))
+    lg = osk.sinkhorn_log_dense(x, a, y, a, eps, 2.0, 3000)
+    assert np.all(np.isfinite(lg["beta"])) and lg["err_row"] < 1e-3
+    w = lp.assignment_cost_bruteforce(osk.cost_matrix(x, y, 2.0))[0]
+    assert lg["s"] <= w <= lg["s"] + eps * (osk.entropy(a) + osk.entropy(a))
