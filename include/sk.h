@@ -52,6 +52,7 @@ enum {
 
 enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / interpolation */
 enum { SK_METHOD_NFFT = 0, SK_METHOD_DIRECT = 1 };
+enum { SK_DOMAIN_SCALING = 0, SK_DOMAIN_LOG = 1 };   /* state of the iteration: Alg. 3 or Alg. 4 */
 enum { SK_SET_X = 0, SK_SET_Y = 1 };        /* which point cloud a stage entry point acts on */
 
 typedef struct sk_plan sk_plan;
@@ -154,6 +155,24 @@ void sk_destroy(sk_plan* plan);
  * or SK_METHOD_DIRECT (the plain O(n m) sums of Eqs. (matexp)/(matexpt), FP32
  * kernel values with FP64 accumulation across tiles). */
 int sk_set_method(sk_plan* plan, int method);
+
+/*
+ * Choose the form of the iteration.  SK_DOMAIN_SCALING (default): Alg. 3, the
+ * state is the scaling vectors u, v.  SK_DOMAIN_LOG: Alg. 4, the state is the
+ * dual variables beta = eps (log u + 1/2), gamma = eps (log v + 1/2) of
+ * Eq. (11), updated by its first-order condition
+ *   beta_i = eps (log a_i - log t_i + 1/2),  t_i = sum_j k_ij exp(gamma_j / eps - 1/2)
+ * (the update printed in Alg. 4 leaves out the + 1/2; with it the value is
+ * the one of Alg. 3 at the same plan).  Each half-step forms its weights as
+ * exp((gamma_j - max gamma) / eps - 1/2) <= e^(-1/2), so no weight leaves the
+ * FP32 range however large the potentials grow (the scaling form's u, v leave
+ * it for small eps); the kernel sums themselves keep their own range.  The
+ * current state is converted (u = exp(beta / eps - 1/2) back, which can
+ * overflow to inf); sk_get_state / sk_set_state / sk_solve's u_out, v_out
+ * then carry beta, gamma.  sk_grad works in either domain.
+ * Errors: SK_ERR_ARG for a NULL plan or an unknown domain.
+ */
+int sk_set_domain(sk_plan* plan, int domain);
 
 /*
  * One kernel-vector product (Eqs. (matexp), (matexpt)):

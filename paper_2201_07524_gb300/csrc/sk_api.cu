@@ -19,6 +19,8 @@ struct sk_plan {
     sk_nfft_params prm{};
     int precision = SK_FP32;
     int method = SK_METHOD_NFFT;
+    int domain = SK_DOMAIN_SCALING;
+    double* shift = nullptr;    // log domain: max of the Y ([0]) and X ([1]) dual variables
     int N = 0, h = 0, n_os = 0, log2n = 0, W = 0, B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 0, bvol = 1;
     int64_t nkeys = 0;
     double beta = 0, knorm = 0;
@@ -646,7 +648,32 @@ Epilogue make_epilogue(sk_plan* P, int mode, Cloud& dst, int slot, double* out) 
     e.ticket = P->ticket;
     e.result = P->stats + 3 * slot;
     e.status = P->status;
+    e.log_domain = P->domain == SK_DOMAIN_LOG ? 1 : 0;
+    e.fp32_logs = P->precision == SK_FP32 ? 1 : 0;
+    e.eps = P->eps;
+    e.lam = 1.0 / P->eps;
+    e.shift = P->shift;
     return e;
+}
+
+// Log domain: the weights exp((g_j - shift) / eps - 1/2) of cloud c's dual
+// variables g into c.work, shift = max g stored at P->shift[slot].
+const double* log_weights(sk_plan* P, Cloud& c, int slot) {
+    k_block_max<<<kRedBlocks, 256, 0, P->ps>>>(c.scal, c.n, P->partial);
+    CK(cudaGetLastError());
+    k_log_weights<<<kRedBlocks, 256, 0, P->ps>>>(c.scal, c.n, P->partial, kRedBlocks, 1.0 / P->eps,
+                                                   P->precision == SK_FP32 ? 1 : 0, c.work, P->shift + slot);
+    CK(cudaGetLastError());
+    P->launches += 2;
+    return c.work;
+}
+
+// The weights of a product from cloud c: its scaling vector, or in the log
+// domain the shifted exponentials of its dual variables (slot 0 for Y, 1 for X).
+const double* source_weights(sk_plan* P, Cloud& c, int slot, Epilogue& e) {
+    if (P->domain != SK_DOMAIN_LOG) return c.scal;
+    e.shift = P->shift + slot;
+    return log_weights(P, c, slot);
 }
 
 template <typename T>
@@ -747,10 +774,14 @@ void product(sk_plan* P, Cloud& src, const double* w, Cloud& dst, const Epilogue
 
 template <typename T>
 void iteration(sk_plan* P) {
-    // odd half-step: u = a ./ (K v)
-    product<T>(P, P->Y, P->Y.scal, P->X, make_epilogue(P, EPI_UPDATE, P->X, SLOT_ROW, nullptr));
+    // odd half-step: u = a ./ (K v)  (log domain: beta = eps (log a - log t + 1/2))
+    Epilogue e1 = make_epilogue(P, EPI_UPDATE, P->X, SLOT_ROW, nullptr);
+    const double* w1 = source_weights(P, P->Y, 0, e1);
+    product<T>(P, P->Y, w1, P->X, e1);
     // even half-step: v = b ./ (K^T u)
-    product<T>(P, P->X, P->X.scal, P->Y, make_epilogue(P, EPI_UPDATE, P->Y, SLOT_COL, nullptr));
+    Epilogue e2 = make_epilogue(P, EPI_UPDATE, P->Y, SLOT_COL, nullptr);
+    const double* w2 = source_weights(P, P->X, 1, e2);
+    product<T>(P, P->X, w2, P->Y, e2);
 }
 
 void run_iteration(sk_plan* P) {
@@ -833,21 +864,27 @@ int read_status(sk_plan* P) {
 
 void clear_status(sk_plan* P) { CK(cudaMemsetAsync(P->status, 0, sizeof(int), P->ps)); }
 
+// sum_i a_i log u_i; in the log domain lam sum_i a_i beta_i - 1/2 (sum a = 1).
 double sum_marg_log(sk_plan* P, const Cloud& c) {
-    k_sum_marg_log<<<kRedBlocks, 256, 0, P->ps>>>(c.marg, c.scal, c.n, P->partial);
+    const int as_is = P->domain == SK_DOMAIN_LOG ? 1 : 0;
+    k_sum_marg_log<<<kRedBlocks, 256, 0, P->ps>>>(c.marg, c.scal, c.n, as_is, P->partial);
     CK(cudaGetLastError());
     ++P->launches;
     const int ops[1] = {0};
     double v = 0.0;
     combine_to_host(P, kRedBlocks, 1, ops, &v);
     ++P->launches;
-    return v;
+    return as_is ? v / P->eps - 0.5 : v;
 }
 
 template <typename T>
 void final_report(sk_plan* P, sk_result* res) {
-    product<T>(P, P->Y, P->Y.scal, P->X, make_epilogue(P, EPI_RESID, P->X, SLOT_RES_ROW, nullptr));
-    product<T>(P, P->X, P->X.scal, P->Y, make_epilogue(P, EPI_RESID, P->Y, SLOT_RES_COL, nullptr));
+    Epilogue e1 = make_epilogue(P, EPI_RESID, P->X, SLOT_RES_ROW, nullptr);
+    const double* w1 = source_weights(P, P->Y, 0, e1);
+    product<T>(P, P->Y, w1, P->X, e1);
+    Epilogue e2 = make_epilogue(P, EPI_RESID, P->Y, SLOT_RES_COL, nullptr);
+    const double* w2 = source_weights(P, P->X, 1, e2);
+    product<T>(P, P->X, w2, P->Y, e2);
     CK(cudaMemcpyAsync(P->pinned, P->stats, sizeof(double) * 3 * NSLOTS, cudaMemcpyDeviceToHost, P->ps));
     CK(cudaStreamSynchronize(P->ps));
     double st[3 * NSLOTS];
@@ -867,7 +904,8 @@ void final_report(sk_plan* P, sk_result* res) {
 // into a caller buffer (host or device) in caller order.
 void dual_variable_out(sk_plan* P, const Cloud& c, double* out) {
     const bool host = !is_device_ptr(out);
-    k_dual_variable<<<nblk(c.n), 256, 0, P->ps>>>(c.scal, c.perm, c.n, P->eps, host ? c.stage : out);
+    k_dual_variable<<<nblk(c.n), 256, 0, P->ps>>>(c.scal, c.perm, c.n, P->eps, P->domain == SK_DOMAIN_LOG ? 1 : 0,
+                                                  host ? c.stage : out);
     CK(cudaGetLastError());
     ++P->launches;
     if (host) {
@@ -895,15 +933,19 @@ void position_gradient(sk_plan* P, Cloud& src, Cloud& dst, double* out) {
     const double inv_nos = 1.0 / P->n_os, inv_s = 1.0 / P->scale;
     Epilogue e = make_epilogue(P, EPI_APPLY, dst, 0, t0);
     e.perm = nullptr;   // sorted order
-    product<T>(P, src, src.scal, dst, e);
+    const int slot = &src == &P->Y ? 0 : 1;
+    const double* ws = source_weights(P, src, slot, e);     // v, or the log domain's shifted weights
+    const double* log_shift = P->domain == SK_DOMAIN_LOG ? P->shift + slot : nullptr;
+    product<T>(P, src, ws, dst, e);
     for (int t = 0; t < d; ++t) {
-        launch_weighted_coord<T>(src.scal, src.coord[t], src.n, inv_nos, inv_s, w, P->ps);
+        launch_weighted_coord<T>(ws, src.coord[t], src.n, inv_nos, inv_s, w, P->ps);
         CK(cudaGetLastError());
         ++P->launches;
         Epilogue et = make_epilogue(P, EPI_APPLY, dst, 0, tt);
         et.perm = nullptr;
         product<T>(P, src, w, dst, et);
-        launch_position_gradient<T>(dst.scal, dst.coord[t], t0, tt, dst.perm, n, d, t, inv_nos, inv_s, gdst, P->ps);
+        launch_position_gradient<T>(dst.scal, dst.coord[t], t0, tt, dst.perm, n, d, t, inv_nos, inv_s, log_shift,
+                                    1.0 / P->eps, gdst, P->ps);
         CK(cudaGetLastError());
         ++P->launches;
     }
@@ -1103,6 +1145,8 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 4));   // [0] reductions, [2..3] column queue
         P->stats = static_cast<double*>(dalloc(P, sizeof(double) * (3 * NSLOTS + 8)));
         P->status = static_cast<int*>(dalloc(P, sizeof(int) * 4));
+        P->shift = static_cast<double*>(dalloc(P, sizeof(double) * 2));
+        CK(cudaMemsetAsync(P->shift, 0, sizeof(double) * 2, P->ps));
         CK(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned) * 4, P->ps));
         CK(cudaMemsetAsync(P->stats, 0, sizeof(double) * (3 * NSLOTS + 8), P->ps));
         CK(cudaMemsetAsync(P->status, 0, sizeof(int) * 4, P->ps));
@@ -1281,6 +1325,26 @@ int sk_set_method(sk_plan* P, int method) {
     if (method != P->method) {
         destroy_graph(P);
         P->method = method;
+    }
+    return SK_OK;
+}
+
+int sk_set_domain(sk_plan* P, int domain) {
+    if (!P || (domain != SK_DOMAIN_SCALING && domain != SK_DOMAIN_LOG)) return SK_ERR_ARG;
+    if (domain == P->domain) return SK_OK;
+    try {
+        CK(cudaSetDevice(P->device));
+        const int to_log = domain == SK_DOMAIN_LOG ? 1 : 0;
+        k_convert_domain<<<nblk(P->X.n), 256, 0, P->ps>>>(P->X.scal, P->X.n, P->eps, to_log);
+        CK(cudaGetLastError());
+        k_convert_domain<<<nblk(P->Y.n), 256, 0, P->ps>>>(P->Y.scal, P->Y.n, P->eps, to_log);
+        CK(cudaGetLastError());
+        P->launches += 2;
+        CK(cudaStreamSynchronize(P->ps));
+        destroy_graph(P);
+        P->domain = domain;
+    } catch (const Fail& f) {
+        return fail_code(f);
     }
     return SK_OK;
 }

@@ -104,6 +104,12 @@ struct Epilogue {
     unsigned* ticket = nullptr;  // zero between launches; the last block resets it
     double* result = nullptr;    // [0] sum (scal_old t - marg)^2, [1] bad count, [2] sum scal_old t
     int* status = nullptr;       // bit 0 set when some t_i <= 0 or not finite (UPDATE)
+    // log domain (Alg. 4): scal holds the dual variables beta; t_i is the sum
+    // with the source weights exp((gamma_j - shift) / eps - 1/2), shift = *shift
+    int log_domain = 0;
+    int fp32_logs = 0;           // logs and exps of FP32-accurate sums in FP32 (FP32 plans)
+    double eps = 0.0, lam = 0.0; // eps and 1 / eps
+    const double* shift = nullptr;
 };
 
 // Piecewise-polynomial form of the Kaiser-Bessel window (the Horner scheme of
@@ -275,6 +281,47 @@ __device__ __forceinline__ double div_newton(double a, double t) {
     return q;
 }
 
+// log v for v > 0 in the FP32 normal range, split as e ln 2 + log(m) with
+// v = m 2^e, m in [1/2, 1): the FP32 logarithm of m carries an absolute error
+// of about 6e-8 whatever the size of log v.
+__device__ __forceinline__ double log_split(float v) {
+    int ex = 0;
+    const float mant = frexpf(v, &ex);
+    return double(ex) * 0.69314718055994530942 + double(logf(mant));
+}
+
+// Log-domain update (Alg. 4 with the first-order condition of Eq. (11)):
+// beta_new = eps (log a - log t + 1/2) with t = exp(lam shift) t', and the
+// residual of the old state u_old t - a = a (exp(lam (beta_old - beta_new)) - 1)
+// (u_new t = a exactly).  RESID: u t = exp(lam (beta + shift) - 1/2) t'.
+__device__ __forceinline__ void epi_point_log(const Epilogue& e, int64_t i, double t, double q, double a,
+                                              double& sq, double& bad, double& dot) {
+    const double sh = *e.shift;
+    if (e.mode == EPI_UPDATE) {
+        const float tf = float(t);
+        if (!(tf >= 1.17549435e-38f && tf <= 3.0e38f)) bad += 1.0;
+        double bn, r;
+        if (!(a > 0.0)) {           // a point without mass: beta = -inf, no residual
+            bn = -INFINITY;
+            r = 0.0;
+        } else if (e.fp32_logs) {
+            bn = e.eps * (log_split(float(a)) - log_split(tf) + 0.5) - sh;
+            r = a * double(expm1f(float(e.lam * (q - bn))));
+        } else {
+            bn = e.eps * (log(a) - log(t) + 0.5) - sh;
+            r = a * expm1(e.lam * (q - bn));
+        }
+        sq = fma(r, r, sq);
+        e.scal[i] = bn;
+    } else {
+        const double ut = a > 0.0 ? exp(e.lam * (q + sh) - 0.5) * t : 0.0;
+        const double r = ut - a;
+        sq = fma(r, r, sq);
+        dot += ut;
+        e.t_store[i] = t;
+    }
+}
+
 // Per-point FP64 epilogue (Eq. (S1) update and Eq. (Error) residual terms).
 // UPDATE: sq += (u_old t - a)^2 and u = a / t (the residual of the state before
 // the update; the sum u_old t and the kernel sums are not needed inside the
@@ -288,6 +335,10 @@ __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t
     }
     const double q = e.scal[i];
     const double a = e.marg[i];
+    if (e.log_domain) {
+        epi_point_log(e, i, t, q, a, sq, bad, dot);
+        return;
+    }
     const double r = fma(q, t, -a);
     sq = fma(r, r, sq);
     if (e.mode == EPI_UPDATE) {
@@ -318,6 +369,10 @@ __device__ __forceinline__ void epi_point_pre(const Epilogue& e, int64_t i, doub
     if (e.add) t += e.add[i];
     if (e.mode == EPI_APPLY) {
         e.out[e.perm ? e.perm[i] : i] = t;
+        return;
+    }
+    if (e.log_domain) {
+        epi_point_log(e, i, t, q, a, sq, bad, dot);
         return;
     }
     const double r = fma(q, t, -a);

@@ -90,12 +90,14 @@ __global__ void k_weight_stats(const double* __restrict__ w, int64_t n, double* 
 }
 
 // Per-block partial of sum_i marg_i log(scal_i).
+// sum_i a_i log u_i (as_is = 0) or sum_i a_i scal_i (as_is = 1: scal holds
+// log-domain dual variables), points without mass skipped.
 __global__ void k_sum_marg_log(const double* __restrict__ marg, const double* __restrict__ scal, int64_t n,
-                               double* __restrict__ partial) {
+                               int as_is, double* __restrict__ partial) {
     double acc = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         const double a = marg[i];
-        if (a > 0.0) acc += a * log(scal[i]);
+        if (a > 0.0) acc += a * (as_is ? scal[i] : log(scal[i]));
     }
     __shared__ double s[256];
     s[threadIdx.x] = acc;
@@ -520,6 +522,63 @@ template void launch_build_mult<double>(double*, int, int, const double*, double
 template void launch_twiddles<float>(void*, int, cudaStream_t);
 template void launch_twiddles<double>(void*, int, cudaStream_t);
 
+// ------------------------------------------------------------ log domain
+// Per-block maxima of v (-inf for an empty block), for the shift of the
+// log-domain weights.
+__global__ void k_block_max(const double* __restrict__ v, int64_t n, double* __restrict__ partial) {
+    double m = -INFINITY;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        m = fmax(m, v[i]);
+    __shared__ double s[256];
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
+}
+
+// Weights of a log-domain half-step: w_j = exp((g_j - shift) / eps - 1/2) with
+// shift = max_j g_j (from the block maxima), so every weight is at most
+// e^(-1/2) and none overflows; block 0 stores the shift for the epilogue.  FP32
+// plans evaluate exp(x) as 2^k exp(x - k ln 2), the reduced argument in FP32.
+__global__ void k_log_weights(const double* __restrict__ g, int64_t n, const double* __restrict__ partial,
+                              int nparts, double lam, int fp32, double* __restrict__ w, double* __restrict__ shift) {
+    __shared__ double s[256];
+    double m = -INFINITY;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) m = fmax(m, partial[k]);
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + k]);
+        __syncthreads();
+    }
+    const double sh = isfinite(s[0]) ? s[0] : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *shift = sh;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double x = lam * (g[i] - sh) - 0.5;
+        double v;
+        if (!(x > -745.0)) {
+            v = 0.0;
+        } else if (fp32) {
+            const double k = rint(x * 1.4426950408889634);
+            const float red = float(fma(-k, 0.69314718055994530942, x));
+            v = double(ldexpf(expf(red), int(k)));
+        } else {
+            v = exp(x);
+        }
+        w[i] = v;
+    }
+}
+
+// Conversion of a state between the domains: beta = eps (log u + 1/2)
+// (to_log) or u = exp(beta / eps - 1/2), the substitution of Eq. (27).
+__global__ void k_convert_domain(double* __restrict__ v, int64_t n, double eps, int to_log) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = to_log ? eps * (log(v[i]) + 0.5) : exp(v[i] / eps - 0.5);
+}
+
 // ------------------------------------------------------------ gradient
 // acc[i] -= (p[i] + q[i]) / 2: a self term's two sides in the divergence's gradient.
 __global__ void k_sub_half_sum(double* __restrict__ acc, const double* __restrict__ p, const double* __restrict__ q,
@@ -529,13 +588,13 @@ __global__ void k_sub_half_sum(double* __restrict__ acc, const double* __restric
 }
 
 
-// Dual variable of a marginal constraint from its scaling vector, in caller
-// order: beta_i = eps (1/2 + log u_i), the substitution alpha_i =
+// Dual variable of a marginal constraint from its scaling vector (or the
+// dual variables themselves, as_is: the log domain), in caller order: beta_i = eps (1/2 + log u_i), the substitution alpha_i =
 // exp(lambda beta_i - 1/2) of Eq. (27) inverted (lambda = 1 / eps).
 __global__ void k_dual_variable(const double* __restrict__ scal, const int* __restrict__ perm, int64_t n, double eps,
-                                double* __restrict__ out) {
+                                int as_is, double* __restrict__ out) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) out[perm[i]] = eps * (0.5 + log(scal[i]));
+    if (i < n) out[perm[i]] = as_is ? scal[i] : eps * (0.5 + log(scal[i]));
 }
 
 // w_j = v_j (y_jt - c_t): a scaling vector times one coordinate relative to
@@ -549,15 +608,19 @@ __global__ void k_weighted_coord(const double* __restrict__ scal, const T* __res
 
 // Position gradient for r = 2, coordinate t, in caller order (row-major n x d):
 // sum_j pi_ij 2 (x_it - y_jt) = 2 u_i ((x_it - c_t) (K v)_i - (K (v (y_t - c_t)))_i).
+// In the log domain scal holds beta and the products were formed with the
+// shifted weights, so the prefactor is u_i e^(lam shift) = exp(lam (beta_i + shift) - 1/2).
 template <typename T>
 __global__ void k_position_gradient(const double* __restrict__ scal, const T* __restrict__ coord,
                                     const double* __restrict__ t0, const double* __restrict__ tt,
                                     const int* __restrict__ perm, int64_t n, int d, int t, double inv_nos,
-                                    double inv_s, double* __restrict__ grad) {
+                                    double inv_s, const double* __restrict__ log_shift, double lam,
+                                    double* __restrict__ grad) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double xc = (double(coord[i]) * inv_nos - 0.5) * inv_s;
-    grad[int64_t(perm[i]) * d + t] = 2.0 * scal[i] * (xc * t0[i] - tt[i]);
+    const double u = log_shift ? exp(lam * (scal[i] + *log_shift) - 0.5) : scal[i];
+    grad[int64_t(perm[i]) * d + t] = 2.0 * u * (xc * t0[i] - tt[i]);
 }
 
 template <typename T>
@@ -569,17 +632,19 @@ void launch_weighted_coord(const double* scal, const void* coord, int64_t n, dou
 
 template <typename T>
 void launch_position_gradient(const double* scal, const void* coord, const double* t0, const double* tt,
-                              const int* perm, int64_t n, int d, int t, double inv_nos, double inv_s, double* grad,
-                              cudaStream_t s) {
+                              const int* perm, int64_t n, int d, int t, double inv_nos, double inv_s,
+                              const double* log_shift, double lam, double* grad, cudaStream_t s) {
     k_position_gradient<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(scal, static_cast<const T*>(coord), t0, tt, perm,
-                                                                     n, d, t, inv_nos, inv_s, grad);
+                                                                     n, d, t, inv_nos, inv_s, log_shift, lam, grad);
 }
 
 template void launch_weighted_coord<float>(const double*, const void*, int64_t, double, double, double*, cudaStream_t);
 template void launch_weighted_coord<double>(const double*, const void*, int64_t, double, double, double*, cudaStream_t);
 template void launch_position_gradient<float>(const double*, const void*, const double*, const double*, const int*,
-                                              int64_t, int, int, double, double, double*, cudaStream_t);
+                                              int64_t, int, int, double, double, const double*, double, double*,
+                                              cudaStream_t);
 template void launch_position_gradient<double>(const double*, const void*, const double*, const double*, const int*,
-                                               int64_t, int, int, double, double, double*, cudaStream_t);
+                                               int64_t, int, int, double, double, const double*, double, double*,
+                                               cudaStream_t);
 
 }  // namespace sk

@@ -10,7 +10,7 @@ void bin_shape(int d, int W, int B[3]);
 __global__ void k_point_bounds(const double* x, int64_t n, int d, double* partial);
 __global__ void k_point_radius(const double* x, int64_t n, int d, double c0, double c1, double c2, double* partial);
 __global__ void k_weight_stats(const double* w, int64_t n, double* partial);
-__global__ void k_sum_marg_log(const double* marg, const double* scal, int64_t n, double* partial);
+__global__ void k_sum_marg_log(const double* marg, const double* scal, int64_t n, int as_is, double* partial);
 __global__ void k_combine(const double* partial, int nblocks, int nf, int op0, int op1, int op2, int op3, int op4,
                           int op5, int op6, double* out);
 
@@ -26,14 +26,18 @@ void launch_gather_points(const int* perm, int64_t n, int d, T* const in[3], T* 
 __global__ void k_bin_starts(const int* key_start, int nbins, int bvol, int* bin_start);
 __global__ void k_count_tasks(const int* bin_start, int nbins, int maxpts, int ncol, int* ntask);
 __global__ void k_sub_half_sum(double* acc, const double* p, const double* q, int64_t n);
-__global__ void k_dual_variable(const double* scal, const int* perm, int64_t n, double eps, double* out);
+__global__ void k_dual_variable(const double* scal, const int* perm, int64_t n, double eps, int as_is, double* out);
 template <typename T>
 void launch_weighted_coord(const double* scal, const void* coord, int64_t n, double inv_nos, double inv_s, double* w,
                            cudaStream_t s);
 template <typename T>
 void launch_position_gradient(const double* scal, const void* coord, const double* t0, const double* tt,
-                              const int* perm, int64_t n, int d, int t, double inv_nos, double inv_s, double* grad,
-                              cudaStream_t s);
+                              const int* perm, int64_t n, int d, int t, double inv_nos, double inv_s,
+                              const double* log_shift, double lam, double* grad, cudaStream_t s);
+__global__ void k_block_max(const double* v, int64_t n, double* partial);
+__global__ void k_log_weights(const double* g, int64_t n, const double* partial, int nparts, double lam, int fp32,
+                              double* w, double* shift);
+__global__ void k_convert_domain(double* v, int64_t n, double eps, int to_log);
 __global__ void k_col_counts(const int* key_start, int nbins, int bvol, int ncol, int bz, int* count);
 __global__ void k_fill_tasks(const int* ntask_off, int nbins, int ncol, int* task);
 __global__ void k_count_subs(const int* bin_start, int nbins, int maxpts, int* nsub);
