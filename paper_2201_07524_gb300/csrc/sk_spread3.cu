@@ -8,12 +8,11 @@
 // window, so a warp keeps the column's whole window -- W^2 rows by (8 + W - 1)
 // z-cells -- in registers, two rows per lane for W = 8:
 //
-//   * each batch of 32 points is first ordered by the z-offset of the points'
-//     cells inside the column (warp ballots), then one lane per point
-//     evaluates that point's 3W window weights into its row of a per-warp
-//     table in shared memory, so the points of equal offset are consecutive
-//     rows and every segment of equal offset has compile-time register
-//     indices;
+//   * one lane per point evaluates that point's 3W window weights into its
+//     row of a per-warp table in shared memory; a column's points come in
+//     non-decreasing z-offset (the sort key), so the points of equal offset
+//     are consecutive rows and every segment of equal offset has
+//     compile-time register indices;
 //   * for each point, every lane scales its rows by the x (and y) weights and
 //     adds (or, when interpolating, gathers) the W z-taps with plain FMAs;
 //   * spreading flushes a finished column into the bin's shared-memory
@@ -218,22 +217,11 @@ __device__ __forceinline__ void row_products(const T* row, const int (&ri)[Q], c
 }
 
 // ------------------------------------------------------------ sorted batches
-// A batch of 32 points is ordered by the z-offset of the
-// points' cells inside the column before the weights are written, so the
-// points of equal offset are consecutive table rows.  Returns this lane's row
-// (lanes with mydz < 0 have none).
-template <int BZ>
-__device__ __forceinline__ int sort_batch(int mydz, int lane) {
-    const unsigned below = (1u << lane) - 1u;
-    int pos = 0, acc = 0;
-#pragma unroll
-    for (int d = 0; d < BZ; ++d) {
-        const unsigned m = __ballot_sync(0xffffffffu, mydz == d);
-        if (mydz == d) pos = acc + __popc(m & below);
-        acc += __popc(m);
-    }
-    return pos;
-}
+// The plan sorts points by (bin, cell inside the bin) with the z axis
+// fastest, from the same rounded coordinates the kernels floor, so the
+// points of a column -- and of every batch of 32 consecutive ones -- come in
+// non-decreasing z-offset: lane l's point is table row l, and the points of
+// equal offset are consecutive rows (a segment, counted with one ballot).
 
 // With 32 a multiple of W and W^2 a multiple of 32, all rows of a lane share
 // j = lane % W, and its x-taps are i = lane / W + q (32 / W), q < Q.  The
@@ -493,7 +481,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 
             for (int base = start; base < end; base += 32) {
                 const int cnt = min(32, end - base);
                 const int mydz = lane < cnt ? int(floor(pf.u2)) - z0 : -1;
-                const int pos = sort_batch<G::BZ>(mydz, lane);
+                const int pos = lane;   // a column's points are ordered by z-offset (the sort key)
                 if (lane < cnt) fill_row_sorted<W, T>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp);
                 pf.load(c0, c1, c2, a.w, base + 32 + lane, base + 32 + lane < end);
                 __syncwarp();
@@ -618,7 +606,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (W <= 8 ? 3 : 2) : (W <=
         for (int base = cur.start; base < cur.end; base += 32) {
             const int cnt = min(32, cur.end - base);
             const int mydz = lane < cnt ? int(floor(pf.u2)) - z0 : -1;
-            const int pos = sort_batch<G::BZ>(mydz, lane);
+            const int pos = lane;   // a column's points are ordered by z-offset (the sort key)
             if (lane < cnt) fill_row_sorted<W, T>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, T(1), a.wp);
             const EpiPrefetch epc = ep;
             // the next batch: this column's, else the next column's first
