@@ -266,19 +266,17 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// a / t in FP64 for t > 0 in the FP32 normal range: an FP32 reciprocal seed
-// (relative error ~2^-23) refined by one Newton-Raphson step for 1/t, which
-// squares the error, then a Newton correction of the quotient itself,
-// q <- q + r (a - t q).  Five FP64 operations instead of a full IEEE division,
-// whose FP64 cost dominates on this GPU; outside that range it divides.
-__device__ __forceinline__ double div_newton(double a, double t) {
-    const float tf = float(t);
+// a / t in FP64 for t > 0 in the FP32 normal range (tf = float(t)): the FP32
+// reciprocal r (relative error below 2^-23) gives q = a r, and one Newton
+// correction of the quotient, q + r (a - t q), squares that error (below
+// 2^-45 relative, far under the error of the kernel sums t).  Four FP64
+// operations instead of a full IEEE division, whose FP64 cost dominates on
+// this GPU; outside that range it divides.
+__device__ __forceinline__ double div_newton(double a, double t, float tf) {
     if (!(tf >= 1.17549435e-38f) || !(tf <= 3.0e38f)) return a / t;
-    double r = double(__frcp_rn(tf));
-    r = fma(r, fma(-t, r, 1.0), r);
-    double q = a * r;
-    q = fma(r, fma(-t, q, a), q);
-    return q;
+    const double r = double(__frcp_rn(tf));
+    const double q = a * r;
+    return fma(r, fma(-t, q, a), q);
 }
 
 // log v for v > 0 in the FP32 normal range, split as e ln 2 + log(m) with
@@ -344,7 +342,7 @@ __device__ __forceinline__ void epi_point(const Epilogue& e, int64_t i, double t
     if (e.mode == EPI_UPDATE) {
         const float tf = float(t);
         if (!(tf >= 1.17549435e-38f && tf <= 3.0e38f)) bad += 1.0;
-        e.scal[i] = div_newton(a, t);
+        e.scal[i] = div_newton(a, t, tf);
     } else {
         dot = fma(q, t, dot);
         e.t_store[i] = t;
@@ -380,7 +378,7 @@ __device__ __forceinline__ void epi_point_pre(const Epilogue& e, int64_t i, doub
     if (e.mode == EPI_UPDATE) {
         const float tf = float(t);
         if (!(tf >= 1.17549435e-38f && tf <= 3.0e38f)) bad += 1.0;
-        e.scal[i] = div_newton(a, t);
+        e.scal[i] = div_newton(a, t, tf);
     } else {
         dot = fma(q, t, dot);
         e.t_store[i] = t;

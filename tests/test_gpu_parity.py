@@ -226,6 +226,24 @@ def test_solve_direct_method_matches_oracle():
     assert abs(res["s"] - ref["s"]) / abs(ref["s"]) <= 1e-5
 
 
+def test_fp64_direct_solve_state_matches_oracle_closely():
+    # FP64 direct sums are exact to ~1e-15, so after 20 iterations the state
+    # pins the fused FP64 update (the Newton quotient a / t) to 1e-11
+    d, n, m, eps, iters = 2, 400, 300, 0.05, 20
+    x = wl.uniform_ball(n, d, 0.2, 27)
+    y = wl.uniform_ball(m, d, 0.2, 28)
+    a, b = wl.dirichlet_weights(n, 29), wl.dirichlet_weights(m, 30)
+    ref = osk.sinkhorn_dense(x, a, y, b, eps, 2.0, iters)
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), eps, 2.0, sk.sk_default_params(precision=sk.SK_FP64))
+    sk.sk_set_method(plan, sk.SK_METHOD_DIRECT)
+    u = torch.zeros(n, dtype=torch.float64, device=DEV)
+    v = torch.zeros(m, dtype=torch.float64, device=DEV)
+    st, res = sk.sk_solve(plan, iters, u_out=u, v_out=v)
+    assert np.max(np.abs(u.cpu().numpy() / ref["u"] - 1)) <= 1e-11
+    assert np.max(np.abs(v.cpu().numpy() / ref["v"] - 1)) <= 1e-11
+    assert abs(res["s"] - ref["s"]) <= 1e-11 * abs(ref["s"])
+
+
 def test_state_checkpoint_and_resume_is_exact():
     x = wl.uniform_ball(800, 2, 0.2, 27)
     y = wl.uniform_ball(600, 2, 0.2, 28)
