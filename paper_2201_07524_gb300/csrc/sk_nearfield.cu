@@ -9,8 +9,8 @@
 // eps_I / 2 over the unit torus, so every neighbour of a point lies in the 5^d
 // cells around its own.  One block takes one non-empty target cell; the
 // sources of the surrounding cells are staged through shared memory in tiles;
-// each thread owns up to kNearPerThread targets.  Partial sums are FP32 per
-// tile and FP64 across tiles.
+// its 512 work items cover the cell's targets, several copies per target when
+// the cell holds few.  Partial sums are FP32 per tile and FP64 across tiles.
 #include <type_traits>
 
 #include "sk_internal.cuh"
@@ -18,7 +18,7 @@
 namespace sk {
 
 constexpr int kNearTile = 512;   // sources staged per tile
-constexpr int kNearPerThread = 2;   // 512 target slots per block: a cell holds a few hundred
+constexpr int kNearPerThread = 2;   // 512 work items per block pass
 constexpr int kNearThreads = 256;
 
 // Cell of each point in the near-field cell list (coordinates in grid units).
@@ -89,10 +89,19 @@ __device__ __forceinline__ T pair_term(T d2, T w, T r2max, T inv_r2, T kc, T hal
 }
 
 // NP: polynomial length of K_I (the plan's p; kMaxP covers every p with zero padding).
+// A pass over a cell's targets has 512 work items (kNearThreads threads x
+// kNearPerThread): `slots` target slots (the pass's targets rounded up to a
+// power of two >= 32) times `copies` = 512 / slots copies, copy c taking the
+// staged sources j = c, c + copies, ...; the copies' sums are combined in
+// shared memory.  A sparse cell so keeps every lane busy with real pairs.
+// Thread t holds slots t % per + q per (per = slots / kNearPerThread) of copy
+// t / per.
 template <int D, typename T, bool R1, int NP>
 __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
     using V = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+    constexpr int kItems = kNearThreads * kNearPerThread;
     __shared__ V src[kNearTile];   // (x, y, z, w) of the staged sources
+    __shared__ double red[kItems];
     const int cell = a.tasks[blockIdx.x];
     int cc[3] = {0, 0, 0};
     {
@@ -115,15 +124,26 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
         lo[t] = t < D ? max(0, cc[t] - 2) : 0;
         hi[t] = t < D ? min(a.nc - 1, cc[t] + 2) : 0;
     }
-    for (int tb = ts; tb < te; tb += kNearThreads * kNearPerThread) {
+    for (int tb = ts; tb < te; tb += kItems) {
+        const int rem = min(kItems, te - tb);
+        int slots = 32;
+        while (slots < rem) slots <<= 1;
+        const int copies = kItems / slots;
+        // a thread's kNearPerThread slots share one copy, so each staged source
+        // it reads serves all of them
+        const int per = slots / kNearPerThread;          // threads per copy
+        const int copy = threadIdx.x / per;
         T xt[kNearPerThread][3];
+        int slot[kNearPerThread];
         double acc[kNearPerThread];
 #pragma unroll
         for (int q = 0; q < kNearPerThread; ++q) {
-            const int i = tb + q * kNearThreads + threadIdx.x;
+            slot[q] = threadIdx.x % per + q * per;
+            const int i = tb + slot[q];
+            const bool ok = slot[q] < rem;
             acc[q] = 0.0;
 #pragma unroll
-            for (int t = 0; t < 3; ++t) xt[q][t] = (t < D && i < te) ? tc[t][i] : (t < D ? T(1e18) : T(0));
+            for (int t = 0; t < 3; ++t) xt[q][t] = (t < D && ok) ? tc[t][i] : (t < D ? T(1e18) : T(0));
         }
         for (int c0 = lo[0]; c0 <= hi[0]; ++c0)
             for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
@@ -148,23 +168,28 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
 #pragma unroll
                         for (int q = 0; q < kNearPerThread; ++q) part[q] = T(0);
 #pragma unroll 2
-                        for (int j = 0; j < cnt; ++j) {
-                            const V s = src[j];
+                        for (int j = copy; j < cnt; j += copies) {
+                            const V sv = src[j];
 #pragma unroll
                             for (int q = 0; q < kNearPerThread; ++q) {
-                                const T dx = xt[q][0] - s.x, dy = xt[q][1] - s.y, dz = xt[q][2] - s.z;
+                                const T dx = xt[q][0] - sv.x, dy = xt[q][1] - sv.y, dz = xt[q][2] - sv.z;
                                 const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                                part[q] += pair_term<T, R1, NP>(d2, s.w, r2max, inv_r2, kc, half_r, ki);
+                                part[q] += pair_term<T, R1, NP>(d2, sv.w, r2max, inv_r2, kc, half_r, ki);
                             }
                         }
 #pragma unroll
                         for (int q = 0; q < kNearPerThread; ++q) acc[q] += double(part[q]);
                     }
                 }
+        // combine the copies of each target slot (deterministic order)
+        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kNearPerThread; ++q) {
-            const int i = tb + q * kNearThreads + threadIdx.x;
-            if (i < te) a.out[a.t_idx[i]] = acc[q];
+        for (int q = 0; q < kNearPerThread; ++q) red[copy * slots + slot[q]] = acc[q];
+        __syncthreads();
+        for (int slot = threadIdx.x; slot < rem; slot += kNearThreads) {
+            double t = 0.0;
+            for (int c = 0; c < copies; ++c) t += red[c * slots + slot];
+            a.out[a.t_idx[tb + slot]] = t;
         }
     }
 }
