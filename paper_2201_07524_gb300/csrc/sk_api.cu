@@ -20,6 +20,7 @@ struct sk_plan {
     int precision = SK_FP32;
     int method = SK_METHOD_NFFT;
     int domain = SK_DOMAIN_SCALING;
+    int near_sub = 2;           // near-field cells per eps_I (2, or 4 for dense clouds)
     double* shift = nullptr;    // log domain: max of the Y ([0]) and X ([1]) dual variables
     int N = 0, h = 0, n_os = 0, log2n = 0, W = 0, B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 0, bvol = 1;
     int64_t nkeys = 0;
@@ -476,10 +477,44 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
     CK(cudaFreeAsync(suboff, P->ps));
 }
 
-// Near-field cell list of one cloud: cubic cells of side 1/nc >= eps_I / 2
-// over the unit torus (so all pairs closer than eps_I lie in the 5^d cells
-// around a point's own), the cloud in that order, and its non-empty cells.
-int near_cells_per_dim(const sk_plan* P) { return std::max(1, int(std::floor(2.0 / P->prm.eps_I))); }
+// Near-field cell list of one cloud: cubic cells of side 1/nc >= eps_I / kNearSub
+// over the unit torus (so all pairs closer than eps_I lie within kNearSub
+// cells of a point's own along every axis; the kernel prunes the cells that
+// cannot hold such a pair), the cloud in that order, and its non-empty cells.
+int near_cells_per_dim(const sk_plan* P) { return std::max(1, int(std::floor(P->near_sub / P->prm.eps_I))); }
+
+// Non-empty near-field cells of cloud c at the plan's current cell size.
+template <typename T>
+int near_occupied_cells(sk_plan* P, Cloud& c) {
+    const int nc = near_cells_per_dim(P);
+    int ncells = 1;
+    for (int t = 0; t < P->d; ++t) ncells *= nc;
+    int *key = nullptr, *count = nullptr, *nonempty = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&key), size_t(c.n) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&count), size_t(ncells) * sizeof(int), P->ps));
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&nonempty), sizeof(int), P->ps));
+    CK(cudaMemsetAsync(count, 0, size_t(ncells) * sizeof(int), P->ps));
+    CK(cudaMemsetAsync(nonempty, 0, sizeof(int), P->ps));
+    launch_near_keys<T>(c.coord, c.n, P->d, double(nc) / P->n_os, nc, key, count, P->ps);
+    CK(cudaGetLastError());
+    launch_count_nonempty(count, ncells, nonempty, P->ps);
+    CK(cudaGetLastError());
+    const int occ = read_int(P, nonempty);
+    CK(cudaFreeAsync(key, P->ps));
+    CK(cudaFreeAsync(count, P->ps));
+    CK(cudaFreeAsync(nonempty, P->ps));
+    return occ;
+}
+
+// Cells per eps_I of the near-field lists: 4 (finer cells, fewer pairs outside
+// eps_I examined) when the cells at 2 would hold 256 points or more on average,
+// else 2 (a block's target slots are filled in units of 32).
+template <typename T>
+void choose_near_sub(sk_plan* P) {
+    P->near_sub = 2;
+    const int occ = near_occupied_cells<T>(P, P->X) + near_occupied_cells<T>(P, P->Y);
+    if (occ > 0 && double(P->X.n + P->Y.n) / occ >= 256.0) P->near_sub = 4;
+}
 
 template <typename T>
 void build_near(sk_plan* P, Cloud& c) {
@@ -751,6 +786,7 @@ void product(sk_plan* P, Cloud& src, const double* w, Cloud& dst, const Epilogue
         na.w = w;
         na.tasks = dst.nf_tasks;
         na.nc = near_cells_per_dim(P);
+        na.sub = P->near_sub;
         const double rg = P->n_os * P->prm.eps_I;
         na.r2max = rg * rg;
         na.inv_r2 = 1.0 / (rg * rg);
@@ -1258,6 +1294,7 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
             build_cloud<float>(P, P->X, xs, as, n);
             build_cloud<float>(P, P->Y, ys, bs, m);
             if (P->nearfield) {
+                choose_near_sub<float>(P);
                 build_near<float>(P, P->X);
                 build_near<float>(P, P->Y);
             }
@@ -1267,6 +1304,7 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
             build_cloud<double>(P, P->X, xs, as, n);
             build_cloud<double>(P, P->Y, ys, bs, m);
             if (P->nearfield) {
+                choose_near_sub<double>(P);
                 build_near<double>(P, P->X);
                 build_near<double>(P, P->Y);
             }

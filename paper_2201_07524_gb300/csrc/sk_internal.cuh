@@ -171,6 +171,7 @@ struct NearArgs {
     const double* w;          // source weights in sorted order
     const int* tasks;         // non-empty target cells
     int nc;                   // near-field cells per dimension
+    int sub;                  // cells per eps_I (2 or 4)
     double r2max;             // (n_os eps_I)^2: squared near-field radius in grid units
     double inv_r2;            // 1 / r2max
     double kcoef;             // K = exp(-kcoef |du|^r) with kcoef = 1 / (eps_s n_os^r)
@@ -229,6 +230,7 @@ void launch_near_scatter(const int* key, int64_t n, const int* start, int* curso
 template <typename T> void launch_near_gather(const int* idx, int64_t n, int d, void* const u[3], void* const o[3],
                                               cudaStream_t s);
 void launch_near_tasks(const int* start, int ncells, int* tasks, int* ntasks, cudaStream_t s);
+void launch_count_nonempty(const int* count, int ncells, int* nonempty, cudaStream_t s);
 template <typename T> cudaError_t launch_nearfield(int d, const NearArgs& a, int ntasks, cudaStream_t s);
 template <typename T> cudaError_t launch_direct(int d, const DirectArgs& a, const Epilogue& e,
                                                 int64_t* launches, cudaStream_t s);

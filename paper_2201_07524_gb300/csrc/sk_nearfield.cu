@@ -6,9 +6,15 @@
 // restores the exact kernel near 0.
 //
 // Both clouds carry a second cell list at plan time: cubic cells of side
-// eps_I / 2 over the unit torus, so every neighbour of a point lies in the 5^d
-// cells around its own.  One block takes one non-empty target cell; the
-// sources of the surrounding cells are staged through shared memory in tiles;
+// h >= eps_I / K (K = 2, or 4 when the cells at K = 2 would hold 256 points
+// or more on average) over the unit torus, so every neighbour of a
+// point lies within K cells of its own along each axis.  Of those (2K+1)^d
+// cells only the ones whose closest approach to the target cell,
+// h sqrt(sum_t max(|o_t| - 1, 0)^2) for offset o, is below eps_I can hold a
+// pair; along the last axis (the fastest in the cell order) the kept cells
+// of each row form one contiguous source range.  One block takes one
+// non-empty target cell; the sources of those rows are staged through shared
+// memory in tiles;
 // its 512 work items cover the cell's targets, several copies per target when
 // the cell holds few.  Partial sums are FP32 per tile and FP64 across tiles.
 #include <type_traits>
@@ -61,6 +67,12 @@ __global__ void k_near_gather(const int* __restrict__ idx, int64_t n, int d, con
     if (d > 2) o2[i] = u2[p];
 }
 
+// Non-empty cells of a count array.
+__global__ void k_count_nonempty(const int* __restrict__ count, int ncells, int* __restrict__ nonempty) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncells && count[c] > 0) atomicAdd(nonempty, 1);
+}
+
 // Non-empty cells of the list (one block task each).
 __global__ void k_near_tasks(const int* __restrict__ start, int ncells, int* __restrict__ tasks,
                              int* __restrict__ ntasks) {
@@ -96,7 +108,7 @@ __device__ __forceinline__ T pair_term(T d2, T w, T r2max, T inv_r2, T kc, T hal
 // shared memory.  A sparse cell so keeps every lane busy with real pairs.
 // Thread t holds slots t % per + q per (per = slots / kNearPerThread) of copy
 // t / per.
-template <int D, typename T, bool R1, int NP>
+template <int D, typename T, bool R1, int NP, int K>
 __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
     using V = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
     constexpr int kItems = kNearThreads * kNearPerThread;
@@ -119,11 +131,8 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
     T ki[kMaxP];
 #pragma unroll
     for (int k = 0; k < kMaxP; ++k) ki[k] = k < a.p ? T(a.ki[k]) : T(0);
-    int lo[3], hi[3];
-    for (int t = 0; t < 3; ++t) {
-        lo[t] = t < D ? max(0, cc[t] - 2) : 0;
-        hi[t] = t < D ? min(a.nc - 1, cc[t] + 2) : 0;
-    }
+    // outer axes: 0 and 1 for D = 3, 0 for D = 2, none for D = 1
+    const int r0 = D == 3 ? K : 0, r1 = D >= 2 ? K : 0;
     for (int tb = ts; tb < te; tb += kItems) {
         const int rem = min(kItems, te - tb);
         int slots = 32;
@@ -145,51 +154,66 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
 #pragma unroll
             for (int t = 0; t < 3; ++t) xt[q][t] = (t < D && ok) ? tc[t][i] : (t < D ? T(1e18) : T(0));
         }
-        for (int c0 = lo[0]; c0 <= hi[0]; ++c0)
-            for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
-                for (int c2 = lo[2]; c2 <= hi[2]; ++c2) {
-                    int sc_id = c0;
-                    if (D > 1) sc_id = sc_id * a.nc + c1;
-                    if (D > 2) sc_id = sc_id * a.nc + c2;
-                    const int ss = a.s_start[sc_id], se = a.s_start[sc_id + 1];
-                    for (int s0 = ss; s0 < se; s0 += kNearTile) {
-                        const int cnt = min(kNearTile, se - s0);
-                        __syncthreads();
-                        for (int j = threadIdx.x; j < cnt; j += kNearThreads) {
-                            V v;
-                            v.x = scd[0][s0 + j];
-                            v.y = D > 1 ? scd[1][s0 + j] : T(0);
-                            v.z = D > 2 ? scd[2][s0 + j] : T(0);
-                            v.w = T(a.w[a.s_idx[s0 + j]]);
-                            src[j] = v;
-                        }
-                        __syncthreads();
-                        T part[kNearPerThread];
-#pragma unroll
-                        for (int q = 0; q < kNearPerThread; ++q) part[q] = T(0);
-#pragma unroll 2
-                        for (int j = copy; j < cnt; j += copies) {
-                            const V sv = src[j];
-#pragma unroll
-                            for (int q = 0; q < kNearPerThread; ++q) {
-                                const T dx = xt[q][0] - sv.x, dy = xt[q][1] - sv.y, dz = xt[q][2] - sv.z;
-                                const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                                part[q] += pair_term<T, R1, NP>(d2, sv.w, r2max, inv_r2, kc, half_r, ki);
-                            }
-                        }
-#pragma unroll
-                        for (int q = 0; q < kNearPerThread; ++q) acc[q] += double(part[q]);
-                    }
+        for (int o0 = -r0; o0 <= r0; ++o0)
+            for (int o1 = -r1; o1 <= r1; ++o1) {
+                // the row of cells along the last axis at outer offsets (o0, o1)
+                int m2 = 0, row = 0;
+                bool inside = true;
+                if (D == 3) {
+                    const int c0 = cc[0] + o0, c1 = cc[1] + o1;
+                    inside = c0 >= 0 && c0 < a.nc && c1 >= 0 && c1 < a.nc;
+                    m2 = max(abs(o0) - 1, 0) * max(abs(o0) - 1, 0) + max(abs(o1) - 1, 0) * max(abs(o1) - 1, 0);
+                    row = (c0 * a.nc + c1) * a.nc;
+                } else if (D == 2) {
+                    const int c0 = cc[0] + o1;
+                    inside = c0 >= 0 && c0 < a.nc;
+                    m2 = max(abs(o1) - 1, 0) * max(abs(o1) - 1, 0);
+                    row = c0 * a.nc;
                 }
+                if (!inside || m2 >= K * K) continue;
+                int mz = 0;   // largest gap (in cells) along the last axis with m2 + gap^2 < K^2
+                while ((mz + 1) * (mz + 1) + m2 < K * K) ++mz;
+                const int cl = cc[D - 1];
+                const int zl = max(0, cl - 1 - mz), zh = min(a.nc - 1, cl + 1 + mz);
+                const int ss = a.s_start[row + zl], se = a.s_start[row + zh + 1];
+                for (int s0 = ss; s0 < se; s0 += kNearTile) {
+                    const int cnt = min(kNearTile, se - s0);
+                    __syncthreads();
+                    for (int j = threadIdx.x; j < cnt; j += kNearThreads) {
+                        V v;
+                        v.x = scd[0][s0 + j];
+                        v.y = D > 1 ? scd[1][s0 + j] : T(0);
+                        v.z = D > 2 ? scd[2][s0 + j] : T(0);
+                        v.w = T(a.w[a.s_idx[s0 + j]]);
+                        src[j] = v;
+                    }
+                    __syncthreads();
+                    T part[kNearPerThread];
+#pragma unroll
+                    for (int q = 0; q < kNearPerThread; ++q) part[q] = T(0);
+#pragma unroll 2
+                    for (int j = copy; j < cnt; j += copies) {
+                        const V sv = src[j];
+#pragma unroll
+                        for (int q = 0; q < kNearPerThread; ++q) {
+                            const T dx = xt[q][0] - sv.x, dy = xt[q][1] - sv.y, dz = xt[q][2] - sv.z;
+                            const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                            part[q] += pair_term<T, R1, NP>(d2, sv.w, r2max, inv_r2, kc, half_r, ki);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kNearPerThread; ++q) acc[q] += double(part[q]);
+                }
+            }
         // combine the copies of each target slot (deterministic order)
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < kNearPerThread; ++q) red[copy * slots + slot[q]] = acc[q];
         __syncthreads();
-        for (int slot = threadIdx.x; slot < rem; slot += kNearThreads) {
+        for (int sl = threadIdx.x; sl < rem; sl += kNearThreads) {
             double t = 0.0;
-            for (int c = 0; c < copies; ++c) t += red[c * slots + slot];
-            a.out[a.t_idx[tb + slot]] = t;
+            for (int c = 0; c < copies; ++c) t += red[c * slots + sl];
+            a.out[a.t_idx[tb + sl]] = t;
         }
     }
 }
@@ -214,6 +238,10 @@ void launch_near_gather(const int* idx, int64_t n, int d, void* const u[3], void
         static_cast<T*>(o[0]), static_cast<T*>(o[1]), static_cast<T*>(o[2]));
 }
 
+void launch_count_nonempty(const int* count, int ncells, int* nonempty, cudaStream_t s) {
+    k_count_nonempty<<<unsigned((ncells + 255) / 256), 256, 0, s>>>(count, ncells, nonempty);
+}
+
 void launch_near_tasks(const int* start, int ncells, int* tasks, int* ntasks, cudaStream_t s) {
     k_near_tasks<<<unsigned((ncells + 255) / 256), 256, 0, s>>>(start, ncells, tasks, ntasks);
 }
@@ -223,7 +251,11 @@ cudaError_t launch_nearfield(int d, const NearArgs& a, int ntasks, cudaStream_t 
     if (ntasks == 0) return cudaSuccess;
     const bool r1 = a.r == 1.0;
     const bool p8 = a.p == 8;
-#define SK_NF(DD, R, NP) k_nearfield<DD, T, R, NP><<<ntasks, kNearThreads, 0, s>>>(a)
+#define SK_NF(DD, R, NP)                                                              \
+    if (a.sub == 4)                                                                   \
+        k_nearfield<DD, T, R, NP, 4><<<ntasks, kNearThreads, 0, s>>>(a);              \
+    else                                                                              \
+        k_nearfield<DD, T, R, NP, 2><<<ntasks, kNearThreads, 0, s>>>(a)
 #define SK_NF_D(DD)                                  \
     if (r1 && p8) SK_NF(DD, true, 8);                 \
     else if (r1) SK_NF(DD, true, kMaxP);              \
