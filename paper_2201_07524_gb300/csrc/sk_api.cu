@@ -467,6 +467,41 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
             CK(cudaMemcpyAsync(c.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
         CK(cudaStreamSynchronize(P->ps));
     }
+    // 2-D strip tasks: runs of at most kStripMaxPts points of one bin, most
+    // points first, so the warps that take the last tasks take short ones.
+    // Small clouds take shorter runs (down to one batch of 32) so that their
+    // tasks still reach every SM.
+    if (P->d == 2) {
+        int dev = 0, sms = 1;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t per_warp = (n + int64_t(sms) * 8 - 1) / (int64_t(sms) * 8);
+        const int run = int(std::min<int64_t>(kStripMaxPts, std::max<int64_t>(32, (per_warp + 31) / 32 * 32)));
+        std::vector<int> bs(size_t(P->nbins) + 1);
+        CK(cudaMemcpyAsync(bs.data(), c.bin_start, bs.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+        std::vector<int> tk;
+        for (int b = 0; b < P->nbins; ++b)
+            for (int s0 = bs[b]; s0 < bs[b + 1]; s0 += run) {
+                tk.push_back(b);
+                tk.push_back(s0);
+                tk.push_back(std::min(bs[b + 1], s0 + run));
+            }
+        const int nt = int(tk.size() / 3);
+        std::vector<int> order(nt);
+        for (int i = 0; i < nt; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+            return tk[3 * p + 2] - tk[3 * p + 1] > tk[3 * q + 2] - tk[3 * q + 1];
+        });
+        std::vector<int> sorted(tk.size());
+        for (int i = 0; i < nt; ++i)
+            for (int k = 0; k < 3; ++k) sorted[3 * i + k] = tk[3 * order[i] + k];
+        c.nstasks = nt;
+        c.stasks = static_cast<int*>(dalloc(P, size_t(3 * std::max(nt, 1)) * sizeof(int)));
+        if (nt > 0)
+            CK(cudaMemcpyAsync(c.stasks, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+    }
     k_fill<<<nblk(n), 256, 0, P->ps>>>(c.scal, n, 1.0);
     CK(cudaGetLastError());
     CK(cudaFreeAsync(tmp_u, P->ps));
@@ -666,6 +701,11 @@ void prepare_kernels(sk_plan* P) {
         ia.ncols = 0;
         CK(launch_interp3<T>(P->W, ia, Epilogue{}, P->ps));
     }
+    if (P->d == 2) {
+        InterpArgs ia{};
+        ia.nstasks = 0;
+        CK(launch_interp2<T>(P->W, ia, Epilogue{}, P->ps));
+    }
     CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
 }
 
@@ -724,6 +764,9 @@ void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
     a.key_start = src.key_start;
     a.tasks = src.tasks;
     a.ntasks = src.ntasks;
+    a.stasks = src.stasks;
+    a.nstasks = src.nstasks;
+    a.queue = P->ticket + 4;
     a.n_os = P->n_os;
     for (int t = 0; t < 3; ++t) a.nb[t] = P->nb[t];
     a.beta = P->beta;
@@ -732,7 +775,7 @@ void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
     a.wp = P->wp;
     const int st = stage_begin(P, SK_STAGE_SPREAD);
     CK(launch_spread<T>(P->d, P->W, a, P->ps));
-    if ((column_kernels(P->d, P->W) ? src.ntasks : src.nsub) > 0) ++P->launches;
+    if ((column_kernels(P->d, P->W) ? src.ntasks : (P->d == 2 ? src.nstasks : src.nsub)) > 0) ++P->launches;
     stage_end(P, st);
 }
 
@@ -750,6 +793,8 @@ void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
     a.knorm = P->knorm;
     a.cols = dst.cols;
     a.ncols = dst.ncols;
+    a.stasks = dst.stasks;
+    a.nstasks = dst.nstasks;
     a.queue = P->ticket + 2;
     a.grid = P->fft.grid_out;
     a.wp = P->wp;
@@ -1178,12 +1223,12 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         const int64_t nmax = std::max(n, m);
         P->partial_blocks = std::max<int64_t>(interp_blocks<double>(nmax), kRedBlocks);
         P->partial = static_cast<double*>(dalloc(P, size_t(P->partial_blocks) * 8 * sizeof(double)));
-        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 4));   // [0] reductions, [2..3] column queue
+        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 8));   // [0] reductions, [2..3] interpolation queue, [4..5] spreading queue
         P->stats = static_cast<double*>(dalloc(P, sizeof(double) * (3 * NSLOTS + 8)));
         P->status = static_cast<int*>(dalloc(P, sizeof(int) * 4));
         P->shift = static_cast<double*>(dalloc(P, sizeof(double) * 2));
         CK(cudaMemsetAsync(P->shift, 0, sizeof(double) * 2, P->ps));
-        CK(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned) * 4, P->ps));
+        CK(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned) * 8, P->ps));
         CK(cudaMemsetAsync(P->stats, 0, sizeof(double) * (3 * NSLOTS + 8), P->ps));
         CK(cudaMemsetAsync(P->status, 0, sizeof(int) * 4, P->ps));
 
@@ -1318,7 +1363,15 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
             prepare_kernels<float>(P);
         else
             prepare_kernels<double>(P);
-        // the column kernels reduce one partial per block
+        // the strip and column kernels reduce one partial per block
+        if (P->d == 2) {
+            const int nt = std::max(P->X.nstasks, P->Y.nstasks);
+            const int need = P->precision == SK_FP32 ? strip2_blocks<float>(P->W, nt) : strip2_blocks<double>(P->W, nt);
+            if (need > P->partial_blocks) {
+                P->partial_blocks = need;
+                P->partial = static_cast<double*>(dalloc(P, size_t(need) * 8 * sizeof(double)));
+            }
+        }
         if (column_kernels(P->d, P->W)) {
             const int ncols = std::max(P->X.ncols, P->Y.ncols);
             const int need = std::max(std::max(P->X.ntasks, P->Y.ntasks),

@@ -75,6 +75,8 @@ struct Cloud {
     int ntasks = 0;
     int* cols = nullptr;        // non-empty (bin, column) pairs, bin * columns + column, most points first (3-D)
     int ncols = 0;
+    int* stasks = nullptr;      // 2-D strip tasks (bin, first point, end point), most points first
+    int nstasks = 0;
     // near-field cell list (only when the kernel needs near-field correction)
     int* nf_start = nullptr;    // CSR over near-field cells
     int* nf_idx = nullptr;      // near-field position -> sorted index
@@ -137,6 +139,9 @@ struct SpreadArgs {
     const int* key_start;  // CSR over sort keys (bin, cell in bin)
     const int* tasks;      // column tasks: (bin, first column, end column)
     int ntasks;
+    const int* stasks;     // 2-D strip tasks: (bin, first point, end point), most points first
+    int nstasks;
+    unsigned* queue;       // 2-D strip queue: [0] next task, [1] warps finished; zero between launches
     int n_os;
     int nb[3];             // bins per dimension
     double beta;           // Kaiser-Bessel shape
@@ -153,6 +158,8 @@ struct InterpArgs {
     int ntasks;
     const int* cols;       // 3-D column queue: (bin, column) codes, most points first
     int ncols;
+    const int* stasks;     // 2-D strip tasks: (bin, first point, end point), most points first
+    int nstasks;
     unsigned* queue;       // [0] next queue entry, [1] warps finished; zero between launches
     int nb[3];
     int n_os;
@@ -217,6 +224,12 @@ template <typename T> int interp_blocks(int64_t n);
 template <typename T> cudaError_t launch_spread3(int W, const SpreadArgs& a, cudaStream_t s);
 template <typename T> cudaError_t launch_interp3(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s);
 template <typename T> int interp3_blocks(int W, int ncols);
+template <typename T> cudaError_t launch_spread2(int W, const SpreadArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_interp2(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s);
+template <typename T> int strip2_blocks(int W, int ntasks);
+constexpr int kStripMaxPts = 128;   // points per 2-D strip task
+inline int strip_bx(int W) { return 33 - W; }   // x-cells of a 2-D strip: its window spans 32 rows
+constexpr int kStripBy = 8;         // y-cells of a 2-D strip
 bool column_kernels(int d, int W);
 void bin_shape(int d, int W, int B[3]);
 template <typename T> cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches);

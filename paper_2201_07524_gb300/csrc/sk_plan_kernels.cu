@@ -126,8 +126,9 @@ __global__ void k_combine(const double* __restrict__ partial, int nblocks, int n
 // ------------------------------------------------------------ bin sorting
 // Sort key of a point: its bin (bins of B[0] x .. x B[d-1] cells, last axis
 // fastest) times the cells per bin, plus its cell inside the bin (last axis
-// fastest).  Sorting by this key keeps every bin contiguous and, inside a bin,
-// every column of cells along the last axis contiguous.
+// fastest; in 2-D the y cell is the major one).  Sorting by this key keeps
+// every bin contiguous and, inside a 3-D bin, every column of cells along the
+// last axis contiguous.
 template <typename T>
 __global__ void k_prepare_points(const double* __restrict__ x, int64_t n, int d, double c0, double c1, double c2,
                                  double scale, int n_os, int B0, int B1, int B2, int nb0, int nb1, int nb2, int m,
@@ -139,7 +140,7 @@ __global__ void k_prepare_points(const double* __restrict__ x, int64_t n, int d,
     const int nb[3] = {nb0, nb1, nb2};
     const int B[3] = {B0, B1, B2};
     T* u[3] = {u0, u1, u2};
-    int bin = 0, loc = 0, bvol = 1;
+    int bin = 0, loc = 0, bvol = 1, lx = 0;
     bool ok = true;
     for (int t = 0; t < d; ++t) {
         const double z = scale * (x[i * d + t] - c[t]) + 0.5;
@@ -154,8 +155,12 @@ __global__ void k_prepare_points(const double* __restrict__ x, int64_t n, int d,
         bt = bt >= nb[t] ? nb[t] - 1 : bt;
         bin = bin * nb[t] + bt;
         loc = loc * B[t] + (f - bt * B[t]);
+        if (t == 0) lx = f - bt * B[t];
         bvol *= B[t];
     }
+    // 2-D: inside a bin the y-cell is the major key (the strip kernels walk a
+    // bin's points in y order); otherwise the last axis is fastest
+    if (d == 2) loc = (loc - lx * B[1]) * B[0] + lx;
     if (!ok) atomicOr(status, 2);
     const int k = bin * bvol + loc;
     key[i] = k;

@@ -17,15 +17,16 @@
 namespace sk {
 
 // Bin shapes in cells (last axis fastest).  In 3-D a bin is 4 x 4 x 8 so that
-// its 16 xy-columns of 8 cells feed the column kernels (sk_spread3.cu).
+// its 16 xy-columns of 8 cells feed the column kernels (sk_spread3.cu); in 2-D
+// a bin is a strip of 33 - W by 8 cells for the strip kernels (same file); the
+// per-point kernels here serve 1-D plans and 3-D plans with W > 10.
 template <int D> struct BinShape;
 template <> struct BinShape<1> { static constexpr int B0 = 512, B1 = 1, B2 = 1; };
-template <> struct BinShape<2> { static constexpr int B0 = 32, B1 = 32, B2 = 1; };
 template <> struct BinShape<3> { static constexpr int B0 = 4, B1 = 4, B2 = 8; };
 
-void bin_shape(int d, int, int B[3]) {
+void bin_shape(int d, int W, int B[3]) {
     if (d == 1) { B[0] = BinShape<1>::B0; B[1] = 1; B[2] = 1; }
-    else if (d == 2) { B[0] = BinShape<2>::B0; B[1] = BinShape<2>::B1; B[2] = 1; }
+    else if (d == 2) { B[0] = strip_bx(W); B[1] = kStripBy; B[2] = 1; }
     else { B[0] = BinShape<3>::B0; B[1] = BinShape<3>::B1; B[2] = BinShape<3>::B2; }
 }
 
@@ -230,7 +231,7 @@ cudaError_t launch_spread(int d, int W, const SpreadArgs& a, cudaStream_t s) {
     if (column_kernels(d, W)) return launch_spread3<T>(W, a, s);
     switch (d) {
         case 1: return spread_w<1, T>(W, a, s);
-        case 2: return spread_w<2, T>(W, a, s);
+        case 2: return launch_spread2<T>(W, a, s);
         case 3: return spread_w<3, T>(W, a, s);
         default: return cudaErrorInvalidValue;
     }
@@ -270,7 +271,9 @@ cudaError_t launch_interp(int d, int W, const InterpArgs& a, const Epilogue& e, 
     }
     switch (d) {
         case 1: return interp_w<1, T>(W, a, e, launches, s);
-        case 2: return interp_w<2, T>(W, a, e, launches, s);
+        case 2:
+            if (launches && a.nstasks > 0) ++*launches;
+            return launch_interp2<T>(W, a, e, s);
         case 3: return interp_w<3, T>(W, a, e, launches, s);
         default: return cudaErrorInvalidValue;
     }

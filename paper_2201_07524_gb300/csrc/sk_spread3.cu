@@ -631,6 +631,211 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (W <= 8 ? 3 : 2) : (W <=
     epi_finish_warps(e, sq, bad, dot, &warps_done);
 }
 
+// ------------------------------------------------------------ 2-D strips
+// The 2-D kernels follow the same plan with one axis fewer.  A bin is a strip
+// of BX = 33 - W x-cells by BY y-cells; every point of it touches x-rows
+// x0 - (m-1) ... x0 + BX + m - 2, exactly 32 rows, so lane l owns row
+// x0 - (m-1) + l over the E = BY + W - 1 y-cells of the strip's window, in
+// registers.  Inside a bin the points are sorted by y-cell first, so a batch
+// of 32 comes in non-decreasing y-offset (segments with compile-time
+// register indices, as in 3-D).  For one point, the W lanes whose rows lie in
+// its x-window take wx[lane - dx] and add (or gather) its W y-taps.  Tasks are
+// runs of at most kStripMaxPts points of one bin, taken by warps from a queue
+// (most points first); spreading adds a task's window to the grid with global
+// atomics at its end, interpolation reduces each point's lane partials
+// through shared memory and runs the FP64 epilogue.
+template <int W, typename T>
+struct Strip2 {
+    static constexpr int BX = 33 - W, BY = kStripBy;
+    static constexpr int E = BY + W - 1;
+    static constexpr int VEC = 16 / int(sizeof(T));
+    static constexpr int WP = (W + VEC - 1) / VEC * VEC;
+    static constexpr int WX = 0, WY = WP;
+    static constexpr int NV = (2 * WP) / VEC;
+    static constexpr int STRIDE = (NV % 2 == 1 ? NV : NV + 1) * VEC;
+};
+
+// Table row of a 2-D point: wx (times `scale`) and wy; returns the point's
+// x-cell and y-cell.
+template <int W, typename T>
+__device__ __forceinline__ void fill_row2(T* row, T u0, T u1, T scale, const WindowPoly& wp, int& fx, int& fy) {
+    using G = Strip2<W, T>;
+    T w[W];
+    window_poly<W, T>(u0, wp, scale, fx, w);
+    store_vec<T, W>(row + G::WX, w);
+    window_poly<W, T>(u1, wp, T(1), fy, w);
+    store_vec<T, W>(row + G::WY, w);
+}
+
+// The x-weight lane `lane` takes from a point whose x-window starts dx rows
+// into the strip's window (0 outside it).
+template <int W, typename T>
+__device__ __forceinline__ T lane_wx(const T* row, int lane, int dx) {
+    const int off = lane - dx;
+    return (off >= 0 && off < W) ? row[Strip2<W, T>::WX + off] : T(0);
+}
+
+template <int W, int E, int DY0, typename T>
+__device__ __forceinline__ void strip_spread_segment(T (&acc)[E], const T* wt, const int* dxs, int lane, int mydy,
+                                                     int& first) {
+    using G = Strip2<W, T>;
+    const int cnt = __popc(__ballot_sync(0xffffffffu, mydy == DY0));
+    for (int p = first; p < first + cnt; ++p) {
+        const T* row = wt + p * G::STRIDE;
+        const T ax = lane_wx<W, T>(row, lane, dxs[p]);
+        T wy[W];
+        load_wz<W, T>(row + G::WY, wy);
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[DY0 + k] = fma(ax, wy[k], acc[DY0 + k]);
+    }
+    first += cnt;
+}
+
+template <int W, int E, typename T, int... DY>
+__device__ __forceinline__ void strip_spread(T (&acc)[E], const T* wt, const int* dxs, int lane, int mydy,
+                                             std::integer_sequence<int, DY...>) {
+    int first = 0;
+    (strip_spread_segment<W, E, DY, T>(acc, wt, dxs, lane, mydy, first), ...);
+}
+
+template <int W, int E, int DY0, typename T>
+__device__ __forceinline__ void strip_interp_segment(const T (&win)[E], const T* wt, const int* dxs, T* rd, int lane,
+                                                     int mydy, int& first) {
+    using G = Strip2<W, T>;
+    const int cnt = __popc(__ballot_sync(0xffffffffu, mydy == DY0));
+    for (int p = first; p < first + cnt; ++p) {
+        const T* row = wt + p * G::STRIDE;
+        const T ax = lane_wx<W, T>(row, lane, dxs[p]);
+        T wy[W];
+        load_wz<W, T>(row + G::WY, wy);
+        T sacc = T(0);
+#pragma unroll
+        for (int k = 0; k < W; ++k) sacc = fma(win[DY0 + k], wy[k], sacc);
+        rd[p * kRedStride + lane] = ax * sacc;
+    }
+    first += cnt;
+}
+
+template <int W, int E, typename T, int... DY>
+__device__ __forceinline__ void strip_interp(const T (&win)[E], const T* wt, const int* dxs, T* rd, int lane, int mydy,
+                                             std::integer_sequence<int, DY...>) {
+    int first = 0;
+    (strip_interp_segment<W, E, DY, T>(win, wt, dxs, rd, lane, mydy, first), ...);
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_spread2_strip(SpreadArgs a) {
+    using G = Strip2<W, T>;
+    constexpr int E = G::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tab = reinterpret_cast<T*>(smem_raw);
+    int* dxall = reinterpret_cast<int*>(tab + kWarps * 32 * G::STRIDE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* wt = tab + warp * 32 * G::STRIDE;
+    int* dxs = dxall + warp * 32;
+    const T* c0 = static_cast<const T*>(a.coord[0]);
+    const T* c1 = static_cast<const T*>(a.coord[1]);
+    T* grid = static_cast<T*>(a.grid);
+    const int n = a.n_os;
+    for (int t = queue_take(a.queue, lane); t < a.nstasks; t = queue_take(a.queue, lane)) {
+        const int bin = a.stasks[3 * t], start = a.stasks[3 * t + 1], end = a.stasks[3 * t + 2];
+        const int x0 = (bin / a.nb[1]) * G::BX, y0 = (bin % a.nb[1]) * G::BY;
+        T acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = T(0);
+        for (int base = start; base < end; base += 32) {
+            const int cnt = min(32, end - base);
+            int mydy = -1;
+            if (lane < cnt) {
+                const int p = base + lane;
+                int fx, fy;
+                fill_row2<W, T>(wt + lane * G::STRIDE, c0[p], c1[p], T(a.w[p]), a.wp, fx, fy);
+                dxs[lane] = fx - x0;
+                mydy = fy - y0;
+            }
+            __syncwarp();
+            strip_spread<W, E, T>(acc, wt, dxs, lane, mydy, std::make_integer_sequence<int, G::BY>{});
+            __syncwarp();
+        }
+        const int xr = x0 - (W / 2 - 1) + lane;
+        if (xr >= 0 && xr < n) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int yr = y0 - (W / 2 - 1) + e;
+                if (yr >= 0 && yr < n && acc[e] != T(0)) atomicAdd(grid + int64_t(xr) * n + yr, acc[e]);
+            }
+        }
+    }
+    queue_leave(a.queue, lane);
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_interp2_strip(InterpArgs a, Epilogue e) {
+    using G = Strip2<W, T>;
+    constexpr int E = G::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tab = reinterpret_cast<T*>(smem_raw);
+    T* red = tab + kWarps * 32 * G::STRIDE;
+    int* dxall = reinterpret_cast<int*>(red + kWarps * 32 * kRedStride);
+    __shared__ unsigned warps_done;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* wt = tab + warp * 32 * G::STRIDE;
+    T* rd = red + warp * 32 * kRedStride;
+    int* dxs = dxall + warp * 32;
+    if (threadIdx.x == 0) warps_done = 0u;
+    __syncthreads();
+    const T* c0 = static_cast<const T*>(a.coord[0]);
+    const T* c1 = static_cast<const T*>(a.coord[1]);
+    const T* grid = static_cast<const T*>(a.grid);
+    const int n = a.n_os;
+    double sq = 0.0, bad = 0.0, dot = 0.0;
+    for (int t = queue_take(a.queue, lane); t < a.nstasks; t = queue_take(a.queue, lane)) {
+        const int bin = a.stasks[3 * t], start = a.stasks[3 * t + 1], end = a.stasks[3 * t + 2];
+        const int x0 = (bin / a.nb[1]) * G::BX, y0 = (bin % a.nb[1]) * G::BY;
+        // the lane's row of the strip's window
+        T win[E];
+        {
+            const int xr = x0 - (W / 2 - 1) + lane;
+            const bool okx = xr >= 0 && xr < n;
+            const T* g = grid + int64_t(okx ? xr : 0) * n;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int yr = y0 - (W / 2 - 1) + k;
+                win[k] = (okx && yr >= 0 && yr < n) ? __ldg(g + yr) : T(0);
+            }
+        }
+        for (int base = start; base < end; base += 32) {
+            const int cnt = min(32, end - base);
+            int mydy = -1;
+            double q = 0.0, am = 0.0;
+            if (lane < cnt) {
+                const int p = base + lane;
+                int fx, fy;
+                fill_row2<W, T>(wt + lane * G::STRIDE, c0[p], c1[p], T(1), a.wp, fx, fy);
+                dxs[lane] = fx - x0;
+                mydy = fy - y0;
+                if (e.mode != EPI_APPLY) {
+                    q = e.scal[p];
+                    am = e.marg[p];
+                }
+            }
+            __syncwarp();
+            strip_interp<W, E, T>(win, wt, dxs, rd, lane, mydy, std::make_integer_sequence<int, G::BY>{});
+            __syncwarp();
+            if (lane < cnt) {
+                T tsum = T(0);
+                const T* pr = rd + lane * kRedStride;
+#pragma unroll 8
+                for (int l = 0; l < 32; ++l) tsum += pr[l];
+                epi_point_pre(e, base + lane, double(tsum), q, am, sq, bad, dot);
+            }
+            __syncwarp();
+        }
+    }
+    queue_leave(a.queue, lane);
+    epi_finish_warps(e, sq, bad, dot, &warps_done);
+}
+
 // ------------------------------------------------------------------ dispatch
 template <int W, typename T>
 size_t spread3_smem() {
@@ -738,6 +943,117 @@ int interp3_blocks(int W, int ncols) {
 
 template int interp3_blocks<float>(int, int);
 template int interp3_blocks<double>(int, int);
+// ------------------------------------------------------------ 2-D strip dispatch
+template <int W, typename T>
+size_t spread2_smem() {
+    using G = Strip2<W, T>;
+    return size_t(kWarps) * 32 * G::STRIDE * sizeof(T) + size_t(kWarps) * 32 * sizeof(int);
+}
+
+template <int W, typename T>
+size_t interp2_smem() {
+    using G = Strip2<W, T>;
+    return (size_t(kWarps) * 32 * G::STRIDE + size_t(kWarps) * 32 * kRedStride) * sizeof(T) +
+           size_t(kWarps) * 32 * sizeof(int);
+}
+
+// Blocks of a persistent strip launch: all resident blocks, but no more than
+// one warp per task -- except that a few tasks still get a block (an SM) each,
+// since the strip loops are bound by the SM's FP64 or FP32 pipes, not by the
+// warps they keep busy.
+template <auto K>
+static int resident_blocks(size_t smem, int tasks) {
+    static int resident[64] = {0}, sm_count[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& r = resident[dev & 63];
+    if (r == 0) {
+        int per_sm = 0, sms = 0;
+        if (opt_in<K>(smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, K, 256, smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        r = std::max(1, per_sm) * sms;
+        sm_count[dev & 63] = sms;
+    }
+    const int want = std::max((tasks + kWarps - 1) / kWarps, std::min(tasks, sm_count[dev & 63]));
+    return std::max(1, std::min(r, want));
+}
+
+template <int W, typename T>
+static cudaError_t spread2_one(const SpreadArgs& a, cudaStream_t s) {
+    const size_t bytes = spread2_smem<W, T>();
+    cudaError_t err = opt_in<k_spread2_strip<W, T>>(bytes);
+    if (err != cudaSuccess) return err;
+    const int blocks = resident_blocks<k_spread2_strip<W, T>>(bytes, a.nstasks);
+    if (blocks == 0) {
+        const cudaError_t last = cudaGetLastError();
+        return last != cudaSuccess ? last : cudaErrorInvalidValue;
+    }
+    if (a.nstasks == 0) return cudaSuccess;
+    k_spread2_strip<W, T><<<blocks, 256, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int W, typename T>
+static cudaError_t interp2_one(const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
+    const size_t bytes = interp2_smem<W, T>();
+    cudaError_t err = opt_in<k_interp2_strip<W, T>>(bytes);
+    if (err != cudaSuccess) return err;
+    const int blocks = resident_blocks<k_interp2_strip<W, T>>(bytes, a.nstasks);
+    if (blocks == 0) {
+        const cudaError_t last = cudaGetLastError();
+        return last != cudaSuccess ? last : cudaErrorInvalidValue;
+    }
+    if (a.nstasks == 0) return cudaSuccess;
+    k_interp2_strip<W, T><<<blocks, 256, bytes, s>>>(a, e);
+    return cudaGetLastError();
+}
+
+#define SK_STRIP_W(FN, ...)                        \
+    switch (W) {                                   \
+        case 4: return FN<4, T>(__VA_ARGS__);      \
+        case 6: return FN<6, T>(__VA_ARGS__);      \
+        case 8: return FN<8, T>(__VA_ARGS__);      \
+        case 10: return FN<10, T>(__VA_ARGS__);    \
+        case 12: return FN<12, T>(__VA_ARGS__);    \
+        case 14: return FN<14, T>(__VA_ARGS__);    \
+        case 16: return FN<16, T>(__VA_ARGS__);    \
+        default: return cudaErrorInvalidValue;     \
+    }
+
+template <typename T>
+cudaError_t launch_spread2(int W, const SpreadArgs& a, cudaStream_t s) {
+    SK_STRIP_W(spread2_one, a, s)
+}
+
+template <typename T>
+cudaError_t launch_interp2(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
+    SK_STRIP_W(interp2_one, a, e, s)
+}
+#undef SK_STRIP_W
+
+template <typename T>
+int strip2_blocks(int W, int ntasks) {
+    switch (W) {
+        case 4: return resident_blocks<k_interp2_strip<4, T>>(interp2_smem<4, T>(), ntasks);
+        case 6: return resident_blocks<k_interp2_strip<6, T>>(interp2_smem<6, T>(), ntasks);
+        case 8: return resident_blocks<k_interp2_strip<8, T>>(interp2_smem<8, T>(), ntasks);
+        case 10: return resident_blocks<k_interp2_strip<10, T>>(interp2_smem<10, T>(), ntasks);
+        case 12: return resident_blocks<k_interp2_strip<12, T>>(interp2_smem<12, T>(), ntasks);
+        case 14: return resident_blocks<k_interp2_strip<14, T>>(interp2_smem<14, T>(), ntasks);
+        case 16: return resident_blocks<k_interp2_strip<16, T>>(interp2_smem<16, T>(), ntasks);
+        default: return 0;
+    }
+}
+
+template cudaError_t launch_spread2<float>(int, const SpreadArgs&, cudaStream_t);
+template cudaError_t launch_spread2<double>(int, const SpreadArgs&, cudaStream_t);
+template cudaError_t launch_interp2<float>(int, const InterpArgs&, const Epilogue&, cudaStream_t);
+template cudaError_t launch_interp2<double>(int, const InterpArgs&, const Epilogue&, cudaStream_t);
+template int strip2_blocks<float>(int, int);
+template int strip2_blocks<double>(int, int);
+
 template cudaError_t launch_spread3<float>(int, const SpreadArgs&, cudaStream_t);
 template cudaError_t launch_spread3<double>(int, const SpreadArgs&, cudaStream_t);
 template cudaError_t launch_interp3<float>(int, const InterpArgs&, const Epilogue&, cudaStream_t);

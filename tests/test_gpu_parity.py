@@ -122,6 +122,43 @@ def test_nfft_matches_ndft(d, N, precision):
     assert np.max(np.abs(got - want)) / np.sum(np.abs(F)) <= TOL_FS[precision]
 
 
+def kb_window_bound(m, sigma=2.0):
+    """Error bound of the Kaiser-Bessel window relative to the l1 norm of the
+    input (Potts and Steidl's estimate, 4 pi (sqrt m + m) (1 - 1/sigma)^(1/4)
+    exp(-2 pi m sqrt(1 - 1/sigma)))."""
+    q = 1.0 - 1.0 / sigma
+    return 4 * math.pi * (math.sqrt(m) + m) * q ** 0.25 * math.exp(-2 * math.pi * m * math.sqrt(q))
+
+
+FLOOR_NFFT = {sk.SK_FP64: 1e-12, sk.SK_FP32: 1e-5}
+
+
+@pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
+@pytest.mark.parametrize("m_w", [2, 3, 4, 5, 6, 7, 8])
+def test_2d_nfft_stages_every_window_width(m_w, precision):
+    # every 2-D window width; a dense cluster puts several hundred points in
+    # one bin (tasks split into runs) next to sparse bins and a ragged tail
+    N, h = 64, 32
+    x = np.concatenate([wl.uniform_ball(1401, 2, 0.2, 21), 0.004 * np.random.default_rng(22).standard_normal((600, 2))])
+    y = np.concatenate([wl.uniform_ball(555, 2, 0.2, 23), 0.11 + 0.002 * np.random.default_rng(24).standard_normal((333, 2))])
+    plan = plan_for(x, y, N=N, m_w=m_w, precision=precision)
+    tol = max(kb_window_bound(m_w), FLOOR_NFFT[precision])
+    w = np.random.default_rng(25).standard_normal(len(x))
+    out = np.zeros((2 * h + 1, 2 * h + 1, 2))
+    sk.sk_adjoint_nfft(plan, sk.SK_SET_X, w, out.reshape(-1))
+    got = out[..., 0] + 1j * out[..., 1]
+    err = np.max(np.abs(_common(got, h, 2) - ofs.adjoint_ndft(x + 0.5, w, N))) / np.sum(np.abs(w))
+    assert err <= tol, (err, tol)
+    rng = np.random.default_rng(26)
+    A = rng.standard_normal((2 * h + 1,) * 2) + 1j * rng.standard_normal((2 * h + 1,) * 2)
+    F = 0.5 * (A + np.conj(A[::-1, ::-1]))
+    buf = np.stack([F.real, F.imag], axis=-1).reshape(-1).copy()
+    t = np.zeros(len(y))
+    sk.sk_nfft(plan, sk.SK_SET_Y, buf, t)
+    err = np.max(np.abs(t - ofs.ndft(y + 0.5, _common(F, h, 2), N).real)) / np.sum(np.abs(F))
+    assert err <= tol, (err, tol)
+
+
 # --------------------------------------------------------- kernel products
 @pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
 @pytest.mark.parametrize("d,n,m,N,eps", [(1, 1000, 777, 64, 0.05), (2, 2000, 1337, 64, 0.05),
