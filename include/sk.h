@@ -53,6 +53,7 @@ enum {
 enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / interpolation */
 enum { SK_METHOD_NFFT = 0, SK_METHOD_DIRECT = 1 };
 enum { SK_DOMAIN_SCALING = 0, SK_DOMAIN_LOG = 1 };   /* state of the iteration: Alg. 3 or Alg. 4 */
+enum { SK_KERNELS_SIMT = 0, SK_KERNELS_TENSOR = 1 };   /* interpolation on CUDA cores or tensor cores */
 enum { SK_SET_X = 0, SK_SET_Y = 1 };        /* which point cloud a stage entry point acts on */
 
 typedef struct sk_plan sk_plan;
@@ -173,6 +174,22 @@ int sk_set_method(sk_plan* plan, int method);
  * Errors: SK_ERR_ARG for a NULL plan or an unknown domain.
  */
 int sk_set_domain(sk_plan* plan, int domain);
+
+/*
+ * Choose how the interpolation step of Eq. (fastsum) (the NFFT: the grid at the
+ * target points) runs.  SK_KERNELS_TENSOR (the default where supported: d = 3,
+ * SK_FP32, 2 <= m_w <= 5): per bin of 4 x 4 x 8 cells, the contraction of the
+ * bin's window box with the z-weights of 128 points at a time is one tensor-core
+ * product (tcgen05, TF32 operands split into high and low parts, three products,
+ * FP32 accumulation), and the x- and y-weights are applied per point on the CUDA
+ * cores.  SK_KERNELS_SIMT: CUDA cores only.  Both meet the FP32 accuracy of the
+ * plan; their sums differ by rounding.
+ * Errors: SK_ERR_ARG for a NULL plan or an unknown value; SK_ERR_UNSUPPORTED
+ * for SK_KERNELS_TENSOR on a plan it does not support (nothing changes).
+ * A tensor-core wait that gives up (bounded) makes sk_solve / sk_solve_batch
+ * return SK_ERR_TIMEOUT when they read results back.
+ */
+int sk_set_kernels(sk_plan* plan, int kernels);
 
 /*
  * One kernel-vector product (Eqs. (matexp), (matexpt)):

@@ -21,6 +21,8 @@ struct sk_plan {
     int method = SK_METHOD_NFFT;
     int domain = SK_DOMAIN_SCALING;
     int near_sub = 2;           // near-field cells per eps_I (2, or 4 for dense clouds)
+    bool tc_ok = false;         // the tensor-core (tcgen05) interpolation supports this plan
+    bool tc = false;            // ... and is selected
     double* shift = nullptr;    // log domain: max of the Y ([0]) and X ([1]) dual variables
     int N = 0, h = 0, n_os = 0, log2n = 0, W = 0, B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 0, bvol = 1;
     int64_t nkeys = 0;
@@ -467,16 +469,21 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
             CK(cudaMemcpyAsync(c.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
         CK(cudaStreamSynchronize(P->ps));
     }
-    // 2-D strip tasks: runs of at most kStripMaxPts points of one bin, most
-    // points first, so the warps that take the last tasks take short ones.
-    // Small clouds take shorter runs (down to one batch of 32) so that their
-    // tasks still reach every SM.
-    if (P->d == 2) {
+    // Run tasks: runs of at most `run` points of one bin, most points first,
+    // so the workers that take the last tasks take short ones.  2-D strips
+    // (one warp per task): at most kStripMaxPts, and small clouds take
+    // shorter runs (down to one batch of 32) so that their tasks still reach
+    // every SM.  3-D tensor-core interpolation (one block per task): at most
+    // kTcRunPts, whole tiles of 128.
+    if (P->d == 2 || P->tc_ok) {
         int dev = 0, sms = 1;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int64_t per_warp = (n + int64_t(sms) * 8 - 1) / (int64_t(sms) * 8);
-        const int run = int(std::min<int64_t>(kStripMaxPts, std::max<int64_t>(32, (per_warp + 31) / 32 * 32)));
+        int run = kTcRunPts;
+        if (P->d == 2) {
+            const int64_t per_warp = (n + int64_t(sms) * 8 - 1) / (int64_t(sms) * 8);
+            run = int(std::min<int64_t>(kStripMaxPts, std::max<int64_t>(32, (per_warp + 31) / 32 * 32)));
+        }
         std::vector<int> bs(size_t(P->nbins) + 1);
         CK(cudaMemcpyAsync(bs.data(), c.bin_start, bs.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
         CK(cudaStreamSynchronize(P->ps));
@@ -706,6 +713,11 @@ void prepare_kernels(sk_plan* P) {
         ia.nstasks = 0;
         CK(launch_interp2<T>(P->W, ia, Epilogue{}, P->ps));
     }
+    if (P->tc_ok) {
+        InterpArgs ia{};
+        ia.nstasks = 0;
+        CK(launch_interp3_tc(P->W, ia, Epilogue{}, P->ps));
+    }
     CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
 }
 
@@ -799,7 +811,12 @@ void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
     a.grid = P->fft.grid_out;
     a.wp = P->wp;
     int st = stage_begin(P, SK_STAGE_INTERP);
-    CK(launch_interp<T>(P->d, P->W, a, e, &P->launches, P->ps));
+    if (P->tc && std::is_same<T, float>::value) {
+        if (a.nstasks > 0) ++P->launches;
+        CK(launch_interp3_tc(P->W, a, e, P->ps));
+    } else {
+        CK(launch_interp<T>(P->d, P->W, a, e, &P->launches, P->ps));
+    }
     stage_end(P, st);
 }
 
@@ -1313,6 +1330,8 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         P->log2n = log2n;
         P->W = 2 * p.m_w;
         bin_shape(d, P->W, P->B);
+        P->tc_ok = tc_supported(d, P->W, P->precision == SK_FP32);
+        P->tc = P->tc_ok;
         P->nbins = 1;
         P->bvol = 1;
         for (int t = 0; t < 3; ++t) {
@@ -1372,6 +1391,14 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
                 P->partial = static_cast<double*>(dalloc(P, size_t(need) * 8 * sizeof(double)));
             }
         }
+        if (P->tc_ok) {
+            const int need = interp3_tc_blocks(P->W, std::max(P->X.nstasks, P->Y.nstasks));
+            if (need <= 0) throw Fail{SK_ERR_CUDA};
+            if (need > P->partial_blocks) {
+                P->partial_blocks = need;
+                P->partial = static_cast<double*>(dalloc(P, size_t(need) * 8 * sizeof(double)));
+            }
+        }
         if (column_kernels(P->d, P->W)) {
             const int ncols = std::max(P->X.ncols, P->Y.ncols);
             const int need = std::max(std::max(P->X.ntasks, P->Y.ntasks),
@@ -1416,6 +1443,17 @@ int sk_set_method(sk_plan* P, int method) {
     if (method != P->method) {
         destroy_graph(P);
         P->method = method;
+    }
+    return SK_OK;
+}
+
+int sk_set_kernels(sk_plan* P, int kernels) {
+    if (!P || (kernels != SK_KERNELS_SIMT && kernels != SK_KERNELS_TENSOR)) return SK_ERR_ARG;
+    if (kernels == SK_KERNELS_TENSOR && !P->tc_ok) return SK_ERR_UNSUPPORTED;
+    const bool tc = kernels == SK_KERNELS_TENSOR;
+    if (tc != P->tc) {
+        destroy_graph(P);
+        P->tc = tc;
     }
     return SK_OK;
 }
@@ -1503,6 +1541,7 @@ int sk_solve(sk_plan* P, int max_iter, double tol, int check_every, double* u_ou
         if (res || u_out || v_out || tol > 0.0) {
             const int st = read_status(P);
             if (st & 1) rc = SK_ERR_UNDERFLOW;
+            if (st & 4) rc = SK_ERR_TIMEOUT;
         }
         leave(P, stream);
     } catch (const Fail& f) {
@@ -1579,7 +1618,9 @@ int sk_solve_batch(sk_plan* const* plans, int count, int max_iter, sk_result* re
                 else
                     final_report<double>(P, res);
                 res->iters = max_iter;
-                if (read_status(P) & 1) rc = SK_ERR_UNDERFLOW;
+                const int st = read_status(P);
+                if (st & 1) rc = SK_ERR_UNDERFLOW;
+                if (st & 4) rc = SK_ERR_TIMEOUT;
             }
             leave(P, stream);
         }

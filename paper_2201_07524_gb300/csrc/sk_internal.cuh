@@ -105,7 +105,8 @@ struct Epilogue {
     double* partial = nullptr;   // 3 doubles per block
     unsigned* ticket = nullptr;  // zero between launches; the last block resets it
     double* result = nullptr;    // [0] sum (scal_old t - marg)^2, [1] bad count, [2] sum scal_old t
-    int* status = nullptr;       // bit 0 set when some t_i <= 0 or not finite (UPDATE)
+    int* status = nullptr;       // bit 0 set when some t_i <= 0 or not finite (UPDATE); bit 2 when a
+                                 // bounded wait of a tensor-core kernel gave up
     // log domain (Alg. 4): scal holds the dual variables beta; t_i is the sum
     // with the source weights exp((gamma_j - shift) / eps - 1/2), shift = *shift
     int log_domain = 0;
@@ -231,6 +232,12 @@ constexpr int kStripMaxPts = 128;   // points per 2-D strip task
 inline int strip_bx(int W) { return 33 - W; }   // x-cells of a 2-D strip: its window spans 32 rows
 constexpr int kStripBy = 8;         // y-cells of a 2-D strip
 bool column_kernels(int d, int W);
+// Tensor-core (tcgen05) interpolation of 3-D FP32 plans (sk_tc.cu): tasks are
+// runs of at most kTcRunPts points of one bin in InterpArgs::stasks.
+constexpr int kTcRunPts = 512;
+bool tc_supported(int d, int W, int precision_fp32);
+cudaError_t launch_interp3_tc(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s);
+int interp3_tc_blocks(int W, int ntasks);
 void bin_shape(int d, int W, int B[3]);
 template <typename T> cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches);
 template <typename T> cudaError_t launch_fft_adjoint(const FftPlan& f, double* fhat, cudaStream_t s,

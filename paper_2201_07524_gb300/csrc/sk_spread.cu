@@ -201,7 +201,7 @@ static cudaError_t spread_one(const SpreadArgs& a, cudaStream_t s) {
     static unsigned long long configured = 0ull;   // one bit per device
     int dev = 0;
     cudaGetDevice(&dev);
-    if (bytes > 48 * 1024 && !(configured & (1ull << (dev & 63)))) {
+    if (!(configured & (1ull << (dev & 63)))) {   // the 48 KB default also counts static shared memory
         cudaError_t err = cudaFuncSetAttribute(k_spread<D, W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                int(bytes));
         if (err != cudaSuccess) return err;

@@ -26,6 +26,7 @@
 #include <utility>
 
 #include "sk_internal.cuh"
+#include "sk_device.cuh"
 
 namespace sk {
 
@@ -58,35 +59,6 @@ constexpr int kSpreadWarps = 8;   // warps per spreading block (one block per bi
 // a point's row is read with 16-byte loads; 36 keeps those loads conflict-free).
 constexpr int kRedStride = 36;
 
-template <typename T> struct PolyDeg;
-template <> struct PolyDeg<float> { static constexpr int D = kPolyDeg32; };
-template <> struct PolyDeg<double> { static constexpr int D = kPolyDeg64; };
-
-template <typename T>
-__device__ __forceinline__ T poly_coef(const WindowPoly& wp, int k, int i);
-template <> __device__ __forceinline__ float poly_coef<float>(const WindowPoly& wp, int k, int i) {
-    return wp.c32[k][i];
-}
-template <> __device__ __forceinline__ double poly_coef<double>(const WindowPoly& wp, int k, int i) {
-    return wp.c64[k][i];
-}
-
-// The W window weights of one coordinate (taps starting at cell f - (m-1)),
-// by Horner's rule on the piecewise polynomial; `scale` multiplies them.
-template <int W, typename T>
-__device__ __forceinline__ void window_poly(T u, const WindowPoly& wp, T scale, int& f, T* w) {
-    constexpr int DEG = PolyDeg<T>::D;
-    const T fl = floor(u);
-    f = int(fl);
-    const T s = T(2) * (u - fl) - T(1);
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-        T acc = poly_coef<T>(wp, k, DEG);
-#pragma unroll
-        for (int i = DEG - 1; i >= 0; --i) acc = fma(acc, s, poly_coef<T>(wp, k, i));
-        w[k] = acc * scale;
-    }
-}
 
 // N values to 16-byte aligned shared memory with vector stores.
 template <typename T, int N>
@@ -518,28 +490,6 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 
     }
 }
 
-// Next entry of the interpolation's column queue for this warp (lane 0 takes
-// it; every lane gets it).
-__device__ __forceinline__ int queue_take(unsigned* q, int lane) {
-    unsigned c = 0u;
-    if (lane == 0) c = atomicAdd(q, 1u);
-    return int(__shfl_sync(0xffffffffu, c, 0));
-}
-
-// A warp that has left the queue loop signs off; the last warp of the grid
-// resets the queue for the next launch (every other warp has already taken
-// its last entry, which precedes its sign-off).
-__device__ __forceinline__ void queue_leave(unsigned* q, int lane) {
-    if (lane == 0) {
-        __threadfence();
-        const unsigned total = gridDim.x * (blockDim.x >> 5);
-        if (atomicAdd(q + 1, 1u) == total - 1u) {
-            q[0] = 0u;
-            q[1] = 0u;
-            __threadfence();
-        }
-    }
-}
 
 // A queue entry: its (bin, column) code and the column's points [start, end).
 struct ColumnRef {
@@ -849,9 +799,10 @@ size_t interp3_smem() {
     return (size_t(kWarps) * 32 * G::STRIDE + size_t(kWarps) * 32 * kRedStride) * sizeof(T);
 }
 
+// Allow a kernel `bytes` of dynamic shared memory (once per device).  Set even
+// below 48 KB: the default limit counts the kernel's static shared memory too.
 template <auto K>
 static cudaError_t opt_in(size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     static unsigned long long configured = 0ull;
     int dev = 0;
     cudaGetDevice(&dev);

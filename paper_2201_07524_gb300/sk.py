@@ -25,6 +25,7 @@ SK_ERR_TOO_LARGE = 10
 SK_FP32, SK_FP64 = 0, 1
 SK_METHOD_NFFT, SK_METHOD_DIRECT = 0, 1
 SK_DOMAIN_SCALING, SK_DOMAIN_LOG = 0, 1
+SK_KERNELS_SIMT, SK_KERNELS_TENSOR = 0, 1
 SK_SET_X, SK_SET_Y = 0, 1
 SK_STAGE_SPREAD, SK_STAGE_FFT, SK_STAGE_INTERP, SK_STAGE_OTHER, SK_STAGE_DIRECT, SK_STAGE_NEAR = 0, 1, 2, 3, 4, 5
 SK_NSTAGES = 6
@@ -64,6 +65,7 @@ _SIGS = {
     "sk_destroy": (None, [_P]),
     "sk_set_method": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_set_domain": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sk_set_kernels": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
     "sk_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D,
                                 ctypes.POINTER(sk_result), _S]),
@@ -202,6 +204,10 @@ def sk_set_method(plan, method):
 
 def sk_set_domain(plan, domain):
     _check(_lib.sk_set_domain(plan.handle, int(domain)), "sk_set_domain")
+
+
+def sk_set_kernels(plan, kernels):
+    _check(_lib.sk_set_kernels(plan.handle, int(kernels)), "sk_set_kernels")
 
 
 def sk_kernel_apply(plan, transpose, vin, out, stream=None):

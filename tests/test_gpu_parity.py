@@ -159,6 +159,54 @@ def test_2d_nfft_stages_every_window_width(m_w, precision):
     assert err <= tol, (err, tol)
 
 
+@pytest.mark.parametrize("m_w", [2, 3, 4, 5])
+def test_3d_tensor_core_interpolation_matches_exact_sums_and_cuda_cores(m_w):
+    # the tcgen05 interpolation (default for 3-D FP32) against the exact sums and
+    # against the CUDA-core kernels on the same plan; a dense cluster puts
+    # thousands of points into a few bins (several tasks per bin, ragged tiles)
+    rng = np.random.default_rng(31 + m_w)
+    x = np.concatenate([wl.uniform_ball(3001, 3, 0.2, 32), 0.01 * rng.standard_normal((2500, 3))])
+    y = np.concatenate([wl.uniform_ball(1777, 3, 0.2, 33), 0.05 + 0.003 * rng.standard_normal((900, 3))])
+    plan = plan_for(x, y, eps=0.02, N=32, m_w=m_w, precision=sk.SK_FP32, user_geometry=False)
+    v = wl.positive_vector(len(y), 34)
+    u = wl.positive_vector(len(x), 35)
+    out = {}
+    for kind in (sk.SK_KERNELS_TENSOR, sk.SK_KERNELS_SIMT):
+        sk.sk_set_kernels(plan, kind)
+        t = np.zeros(len(x))
+        tt = np.zeros(len(y))
+        sk.sk_kernel_apply(plan, 0, v, t)
+        sk.sk_kernel_apply(plan, 1, u, tt)
+        out[kind] = (t, tt)
+    t_exact = osk.kernel_apply(x, y, v, 0.02, 2.0)
+    tt_exact = osk.kernel_apply_T(x, y, u, 0.02, 2.0)
+    # the window error bound of m_w with sigma = 2 (relative to the l1 norm,
+    # here of the weights times max K = 1), or the FP32 floor
+    tol = max(1e-5, 4 * kb_window_bound(m_w))
+    for kind in out:
+        assert efs(out[kind][0], t_exact) <= tol, (kind, efs(out[kind][0], t_exact))
+        assert efs(out[kind][1], tt_exact) <= tol
+    # the two kernels differ by FP32 rounding only (the FP32 tolerance)
+    for a, b in zip(out[sk.SK_KERNELS_TENSOR], out[sk.SK_KERNELS_SIMT]):
+        assert np.max(np.abs(a - b)) <= TOL_FS[sk.SK_FP32] * np.max(np.abs(b))
+
+
+def test_kernel_selection_errors():
+    x = wl.uniform_ball(100, 3, 0.2, 40)
+    plan64 = plan_for(x, x, precision=sk.SK_FP64, N=16)
+    with pytest.raises(sk.SkError) as err:
+        sk.sk_set_kernels(plan64, sk.SK_KERNELS_TENSOR)
+    assert err.value.status == sk.SK_ERR_UNSUPPORTED
+    sk.sk_set_kernels(plan64, sk.SK_KERNELS_SIMT)
+    plan2 = plan_for(wl.uniform_ball(100, 2, 0.2, 41), wl.uniform_ball(90, 2, 0.2, 42), precision=sk.SK_FP32)
+    with pytest.raises(sk.SkError) as err:
+        sk.sk_set_kernels(plan2, sk.SK_KERNELS_TENSOR)
+    assert err.value.status == sk.SK_ERR_UNSUPPORTED
+    with pytest.raises(sk.SkError) as err:
+        sk.sk_set_kernels(plan2, 7)
+    assert err.value.status == sk.SK_ERR_ARG
+
+
 # --------------------------------------------------------- kernel products
 @pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
 @pytest.mark.parametrize("d,n,m,N,eps", [(1, 1000, 777, 64, 0.05), (2, 2000, 1337, 64, 0.05),
