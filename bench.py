@@ -191,8 +191,12 @@ def algorithmic_counts(w, n_os):
             "interp": (2.0 * taps * n, grid_bytes + n * (4 * d + 8 * 3))}
 
 
-def kernel_name(stage, w):
-    return "k_%s3_col<%d, float>" % (stage, 2 * w.m_w) if w.d == 3 else None
+def kernel_name(stage, w, tensor_cores):
+    if w.d != 3:
+        return None
+    if stage == "interp" and tensor_cores:
+        return "k_interp3_tc<%d>" % (2 * w.m_w)
+    return "k_%s3_col<%d, float>" % (stage, 2 * w.m_w)
 
 
 def measured_traffic(kname):
@@ -353,6 +357,7 @@ def run_ours(args, rank, world):
     counts = algorithmic_counts(w, info["n_os"])
     per_launch = {k: (stages[k][0] / stages[k][1] if stages[k][1] else 0.0) for k in stages}
     dominant = max(("spread", "interp"), key=lambda k: per_launch[k])
+    kname = kernel_name(dominant, w, info.get("tensor_cores", 0))
     flops, bytes_ = counts[dominant]
     dur_s = per_launch[dominant] / 1e3
     alu_peak = fp32_alu_peak_tflops(pk)
@@ -396,9 +401,9 @@ def run_ours(args, rank, world):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": kernel_name(dominant, w) or dominant, "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": kname or dominant, "achieved": achieved,
                          "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                         "traffic": measured_traffic(kernel_name(dominant, w)),
+                         "traffic": measured_traffic(kname),
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s peaks file)"
                                         % (float(pk.get("sm_max_mhz", 2070.0)), pk_kind),
                          "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,

@@ -122,6 +122,7 @@ typedef struct {
     double center[3], scale, eps_B, eps_I;
     int n_subproblems_x, n_subproblems_y;
     int64_t device_bytes;        /* device memory the plan holds */
+    int tensor_cores;            /* 1: interpolation runs on tensor cores (sk_set_kernels) */
 } sk_info;
 
 /* Text for a status code (static storage, never NULL). */

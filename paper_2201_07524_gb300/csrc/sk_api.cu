@@ -1814,6 +1814,7 @@ int sk_plan_info(const sk_plan* P, sk_info* info) {
     info->n_subproblems_x = P->X.nsub;
     info->n_subproblems_y = P->Y.nsub;
     info->device_bytes = P->bytes;
+    info->tensor_cores = P->tc ? 1 : 0;
     return SK_OK;
 }
 

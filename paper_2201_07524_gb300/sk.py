@@ -50,7 +50,7 @@ class sk_info(ctypes.Structure):
                 ("nearfield", ctypes.c_int), ("eps", ctypes.c_double), ("r", ctypes.c_double),
                 ("eps_scaled", ctypes.c_double), ("center", ctypes.c_double * 3), ("scale", ctypes.c_double),
                 ("eps_B", ctypes.c_double), ("eps_I", ctypes.c_double), ("n_subproblems_x", ctypes.c_int),
-                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
+                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("tensor_cores", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
