@@ -3,12 +3,18 @@
 // coefficients, written for shared memory:
 //
 //   * Every block loads P pencils of length n (P * n = kFftBlockElems complex
-//     values, or one pencil when n is larger) into shared memory, runs a
-//     radix-2 FFT there and writes back.  Blocks are small (two butterflies
-//     per thread and stage), so a launch has many of them and their load,
-//     barrier and store latencies overlap on every SM.
-//     Pencils are padded to n+1 elements so that the loads, which walk the
-//     pencils in parallel, do not collide in shared-memory banks.
+//     values, or one pencil when n is larger) into shared memory, transforms
+//     them there and writes back.  The transform is a Stockham (self-sorting)
+//     FFT of radix 8 (a last stage of radix 4 or 2 when log2 n is not a
+//     multiple of 3): each of the n/8 threads of a pencil reads 8 elements,
+//     applies the stage's twiddles, does its 8-point (or 2 x 4-point, or
+//     4 x 2-point) DFT in registers and writes the 8 results back, so a
+//     128-point pencil takes three stages with natural order in and out.
+//     Blocks are small (n/8 threads per pencil), so a launch has many of them
+//     and their load, barrier and store latencies overlap on every SM.
+//     Element e of a pencil sits at e + e/8 (one pad per 8 elements), which
+//     keeps the stride-R stores of the first stages and the parallel walks of
+//     the load phases off each other's shared-memory banks.
 //   * The grid is real, so the first pass packs two real rows into one complex
 //     FFT and splits the result into two half spectra (k = 0..h along the
 //     contiguous axis); the last inverse pass does the reverse.
@@ -39,11 +45,20 @@ constexpr int kFftBlockElems = 256;
 
 __host__ __device__ __forceinline__ int fft_pencils(int n) { return n >= kFftBlockElems ? 1 : kFftBlockElems / n; }
 
-// Threads of an FFT block: two butterflies per thread and stage, 32 to 256.
-__host__ __device__ __forceinline__ int fft_threads(int n) {
-    const int t = fft_pencils(n) * n / 4;
-    return t < 32 ? 32 : (t > 256 ? 256 : t);
-}
+// Elements of a pencil per thread: 8 in FP32 (radix-8 stages); 4 in FP64
+// (radix-4 stages), whose arithmetic is slow enough on this GPU that the
+// shorter per-thread chains and twice the threads pay -- except for pencils
+// longer than 2048, which keep 8 so that a block stays within 512 threads.
+template <typename T>
+__host__ __device__ __forceinline__ int fft_ept(int n) { return (sizeof(T) == 8 && n <= 2048) ? 4 : 8; }
+
+// Threads of an FFT block (16 to 512).
+template <typename T>
+__host__ __device__ __forceinline__ int fft_threads(int n) { return fft_pencils(n) * n / fft_ept<T>(n); }
+
+// Padded position of element e of a pencil; a pencil spans fft_stride(n) slots.
+__host__ __device__ __forceinline__ int pidx(int e) { return e + (e >> 3); }
+__host__ __device__ __forceinline__ int fft_stride(int n) { return n + n / 8; }
 
 // Row pairs of the real passes: pair q covers rows r0 = o * ostride + y and
 // r0 + 1 with o = olo + q / npo and y = ylo + 2 (q % npo).
@@ -66,69 +81,143 @@ __device__ __forceinline__ C cmul(C a, C b) {
     return r;
 }
 
-__device__ __forceinline__ int bitrev(int v, int log2n) { return int(__brev(unsigned(v)) >> (32 - log2n)); }
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
 
-// Decimation in time: input in bit-reversed order, output in natural order.
-// `tw` is the block's shared-memory copy of the n/2 twiddles.
-template <typename T, bool INV>
-__device__ void fft_dit(typename Cplx<T>::type* buf, int ns, int n, int log2n, int P,
-                        const typename Cplx<T>::type* tw) {
-    using C = typename Cplx<T>::type;
-    const int half = n >> 1;
-    const int total = P * half;
-    for (int s = 0; s < log2n; ++s) {
-        __syncthreads();
-        const int hs = 1 << s;
-        const int shift = log2n - 1 - s;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int p = b >> (log2n - 1);
-            const int j = b & (half - 1);
-            const int k = j & (hs - 1);
-            const int i0 = ((j >> s) << (s + 1)) + k;
-            C w = tw[k << shift];
-            if (INV) w.y = -w.y;
-            C* base = buf + p * ns;
-            const C a = base[i0];
-            const C t = cmul(w, base[i0 + hs]);
-            base[i0].x = a.x + t.x;
-            base[i0].y = a.y + t.y;
-            base[i0 + hs].x = a.x - t.x;
-            base[i0 + hs].y = a.y - t.y;
-        }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) {
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+
+// a * (-i) for the forward transform, a * i for the inverse.
+template <typename C, bool INV>
+__device__ __forceinline__ C mul_mi(C a) {
+    C r;
+    r.x = INV ? -a.y : a.y;
+    r.y = INV ? a.x : -a.x;
+    return r;
+}
+
+// Twiddle exp(-+2 pi i m / n), 0 <= m < n, from the table of the first n/2.
+template <typename C, bool INV>
+__device__ __forceinline__ C twiddle(const C* tw, int m, int n) {
+    const int h = n >> 1;
+    C w = tw[m < h ? m : m - h];
+    if (m >= h) {
+        w.x = -w.x;
+        w.y = -w.y;
+    }
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// In-register DFTs (y_r = sum_q x_q w^(q r), w = exp(-+2 pi i / R)).
+template <typename C, bool INV>
+__device__ __forceinline__ void dft2(C* x) {
+    const C a = x[0];
+    x[0] = cadd(a, x[1]);
+    x[1] = csub(a, x[1]);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft4(C* x) {
+    const C a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
+    const C a2 = cadd(x[1], x[3]), a3 = mul_mi<C, INV>(csub(x[1], x[3]));
+    x[0] = cadd(a0, a2);
+    x[2] = csub(a0, a2);
+    x[1] = cadd(a1, a3);
+    x[3] = csub(a1, a3);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft8(C* x) {
+    using T = decltype(x[0].x);
+    const T h = T(0.70710678118654752440);   // 1/sqrt(2)
+    C e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
+    dft4<C, INV>(e);
+    dft4<C, INV>(o);
+    // o[r] *= w8^r, w8 = (1 -+ i) / sqrt(2)
+    {
+        const C a = o[1];
+        o[1].x = INV ? (a.x - a.y) * h : (a.x + a.y) * h;
+        o[1].y = INV ? (a.x + a.y) * h : (a.y - a.x) * h;
+    }
+    o[2] = mul_mi<C, INV>(o[2]);
+    {
+        const C a = o[3];
+        o[3].x = INV ? -(a.x + a.y) * h : (a.y - a.x) * h;
+        o[3].y = INV ? (a.x - a.y) * h : -(a.x + a.y) * h;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        x[r] = cadd(e[r], o[r]);
+        x[r + 4] = csub(e[r], o[r]);
+    }
+}
+
+// One Stockham stage of radix R on the thread's E elements (E/R butterflies):
+// butterfly jj reads x_q = X[jj + q n/R], scales it by w_L^(q k) (L = Ns R,
+// k = jj mod Ns), takes the R-point DFT and writes y_r to
+// X[(jj - k) R + k + r Ns].  All reads precede a barrier, then the writes.
+template <typename C, bool INV, int R, int E>
+__device__ __forceinline__ void stockham_stage(C* pen, int n, int Ns, int t, const C* tw) {
+    constexpr int B = E / R;
+    const int stride = n / R, per = n / E;
+    C x[E];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int jj = t + b * per;
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[b * R + r] = pen[pidx(jj + r * stride)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int jj = t + b * per;
+        const int k = jj & (Ns - 1);
+        const int step = k * (n / (Ns * R));
+#pragma unroll
+        for (int q = 1; q < R; ++q) x[b * R + q] = cmul(x[b * R + q], twiddle<C, INV>(tw, q * step, n));
+        if (R == 8) dft8<C, INV>(x + b * R);
+        else if (R == 4) dft4<C, INV>(x + b * R);
+        else dft2<C, INV>(x + b * R);
+        const int base = (jj - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) pen[pidx(base + r * Ns)] = x[b * R + r];
     }
     __syncthreads();
 }
 
-// Decimation in frequency: input in natural order, output in bit-reversed order.
+// Transform the block's P pencils in place (natural order in and out; pencil
+// p at buf + p * ns, element e at pidx(e)); the block has exactly
+// fft_threads<T>(n) threads.  `tw` is the block's shared copy of the n/2
+// twiddles.  Radix E = fft_ept stages while they fit, then one of radix 4 or 2.
+template <typename C, bool INV, int E>
+__device__ __forceinline__ void stockham_all(C* buf, int ns, int n, int log2n, const C* tw) {
+    constexpr int LE = E == 8 ? 3 : 2;
+    const int per = n / E;
+    const int p = threadIdx.x / per, t = threadIdx.x - p * per;
+    C* pen = buf + p * ns;
+    int Ns = 1, rem = log2n;
+    for (; rem >= LE; rem -= LE, Ns <<= LE) stockham_stage<C, INV, E, E>(pen, n, Ns, t, tw);
+    if (rem == 2) stockham_stage<C, INV, 4, E>(pen, n, Ns, t, tw);
+    else if (rem == 1) stockham_stage<C, INV, 2, E>(pen, n, Ns, t, tw);
+}
+
 template <typename T, bool INV>
-__device__ void fft_dif(typename Cplx<T>::type* buf, int ns, int n, int log2n, int P,
-                        const typename Cplx<T>::type* tw) {
+__device__ void fft_stockham(typename Cplx<T>::type* buf, int ns, int n, int log2n, const typename Cplx<T>::type* tw) {
     using C = typename Cplx<T>::type;
-    const int half = n >> 1;
-    const int total = P * half;
-    for (int s = log2n - 1; s >= 0; --s) {
-        __syncthreads();
-        const int hs = 1 << s;
-        const int shift = log2n - 1 - s;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int p = b >> (log2n - 1);
-            const int j = b & (half - 1);
-            const int k = j & (hs - 1);
-            const int i0 = ((j >> s) << (s + 1)) + k;
-            C w = tw[k << shift];
-            if (INV) w.y = -w.y;
-            C* base = buf + p * ns;
-            const C a = base[i0];
-            const C c = base[i0 + hs];
-            C dlt;
-            dlt.x = a.x - c.x;
-            dlt.y = a.y - c.y;
-            base[i0].x = a.x + c.x;
-            base[i0].y = a.y + c.y;
-            base[i0 + hs] = cmul(dlt, w);
-        }
-    }
     __syncthreads();
+    if (fft_ept<T>(n) == 4)
+        stockham_all<C, INV, 4>(buf, ns, n, log2n, tw);
+    else
+        stockham_all<C, INV, 8>(buf, ns, n, log2n, tw);
 }
 
 // Shared memory of an FFT block: the n/2 twiddles, then P pencils of n + 1.
@@ -151,12 +240,12 @@ __device__ __forceinline__ void load_twiddles(C* dst, const C* __restrict__ src,
 
 // Elements a thread loads per round; a round's loads are all issued before
 // any of them is stored, so their latencies overlap.
-constexpr int kFftLoadsPerRound = 4;
+constexpr int kFftLoadsPerRound = 8;
 
 // Two real rows of length n -> two half spectra of length h+1 (output rows
 // are the same row indices in A1).  The input rows are zeroed after reading.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
+__global__ void __launch_bounds__(512) k_fft_r2c_rows(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
                                                       RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ twg) {
     using C = typename Cplx<T>::type;
@@ -165,7 +254,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typenam
     const C* tw = sm.tw;
     load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
-    const int ns = n + 1;
+    const int ns = fft_stride(n);
     const int64_t q0 = int64_t(blockIdx.x) * P;
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * blockDim.x) {
         C z[kFftLoadsPerRound];
@@ -191,10 +280,10 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typenam
                 g[at[j]] = T(0);
                 g[at[j] + n] = T(0);
             }
-            buf[(e >> log2n) * ns + bitrev(e & (n - 1), log2n)] = z[j];
+            buf[(e >> log2n) * ns + pidx(e & (n - 1))] = z[j];
         }
     }
-    fft_dit<T, false>(buf, ns, n, log2n, P, tw);
+    fft_stockham<T, false>(buf, ns, n, log2n, tw);
     const int H = h + 1;
     for (int e = threadIdx.x; e < P * H; e += blockDim.x) {
         const int p = e / H;
@@ -202,8 +291,8 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typenam
         const int64_t q = q0 + p;
         if (q >= rp.npairs) continue;
         const int64_t r0 = pair_row(rp, q);
-        const C zk = buf[p * ns + k];
-        const C zm = buf[p * ns + ((n - k) & (n - 1))];
+        const C zk = buf[p * ns + pidx(k)];
+        const C zm = buf[p * ns + pidx((n - k) & (n - 1))];
         C A, Bv;
         A.x = (zk.x + zm.x) * T(0.5);
         A.y = (zk.y - zm.y) * T(0.5);
@@ -216,7 +305,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c_rows(T* __restrict__ g, typenam
 
 // Two half spectra -> two real rows, by Hermitian completion.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
+__global__ void __launch_bounds__(512) k_fft_c2r_rows(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
                                                       RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ twg) {
     using C = typename Cplx<T>::type;
@@ -225,7 +314,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::ty
     const C* tw = sm.tw;
     load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
-    const int ns = n + 1;
+    const int ns = fft_stride(n);
     const int H = h + 1;
     const int64_t q0 = int64_t(blockIdx.x) * P;
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * blockDim.x) {
@@ -267,17 +356,17 @@ __global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::ty
                 z.x = T(0);
                 z.y = T(0);
             }
-            buf[(e >> log2n) * ns + pos] = z;
+            buf[(e >> log2n) * ns + pidx(pos)] = z;
         }
     }
-    fft_dif<T, true>(buf, ns, n, log2n, P, tw);
+    fft_stockham<T, true>(buf, ns, n, log2n, tw);
     for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
         const int p = e >> log2n;
         const int l = e & (n - 1);
         const int64_t q = q0 + p;
         if (q >= rp.npairs) continue;
         const int64_t r0 = pair_row(rp, q);
-        const C v = buf[p * ns + bitrev(l, log2n)];
+        const C v = buf[p * ns + pidx(l)];
         g[r0 * n + l] = v.x;
         g[(r0 + 1) * n + l] = v.y;
     }
@@ -289,7 +378,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r_rows(const typename Cplx<T>::ty
 // o in [olo, olo + ocnt) are transformed, and a FULL output is stored only for
 // k in [klo, klo + kcnt).
 template <typename T, int INM, int OUTM, bool INV>
-__global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* __restrict__ in,
+__global__ void __launch_bounds__(512) k_fft_axis(const typename Cplx<T>::type* __restrict__ in,
                                                   typename Cplx<T>::type* __restrict__ out, int64_t olo, int64_t ocnt,
                                                   int64_t I, int klo, int kcnt, int n, int log2n, int h,
                                                   const typename Cplx<T>::type* __restrict__ twg) {
@@ -299,7 +388,7 @@ __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* 
     const C* tw = sm.tw;
     load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
-    const int ns = n + 1;
+    const int ns = fft_stride(n);
     const int64_t Q = ocnt * I;
     const int64_t q0 = int64_t(blockIdx.x) * P;
     const int Lin = INM == FULL ? n : 2 * h + 1;
@@ -330,10 +419,10 @@ __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* 
             const int e = e0 + j * blockDim.x + threadIdx.x;
             const int k = e / P;
             const int pos = INM == FULL ? k : ((k - h) & (n - 1));
-            buf[(e - k * P) * ns + bitrev(pos, log2n)] = v[j];
+            buf[(e - k * P) * ns + pidx(pos)] = v[j];
         }
     }
-    fft_dit<T, INV>(buf, ns, n, log2n, P, tw);
+    fft_stockham<T, INV>(buf, ns, n, log2n, tw);
     for (int e = threadIdx.x; e < P * kn; e += blockDim.x) {
         const int kk = e / P;
         const int pl = e - kk * P;
@@ -342,7 +431,7 @@ __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* 
         const int k = k0 + kk;
         const int64_t o = olo + q / I, i = q % I;
         const int pos = OUTM == FULL ? k : ((k - h) & (n - 1));
-        out[(o * Lout + k) * I + i] = buf[pl * ns + pos];
+        out[(o * Lout + k) * I + i] = buf[pl * ns + pidx(pos)];
     }
 }
 
@@ -351,7 +440,7 @@ __global__ void __launch_bounds__(256) k_fft_axis(const typename Cplx<T>::type* 
 // Only axis-0 positions in [xlo, xlo + xcnt) are loaded (the rest are zero)
 // and stored (the rest are never read).
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::type* __restrict__ data, int64_t I,
+__global__ void __launch_bounds__(512) k_fft_axis0_convolve(typename Cplx<T>::type* __restrict__ data, int64_t I,
                                                             int xlo, int xcnt, int n, int log2n, int h,
                                                             const T* __restrict__ mult,
                                                             const typename Cplx<T>::type* __restrict__ twg) {
@@ -361,7 +450,7 @@ __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::ty
     const C* tw = sm.tw;
     load_twiddles(sm.tw, twg, n);
     const int P = fft_pencils(n);
-    const int ns = n + 1;
+    const int ns = fft_stride(n);
     const int64_t q0 = int64_t(blockIdx.x) * P;
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * blockDim.x) {
         C v[kFftLoadsPerRound];
@@ -379,7 +468,7 @@ __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::ty
             const int e = e0 + j * blockDim.x + threadIdx.x;
             if (e >= P * n) continue;
             const int k = e / P;
-            buf[(e - k * P) * ns + bitrev(k, log2n)] = v[j];
+            buf[(e - k * P) * ns + pidx(k)] = v[j];
         }
     }
     // when one round covers the block, the multiplier of each element this
@@ -395,14 +484,14 @@ __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::ty
         const int k = pos <= (n >> 1) ? pos : pos - n;
         mv[j] = (one_round && e < P * n && q < I && k >= -h && k <= h) ? mult[int64_t(k + h) * I + q] : T(0);
     }
-    fft_dit<T, false>(buf, ns, n, log2n, P, tw);
+    fft_stockham<T, false>(buf, ns, n, log2n, tw);
     if (one_round) {
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = j * blockDim.x + threadIdx.x;
             if (e >= P * n) continue;
             const int pos = e / P;
-            C& v = buf[(e - pos * P) * ns + pos];
+            C& v = buf[(e - pos * P) * ns + pidx(pos)];
             v.x *= mv[j];
             v.y *= mv[j];
         }
@@ -412,7 +501,7 @@ __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::ty
             const int pl = e - pos * P;
             const int64_t q = q0 + pl;
             const int k = pos <= (n >> 1) ? pos : pos - n;
-            C& v = buf[pl * ns + pos];
+            C& v = buf[pl * ns + pidx(pos)];
             if (q < I && k >= -h && k <= h) {
                 const T m = mult[int64_t(k + h) * I + q];
                 v.x *= m;
@@ -423,12 +512,12 @@ __global__ void __launch_bounds__(256) k_fft_axis0_convolve(typename Cplx<T>::ty
             }
         }
     }
-    fft_dif<T, true>(buf, ns, n, log2n, P, tw);
+    fft_stockham<T, true>(buf, ns, n, log2n, tw);
     for (int e = threadIdx.x; e < P * xcnt; e += blockDim.x) {
         const int k = xlo + e / P;
         const int pl = e % P;
         const int64_t q = q0 + pl;
-        if (q < I) data[int64_t(k) * I + q] = buf[pl * ns + bitrev(k, log2n)];
+        if (q < I) data[int64_t(k) * I + q] = buf[pl * ns + pidx(k)];
     }
 }
 
@@ -498,14 +587,14 @@ __global__ void k_fill_forward(const double* __restrict__ fhat, int d, int h, co
 
 template <typename T>
 static size_t fft_smem_bytes(int n) {
-    return (size_t(n / 2) + size_t(fft_pencils(n)) * size_t(n + 1)) * sizeof(typename Cplx<T>::type);
+    return (size_t(n / 2) + size_t(fft_pencils(n)) * size_t(fft_stride(n))) * sizeof(typename Cplx<T>::type);
 }
 
 // Largest dynamic shared memory any FFT launch of this precision can use:
 // one pencil of the largest length, 4096, and its twiddles.
 template <typename T>
 static size_t fft_smem_max() {
-    return size_t(2048 + 4096 + 1) * sizeof(typename Cplx<T>::type);
+    return size_t(2048 + fft_stride(4096)) * sizeof(typename Cplx<T>::type);
 }
 
 // Opt a kernel into its largest shared-memory size once per device (the cache
@@ -557,7 +646,7 @@ static cudaError_t run_r2c(const FftPlan& f, int64_t* launches, cudaStream_t s) 
     SK_TRY((ensure_smem<T, k_fft_r2c_rows<T>>()));
     const RowPairs rp = row_pairs(f);
     const int P = fft_pencils(f.n);
-    k_fft_r2c_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_r2c_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<T*>(f.grid), static_cast<C*>(f.A1), rp, f.n, f.log2n, f.h, static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
@@ -569,7 +658,7 @@ static cudaError_t run_c2r(const FftPlan& f, int64_t* launches, cudaStream_t s) 
     SK_TRY((ensure_smem<T, k_fft_c2r_rows<T>>()));
     const RowPairs rp = row_pairs(f);
     const int P = fft_pencils(f.n);
-    k_fft_c2r_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_c2r_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<const C*>(f.A1), static_cast<T*>(f.grid_out), rp, f.n, f.log2n, f.h,
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
@@ -583,7 +672,7 @@ static cudaError_t run_axis(const FftPlan& f, const void* in, void* out, int64_t
     SK_TRY((ensure_smem<T, k_fft_axis<T, INM, OUTM, INV>>()));
     const int P = fft_pencils(f.n);
     const int64_t Q = ocnt * I;
-    k_fft_axis<T, INM, OUTM, INV><<<unsigned((Q + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_axis<T, INM, OUTM, INV><<<unsigned((Q + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<const C*>(in), static_cast<C*>(out), olo, ocnt, I, klo, kcnt, f.n, f.log2n, f.h,
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
@@ -609,7 +698,7 @@ static cudaError_t run_axis0_convolve(const FftPlan& f, void* data, int64_t I, i
     const int P = fft_pencils(f.n);
     int xlo, xcnt;
     axis0_range(f, xlo, xcnt);
-    k_fft_axis0_convolve<T><<<unsigned((I + P - 1) / P), fft_threads(f.n), fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_axis0_convolve<T><<<unsigned((I + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<C*>(data), I, xlo, xcnt, f.n, f.log2n, f.h, static_cast<const T*>(f.mult),
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;

@@ -99,9 +99,11 @@ def test_adjoint_nfft_matches_adjoint_ndft(d, N, precision):
     want = ofs.adjoint_ndft(x + 0.5, w, N)
     err = np.max(np.abs(_common(got, h, d) - want)) / np.sum(np.abs(w))
     assert err <= TOL_FS[precision]
-    # Hermitian symmetry of the real-data spectrum, including the +N/2 planes
+    # Hermitian symmetry of the real-data spectrum, including the +N/2 planes:
+    # exact in exact arithmetic, so to the precision's rounding level here
     flip = got[tuple([slice(None, None, -1)] * d)]
-    assert np.max(np.abs(got - np.conj(flip))) <= 1e-12 * np.max(np.abs(got)) + 1e-300
+    sym_tol = 1e-12 if precision == sk.SK_FP64 else 1e-6
+    assert np.max(np.abs(got - np.conj(flip))) <= sym_tol * np.max(np.abs(got)) + 1e-300
 
 
 @pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
