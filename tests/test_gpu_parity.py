@@ -228,6 +228,21 @@ def test_kernel_apply_matches_exact_sums(d, n, m, N, eps, precision):
     assert efs(tt.cpu().numpy(), osk.kernel_apply_T(x, y, u, eps, 2.0)) <= TOL_FS[precision]
 
 
+@pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
+@pytest.mark.parametrize("d,N", [(1, 2048), (1, 1024), (2, 512)])
+def test_kernel_apply_longest_pencils(d, N, precision):
+    # the largest FFT lengths (n_os = 4096 in 1-D, where FP64 pencils switch
+    # to 8 elements per thread; 1024 in 2-D) against the exact sums
+    x = wl.uniform_ball(1500, d, 0.2, 51)
+    y = wl.uniform_ball(1300, d, 0.2, 52)
+    eps = 2e-4 if d == 1 else 0.002
+    plan = plan_for(x, y, eps=eps, N=N, precision=precision, user_geometry=False)
+    v = wl.positive_vector(len(y), 53)
+    t = np.zeros(len(x))
+    sk.sk_kernel_apply(plan, 0, v, t)
+    assert efs(t, osk.kernel_apply(x, y, v, eps, 2.0)) <= TOL_FS[precision]
+
+
 def test_kernel_apply_host_buffers_and_ragged_tiny_sizes():
     # host (numpy) in/out buffers; sizes below one block and not multiples of anything
     for n, m in [(1, 1), (1, 5), (7, 1), (33, 65)]:
