@@ -178,13 +178,14 @@ int sk_set_domain(sk_plan* plan, int domain);
 
 /*
  * Choose how the interpolation step of Eq. (fastsum) (the NFFT: the grid at the
- * target points) runs.  SK_KERNELS_TENSOR (the default where supported: d = 3,
- * SK_FP32, 2 <= m_w <= 5): per bin of 4 x 4 x 8 cells, the contraction of the
- * bin's window box with the z-weights of 128 points at a time is one tensor-core
- * product (tcgen05, TF32 operands split into high and low parts, three products,
- * FP32 accumulation), and the x- and y-weights are applied per point on the CUDA
- * cores.  SK_KERNELS_SIMT: CUDA cores only.  Both meet the FP32 accuracy of the
- * plan; their sums differ by rounding.
+ * target points) runs.  SK_KERNELS_TENSOR (the default where supported: SK_FP32
+ * plans with d = 3 and 2 <= m_w <= 5, or d = 2): per bin (4 x 4 x 8 cells in
+ * 3-D, a strip of 33 - 2 m_w by 8 cells in 2-D) the contraction of the bin's
+ * window box with the last-axis weights of 128 points at a time is one
+ * tensor-core product (tcgen05, TF32 operands split into high and low parts,
+ * three products, FP32 accumulation); the other axes' weights are applied per
+ * point on the CUDA cores.  SK_KERNELS_SIMT: CUDA cores only.  Both meet the
+ * FP32 accuracy of the plan; their sums differ by rounding.
  * Errors: SK_ERR_ARG for a NULL plan or an unknown value; SK_ERR_UNSUPPORTED
  * for SK_KERNELS_TENSOR on a plan it does not support (nothing changes).
  * A tensor-core wait that gives up (bounded) makes sk_solve / sk_solve_batch

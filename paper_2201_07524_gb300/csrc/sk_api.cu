@@ -360,6 +360,33 @@ int read_int(sk_plan* P, const int* dev) {
     return v;
 }
 
+// Runs of at most `run` consecutive points of one bin (bin CSR `bs`), most
+// points first, so the workers that take the last tasks take short ones;
+// uploaded as (bin, first point, end point) triples.
+int* upload_runs(sk_plan* P, const std::vector<int>& bs, int run, int& count) {
+    std::vector<int> tk;
+    for (int b = 0; b + 1 < int(bs.size()); ++b)
+        for (int s0 = bs[b]; s0 < bs[b + 1]; s0 += run) {
+            tk.push_back(b);
+            tk.push_back(s0);
+            tk.push_back(std::min(bs[b + 1], s0 + run));
+        }
+    const int nt = int(tk.size() / 3);
+    std::vector<int> order(nt);
+    for (int i = 0; i < nt; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+        return tk[3 * p + 2] - tk[3 * p + 1] > tk[3 * q + 2] - tk[3 * q + 1];
+    });
+    std::vector<int> sorted(tk.size());
+    for (int i = 0; i < nt; ++i)
+        for (int k = 0; k < 3; ++k) sorted[3 * i + k] = tk[3 * order[i] + k];
+    count = nt;
+    int* d = static_cast<int*>(dalloc(P, size_t(3 * std::max(nt, 1)) * sizeof(int)));
+    if (nt > 0) CK(cudaMemcpyAsync(d, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    return d;
+}
+
 template <typename T>
 void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, int64_t n) {
     c.n = n;
@@ -469,45 +496,23 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
             CK(cudaMemcpyAsync(c.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
         CK(cudaStreamSynchronize(P->ps));
     }
-    // Run tasks: runs of at most `run` points of one bin, most points first,
-    // so the workers that take the last tasks take short ones.  2-D strips
-    // (one warp per task): at most kStripMaxPts, and small clouds take
-    // shorter runs (down to one batch of 32) so that their tasks still reach
-    // every SM.  3-D tensor-core interpolation (one block per task): at most
-    // kTcRunPts, whole tiles of 128.
+    // Run tasks: 2-D strips (one warp per task): at most kStripMaxPts points,
+    // and small clouds take shorter runs (down to one batch of 32) so that
+    // their tasks still reach every SM; tensor-core interpolation (one block
+    // per task): at most kTcRunPts, whole tiles of 128.
     if (P->d == 2 || P->tc_ok) {
         int dev = 0, sms = 1;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        int run = kTcRunPts;
-        if (P->d == 2) {
-            const int64_t per_warp = (n + int64_t(sms) * 8 - 1) / (int64_t(sms) * 8);
-            run = int(std::min<int64_t>(kStripMaxPts, std::max<int64_t>(32, (per_warp + 31) / 32 * 32)));
-        }
         std::vector<int> bs(size_t(P->nbins) + 1);
         CK(cudaMemcpyAsync(bs.data(), c.bin_start, bs.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
         CK(cudaStreamSynchronize(P->ps));
-        std::vector<int> tk;
-        for (int b = 0; b < P->nbins; ++b)
-            for (int s0 = bs[b]; s0 < bs[b + 1]; s0 += run) {
-                tk.push_back(b);
-                tk.push_back(s0);
-                tk.push_back(std::min(bs[b + 1], s0 + run));
-            }
-        const int nt = int(tk.size() / 3);
-        std::vector<int> order(nt);
-        for (int i = 0; i < nt; ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
-            return tk[3 * p + 2] - tk[3 * p + 1] > tk[3 * q + 2] - tk[3 * q + 1];
-        });
-        std::vector<int> sorted(tk.size());
-        for (int i = 0; i < nt; ++i)
-            for (int k = 0; k < 3; ++k) sorted[3 * i + k] = tk[3 * order[i] + k];
-        c.nstasks = nt;
-        c.stasks = static_cast<int*>(dalloc(P, size_t(3 * std::max(nt, 1)) * sizeof(int)));
-        if (nt > 0)
-            CK(cudaMemcpyAsync(c.stasks, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
-        CK(cudaStreamSynchronize(P->ps));
+        if (P->d == 2) {
+            const int64_t per_warp = (n + int64_t(sms) * 8 - 1) / (int64_t(sms) * 8);
+            const int run = int(std::min<int64_t>(kStripMaxPts, std::max<int64_t>(32, (per_warp + 31) / 32 * 32)));
+            c.stasks = upload_runs(P, bs, run, c.nstasks);
+        }
+        if (P->tc_ok) c.ttasks = upload_runs(P, bs, kTcRunPts, c.nttasks);
     }
     k_fill<<<nblk(n), 256, 0, P->ps>>>(c.scal, n, 1.0);
     CK(cudaGetLastError());
@@ -715,8 +720,8 @@ void prepare_kernels(sk_plan* P) {
     }
     if (P->tc_ok) {
         InterpArgs ia{};
-        ia.nstasks = 0;
-        CK(launch_interp3_tc(P->W, ia, Epilogue{}, P->ps));
+        ia.nttasks = 0;
+        CK(launch_interp_tc(P->d, P->W, ia, Epilogue{}, P->ps));
     }
     CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
 }
@@ -807,13 +812,15 @@ void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
     a.ncols = dst.ncols;
     a.stasks = dst.stasks;
     a.nstasks = dst.nstasks;
+    a.ttasks = dst.ttasks;
+    a.nttasks = dst.nttasks;
     a.queue = P->ticket + 2;
     a.grid = P->fft.grid_out;
     a.wp = P->wp;
     int st = stage_begin(P, SK_STAGE_INTERP);
     if (P->tc && std::is_same<T, float>::value) {
-        if (a.nstasks > 0) ++P->launches;
-        CK(launch_interp3_tc(P->W, a, e, P->ps));
+        if (a.nttasks > 0) ++P->launches;
+        CK(launch_interp_tc(P->d, P->W, a, e, P->ps));
     } else {
         CK(launch_interp<T>(P->d, P->W, a, e, &P->launches, P->ps));
     }
@@ -1392,7 +1399,7 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
             }
         }
         if (P->tc_ok) {
-            const int need = interp3_tc_blocks(P->W, std::max(P->X.nstasks, P->Y.nstasks));
+            const int need = interp_tc_blocks(P->d, P->W, std::max(P->X.nttasks, P->Y.nttasks));
             if (need <= 0) throw Fail{SK_ERR_CUDA};
             if (need > P->partial_blocks) {
                 P->partial_blocks = need;

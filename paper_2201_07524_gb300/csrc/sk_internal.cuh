@@ -77,6 +77,8 @@ struct Cloud {
     int ncols = 0;
     int* stasks = nullptr;      // 2-D strip tasks (bin, first point, end point), most points first
     int nstasks = 0;
+    int* ttasks = nullptr;      // tensor-core interpolation runs (bin, first point, end point), most points first
+    int nttasks = 0;
     // near-field cell list (only when the kernel needs near-field correction)
     int* nf_start = nullptr;    // CSR over near-field cells
     int* nf_idx = nullptr;      // near-field position -> sorted index
@@ -161,6 +163,8 @@ struct InterpArgs {
     int ncols;
     const int* stasks;     // 2-D strip tasks: (bin, first point, end point), most points first
     int nstasks;
+    const int* ttasks;     // tensor-core runs: (bin, first point, end point), most points first
+    int nttasks;
     unsigned* queue;       // [0] next queue entry, [1] warps finished; zero between launches
     int nb[3];
     int n_os;
@@ -232,12 +236,12 @@ constexpr int kStripMaxPts = 128;   // points per 2-D strip task
 inline int strip_bx(int W) { return 33 - W; }   // x-cells of a 2-D strip: its window spans 32 rows
 constexpr int kStripBy = 8;         // y-cells of a 2-D strip
 bool column_kernels(int d, int W);
-// Tensor-core (tcgen05) interpolation of 3-D FP32 plans (sk_tc.cu): tasks are
-// runs of at most kTcRunPts points of one bin in InterpArgs::stasks.
+// Tensor-core (tcgen05) interpolation of FP32 plans, 2-D and 3-D (sk_tc.cu):
+// tasks are runs of at most kTcRunPts points of one bin in InterpArgs::ttasks.
 constexpr int kTcRunPts = 512;
 bool tc_supported(int d, int W, int precision_fp32);
-cudaError_t launch_interp3_tc(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s);
-int interp3_tc_blocks(int W, int ntasks);
+cudaError_t launch_interp_tc(int d, int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s);
+int interp_tc_blocks(int d, int W, int ntasks);
 void bin_shape(int d, int W, int B[3]);
 template <typename T> cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches);
 template <typename T> cudaError_t launch_fft_adjoint(const FftPlan& f, double* fhat, cudaStream_t s,

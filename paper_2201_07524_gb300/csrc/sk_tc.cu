@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
         if (tid == 0) task = int(atomicAdd(a.queue, 1u));
         __syncthreads();
         const int t = task;
-        if (t >= a.nstasks || abort_flag) break;
-        const int bin = a.stasks[3 * t], start = a.stasks[3 * t + 1], end = a.stasks[3 * t + 2];
+        if (t >= a.nttasks || abort_flag) break;
+        const int bin = a.ttasks[3 * t], start = a.ttasks[3 * t + 1], end = a.ttasks[3 * t + 2];
         const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
         const int x0 = bx * 4, y0 = by * 4, z0 = bz * 8;
         // the box: rows (x0 - (m-1) + i, y0 - (m-1) + j), z from z0 - 4; zero
@@ -327,6 +327,178 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
     if (warp == 0) tc_dealloc(tmem, S::COLS);
 }
 
+
+// ------------------------------------------------------------ 2-D interpolation
+// The same contraction for 2-D plans.  A bin is a strip of 33 - W x-cells by
+// 8 y-cells, so its box is exactly 32 x-rows by 24 y-entries (from y0 - 8,
+// 16-byte aligned, to y0 + 15, past the last tap y0 + 7 + m for m <= 8):
+// H = Wy Gᵀ is one 128 x 32 x 24 product per tile (N = 32 box rows, 32
+// tensor-memory columns).  The point's x-offset in the strip spans 33 - W
+// values, too many for register selects, so each thread parks its 32 H
+// values in its own shared-memory row and reads back the W of its window.
+template <int W>
+struct Tc2 {
+    static constexpr int M_W = W / 2;
+    static constexpr int BX = 33 - W;            // x-cells of a strip bin
+    static constexpr int N = 32;                 // box x-rows
+    static constexpr int YLEAD = 8;              // the box starts at y0 - 8
+    static constexpr int KY = 24;                // y entries
+    static constexpr int KC = KY / 4;
+    static constexpr int LBO = 128, SBO = KC * 128;
+    static constexpr int A_BYTES = 16 * SBO;
+    static constexpr int B_BYTES = (N / 8) * SBO;
+    static constexpr int HS = 36;                // floats per thread's H row (16-byte rows, staggered banks)
+    static constexpr int H_BYTES = 128 * HS * 4;
+    static constexpr int OPERANDS = 2 * A_BYTES + 2 * B_BYTES + H_BYTES;
+    static constexpr int COLS = 32;
+    static constexpr int BLOCKS_PER_SM = 8;
+    static_assert(M_W >= 2 && M_W <= 8, "window widths 4..16");
+};
+
+template <int W>
+__global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
+    using S = Tc2<W>;
+    constexpr int m = S::M_W;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* a_hi = smem_raw;
+    unsigned char* a_lo = a_hi + S::A_BYTES;
+    unsigned char* b_hi = a_lo + S::A_BYTES;
+    unsigned char* b_lo = b_hi + S::B_BYTES;
+    float* hrow = reinterpret_cast<float*>(b_lo + S::B_BYTES) + threadIdx.x * S::HS;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int task, abort_flag;
+    __shared__ unsigned warps_done;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc_alloc(&tmem_slot, S::COLS);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        warps_done = 0u;
+        abort_flag = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);
+    constexpr uint32_t idesc = tc_idesc_tf32(128, S::N);
+    const float* c0 = static_cast<const float*>(a.coord[0]);
+    const float* c1 = static_cast<const float*>(a.coord[1]);
+    const float* grid = static_cast<const float*>(a.grid);
+    const int n = a.n_os;
+    unsigned char* row_hi = a_hi + (tid >> 3) * S::SBO + (tid & 7) * 16;
+    unsigned char* row_lo = a_lo + (tid >> 3) * S::SBO + (tid & 7) * 16;
+    uint32_t phase = 0;
+    bool failed = false;
+    double sq = 0.0, bad = 0.0, dot = 0.0;
+    for (;;) {
+        if (tid == 0) task = int(atomicAdd(a.queue, 1u));
+        __syncthreads();
+        const int t = task;
+        if (t >= a.nttasks || abort_flag) break;
+        const int bin = a.ttasks[3 * t], start = a.ttasks[3 * t + 1], end = a.ttasks[3 * t + 2];
+        const int x0 = (bin / a.nb[1]) * S::BX, y0 = (bin % a.nb[1]) * 8;
+        // the box: rows x0 - (m-1) + i, y from y0 - 8; zero outside the grid
+        {
+            constexpr int LOADS = (S::N * S::KC + 127) / 128;
+            float4 v[LOADS];
+#pragma unroll
+            for (int l = 0; l < LOADS; ++l) {
+                const int q = tid + 128 * l;
+                const int r = q / S::KC, c = q - r * S::KC;
+                const int xr = x0 - (m - 1) + r, yc = y0 - S::YLEAD + 4 * c;
+                v[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < S::N * S::KC && xr >= 0 && xr < n && yc >= 0 && yc + 4 <= n)
+                    v[l] = __ldg(reinterpret_cast<const float4*>(grid + int64_t(xr) * n + yc));
+            }
+#pragma unroll
+            for (int l = 0; l < LOADS; ++l) {
+                const int q = tid + 128 * l;
+                if (q >= S::N * S::KC) continue;
+                const int r = q / S::KC, c = q - r * S::KC;
+                const float4 h = make_float4(tf32_hi(v[l].x), tf32_hi(v[l].y), tf32_hi(v[l].z), tf32_hi(v[l].w));
+                const int off = (r >> 3) * S::SBO + c * S::LBO + (r & 7) * 16;
+                *reinterpret_cast<float4*>(b_hi + off) = h;
+                *reinterpret_cast<float4*>(b_lo + off) =
+                    make_float4(v[l].x - h.x, v[l].y - h.y, v[l].z - h.z, v[l].w - h.w);
+            }
+        }
+        for (int base = start; base < end; base += 128) {
+            const int p = base + tid;
+            const bool ok = p < end;
+            float wx[W], wy[W];
+            int dx = 0, k0 = 0;
+            EpiPrefetch ep;
+            ep.load(e, p, ok);
+            if (ok) {
+                int fx, fy;
+                window_poly<W, float>(c0[p], a.wp, 1.f, fx, wx);
+                window_poly<W, float>(c1[p], a.wp, 1.f, fy, wy);
+                dx = min(max(fx - x0, 0), S::BX - 1);
+                k0 = min(max(fy - y0 + S::YLEAD - (m - 1), 0), S::KY - W);
+            } else {
+#pragma unroll
+                for (int k = 0; k < W; ++k) wx[k] = wy[k] = 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c < S::KC; ++c) {
+                *reinterpret_cast<float4*>(row_hi + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4*>(row_lo + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int kk = k0 + k;
+                const int off = (kk >> 2) * S::LBO + (kk & 3) * 4;
+                const float h = tf32_hi(wy[k]);
+                *reinterpret_cast<float*>(row_hi + off) = h;
+                *reinterpret_cast<float*>(row_lo + off) = wy[k] - h;
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (abort_flag) break;
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t ah = smem_addr(a_hi), al = smem_addr(a_lo), bh = smem_addr(b_hi), bl = smem_addr(b_lo);
+#pragma unroll
+                for (int s2 = 0; s2 < S::KY / 8; ++s2) {
+                    const uint32_t o = uint32_t(s2 * 2 * S::LBO);
+                    tc_mma_tf32(tmem, tc_desc(ah + o, S::LBO, S::SBO), tc_desc(bh + o, S::LBO, S::SBO), idesc, s2 > 0);
+                    tc_mma_tf32(tmem, tc_desc(ah + o, S::LBO, S::SBO), tc_desc(bl + o, S::LBO, S::SBO), idesc, 1u);
+                    tc_mma_tf32(tmem, tc_desc(al + o, S::LBO, S::SBO), tc_desc(bh + o, S::LBO, S::SBO), idesc, 1u);
+                }
+                tc_commit(&bar);
+            }
+            const bool done = mbar_wait(&bar, phase);
+            phase ^= 1u;
+            if (!done) {
+                failed = true;
+                abort_flag = 1;
+                if (e.status) atomicOr(e.status, 4);
+            }
+            tc_fence_after();
+            {
+                float h[32];
+                tmem_ld32(tlane, h);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    *reinterpret_cast<float4*>(hrow + 4 * c) = make_float4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+            }
+            float tv = 0.f;
+#pragma unroll
+            for (int q = 0; q < W; ++q) tv = fmaf(wx[q], hrow[dx + q], tv);
+            if (ok && !failed) epi_point_pre(e, p, double(tv), ep.q, ep.a, sq, bad, dot);
+            tc_fence_before();
+        }
+    }
+    if (failed) mbar_wait(&bar, phase ^ 1u);
+    queue_leave(a.queue, lane);
+    epi_finish_warps(e, sq, bad, dot, &warps_done);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, S::COLS);
+}
+
 // ------------------------------------------------------------ launchers
 struct TcLaunch {
     int smem = 0;     // dynamic shared memory per block
@@ -369,57 +541,83 @@ static cudaError_t tc_config(TcLaunch& L) {
     return cudaSuccess;
 }
 
-template <int W>
-static cudaError_t interp3_tc_config(TcLaunch*& out) {
+template <int D, int W>
+static cudaError_t interp_tc_config(TcLaunch*& out) {
     static TcLaunch cfg[64];
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     TcLaunch& L = cfg[dev & 63];
     if (L.blocks == 0) {
-        using S = Tc3<W>;
-        err = tc_config<k_interp3_tc<W>, S::OPERANDS, S::BLOCKS_PER_SM>(L);
+        if constexpr (D == 3) {
+            using S = Tc3<W>;
+            err = tc_config<k_interp3_tc<W>, S::OPERANDS, S::BLOCKS_PER_SM>(L);
+        } else {
+            using S = Tc2<W>;
+            err = tc_config<k_interp2_tc<W>, S::OPERANDS, S::BLOCKS_PER_SM>(L);
+        }
         if (err != cudaSuccess) return err;
     }
     out = &L;
     return cudaSuccess;
 }
 
-template <int W>
-static cudaError_t interp3_tc_one(const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
+template <int D, int W>
+static cudaError_t interp_tc_one(const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
     TcLaunch* L = nullptr;
-    cudaError_t err = interp3_tc_config<W>(L);
+    cudaError_t err = interp_tc_config<D, W>(L);
     if (err != cudaSuccess) return err;
-    if (a.nstasks == 0) return cudaSuccess;
-    const int blocks = std::max(1, std::min(L->blocks, a.nstasks));
-    k_interp3_tc<W><<<blocks, 128, L->smem, s>>>(a, e);
+    if (a.nttasks == 0) return cudaSuccess;
+    const int blocks = std::max(1, std::min(L->blocks, a.nttasks));
+    if constexpr (D == 3)
+        k_interp3_tc<W><<<blocks, 128, L->smem, s>>>(a, e);
+    else
+        k_interp2_tc<W><<<blocks, 128, L->smem, s>>>(a, e);
     return cudaGetLastError();
 }
 
-bool tc_supported(int d, int W, int precision_fp32) { return d == 3 && precision_fp32 && W >= 4 && W <= 10; }
-
-cudaError_t launch_interp3_tc(int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
-    switch (W) {
-        case 4: return interp3_tc_one<4>(a, e, s);
-        case 6: return interp3_tc_one<6>(a, e, s);
-        case 8: return interp3_tc_one<8>(a, e, s);
-        case 10: return interp3_tc_one<10>(a, e, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-int interp3_tc_blocks(int W, int ntasks) {
+template <int D, int W>
+static int interp_tc_grid(int ntasks) {
     TcLaunch* L = nullptr;
-    cudaError_t err = cudaErrorInvalidValue;
-    switch (W) {
-        case 4: err = interp3_tc_config<4>(L); break;
-        case 6: err = interp3_tc_config<6>(L); break;
-        case 8: err = interp3_tc_config<8>(L); break;
-        case 10: err = interp3_tc_config<10>(L); break;
-        default: break;
-    }
-    if (err != cudaSuccess || !L) return 0;
+    if (interp_tc_config<D, W>(L) != cudaSuccess || !L) return 0;
     return std::max(1, std::min(L->blocks, ntasks));
 }
+
+bool tc_supported(int d, int W, int precision_fp32) {
+    return precision_fp32 && ((d == 3 && W >= 4 && W <= 10) || (d == 2 && W >= 4 && W <= 16));
+}
+
+#define SK_TC_CASES(FN, ...)                                    \
+    if (d == 3) {                                               \
+        switch (W) {                                            \
+            case 4: return FN<3, 4>(__VA_ARGS__);               \
+            case 6: return FN<3, 6>(__VA_ARGS__);               \
+            case 8: return FN<3, 8>(__VA_ARGS__);               \
+            case 10: return FN<3, 10>(__VA_ARGS__);             \
+            default: break;                                     \
+        }                                                       \
+    } else if (d == 2) {                                        \
+        switch (W) {                                            \
+            case 4: return FN<2, 4>(__VA_ARGS__);               \
+            case 6: return FN<2, 6>(__VA_ARGS__);               \
+            case 8: return FN<2, 8>(__VA_ARGS__);               \
+            case 10: return FN<2, 10>(__VA_ARGS__);             \
+            case 12: return FN<2, 12>(__VA_ARGS__);             \
+            case 14: return FN<2, 14>(__VA_ARGS__);             \
+            case 16: return FN<2, 16>(__VA_ARGS__);             \
+            default: break;                                     \
+        }                                                       \
+    }
+
+cudaError_t launch_interp_tc(int d, int W, const InterpArgs& a, const Epilogue& e, cudaStream_t s) {
+    SK_TC_CASES(interp_tc_one, a, e, s)
+    return cudaErrorInvalidValue;
+}
+
+int interp_tc_blocks(int d, int W, int ntasks) {
+    SK_TC_CASES(interp_tc_grid, ntasks)
+    return 0;
+}
+#undef SK_TC_CASES
 
 }  // namespace sk

@@ -331,3 +331,47 @@ def sk_direct_residual_noalloc(x, u, a, y, v, eps, r, t_out, stats_out, stream=N
                                            _ptr(t_out, n, "t_out"), _ptr(stats_out, 2, "stats_out"),
                                            _stream(stream)), "sk_direct_residual_noalloc")
     return t_out, stats_out
+
+
+def _divergence_function():
+    """torch.autograd.Function over sk_divergence (built on first use, so that
+    importing this module does not require torch)."""
+    import torch
+
+    class SinkhornDivergence(torch.autograd.Function):
+        """Sinkhorn divergence S = s(x, y) - s(x, x)/2 - s(y, y)/2 as a function
+        of the positions and weights (CUDA float64 tensors).  The forward pass
+        solves the three problems through sk_divergence, which also returns the
+        gradients (the dual variables and the position gradients at the final
+        iterates, see sk_grad); the backward pass scales those by the incoming
+        gradient.  No iterate is stored."""
+
+        @staticmethod
+        def forward(ctx, x, a, y, b, eps, r, max_iter, tol, params):
+            x, a, y, b = (t.detach().contiguous() for t in (x, a, y, b))
+            ga, gb = torch.zeros_like(a), torch.zeros_like(b)
+            gx, gy = torch.zeros_like(x), torch.zeros_like(y)
+            sd, _, _, _ = sk_divergence(x, a, y, b, eps, r, max_iter, tol, params, grad_a=ga, grad_b=gb,
+                                        grad_x=gx, grad_y=gy)
+            ctx.save_for_backward(gx, ga, gy, gb)
+            return torch.tensor(sd, dtype=torch.float64, device=x.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            gx, ga, gy, gb = ctx.saved_tensors
+            return g * gx, g * ga, g * gy, g * gb, None, None, None, None, None
+
+    return SinkhornDivergence
+
+
+_SinkhornDivergence = None
+
+
+def sinkhorn_divergence(x, a, y, b, eps, r=2.0, max_iter=200, tol=0.0, params=None):
+    """Differentiable Sinkhorn divergence of (x, a) and (y, b): x is n x d, y is
+    m x d, a and b the weights, all CUDA float64 tensors.  Returns a 0-d tensor;
+    torch.autograd gives its gradient with respect to all four."""
+    global _SinkhornDivergence
+    if _SinkhornDivergence is None:
+        _SinkhornDivergence = _divergence_function()
+    return _SinkhornDivergence.apply(x, a, y, b, eps, r, max_iter, tol, params)

@@ -174,6 +174,26 @@ def test_divergence_gradient_matches_oracle():
     assert np.max(np.abs(gy.reshape(m, d) - ey)) <= 1e-5 * scale
 
 
+def test_divergence_autograd_matches_direct_gradients():
+    # torch.autograd over the divergence returns the gradients sk_divergence
+    # computes, scaled by the incoming gradient
+    n, m, d, eps, iters = 300, 250, 3, 0.05, 100
+    x = cuda(wl.gaussian_mixture(n, d, 4, 0.05, 0.1, 141)).requires_grad_()
+    y = cuda(wl.uniform_ball(m, d, 0.2, 142)).requires_grad_()
+    a = cuda(wl.dirichlet_weights(n, 143)).requires_grad_()
+    b = cuda(wl.dirichlet_weights(m, 144)).requires_grad_()
+    prm = sk.sk_default_params(precision=sk.SK_FP64)
+    sd = sk.sinkhorn_divergence(x, a, y, b, eps, 2.0, iters, params=prm)
+    (3.0 * sd).backward()
+    g = [torch.zeros(k, dtype=torch.float64, device="cuda") for k in (n, m, n * d, m * d)]
+    ref = sk.sk_divergence(x.detach(), a.detach(), y.detach(), b.detach(), eps, 2.0, iters, params=prm,
+                           grad_a=g[0], grad_b=g[1], grad_x=g[2], grad_y=g[3])
+    # two separate solves: spreading adds with atomics, so agreement to rounding
+    assert abs(float(sd.detach()) - ref[0]) <= 1e-12 * abs(ref[0])
+    for got, want in ((a.grad, g[0]), (b.grad, g[1]), (x.grad.reshape(-1), g[2]), (y.grad.reshape(-1), g[3])):
+        assert torch.allclose(got, 3.0 * want, rtol=0, atol=1e-10 * float(want.abs().max()))
+
+
 def test_divergence_gradient_finite_differences():
     # the differentiation check on Gaussian-mixture clouds in 3-D (r = 2,
     # eps = 0.02): central differences with step 1e-4 of the divergence,

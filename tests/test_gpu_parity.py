@@ -193,6 +193,34 @@ def test_3d_tensor_core_interpolation_matches_exact_sums_and_cuda_cores(m_w):
         assert np.max(np.abs(a - b)) <= TOL_FS[sk.SK_FP32] * np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("m_w", [2, 4, 6, 8])
+def test_2d_tensor_core_interpolation_matches_exact_sums_and_cuda_cores(m_w):
+    # the 2-D tcgen05 interpolation (default for 2-D FP32) against the exact
+    # sums and the strip kernels; a Gaussian-mixture source puts several
+    # hundred points into single strips (several runs per bin)
+    x = wl.gaussian_mixture(4000, 2, 4, 0.01, 0.1, 61)
+    y = wl.uniform_ball(3000, 2, 0.2, 62)
+    plan = plan_for(x, y, eps=0.01, N=128, m_w=m_w, precision=sk.SK_FP32, user_geometry=False)
+    v = wl.positive_vector(len(y), 63)
+    u = wl.positive_vector(len(x), 64)
+    out = {}
+    for kind in (sk.SK_KERNELS_TENSOR, sk.SK_KERNELS_SIMT):
+        sk.sk_set_kernels(plan, kind)
+        t = np.zeros(len(x))
+        tt = np.zeros(len(y))
+        sk.sk_kernel_apply(plan, 0, v, t)
+        sk.sk_kernel_apply(plan, 1, u, tt)
+        out[kind] = (t, tt)
+    tol = max(1e-5, 4 * kb_window_bound(m_w))
+    t_exact = osk.kernel_apply(x, y, v, 0.01, 2.0)
+    tt_exact = osk.kernel_apply_T(x, y, u, 0.01, 2.0)
+    for kind in out:
+        assert efs(out[kind][0], t_exact) <= tol
+        assert efs(out[kind][1], tt_exact) <= tol
+    for a, b in zip(out[sk.SK_KERNELS_TENSOR], out[sk.SK_KERNELS_SIMT]):
+        assert np.max(np.abs(a - b)) <= TOL_FS[sk.SK_FP32] * np.max(np.abs(b))
+
+
 def test_kernel_selection_errors():
     x = wl.uniform_ball(100, 3, 0.2, 40)
     plan64 = plan_for(x, x, precision=sk.SK_FP64, N=16)
@@ -200,13 +228,18 @@ def test_kernel_selection_errors():
         sk.sk_set_kernels(plan64, sk.SK_KERNELS_TENSOR)
     assert err.value.status == sk.SK_ERR_UNSUPPORTED
     sk.sk_set_kernels(plan64, sk.SK_KERNELS_SIMT)
-    plan2 = plan_for(wl.uniform_ball(100, 2, 0.2, 41), wl.uniform_ball(90, 2, 0.2, 42), precision=sk.SK_FP32)
+    plan1 = plan_for(wl.uniform_ball(100, 1, 0.2, 41), wl.uniform_ball(90, 1, 0.2, 42), precision=sk.SK_FP32)
     with pytest.raises(sk.SkError) as err:
-        sk.sk_set_kernels(plan2, sk.SK_KERNELS_TENSOR)
+        sk.sk_set_kernels(plan1, sk.SK_KERNELS_TENSOR)
     assert err.value.status == sk.SK_ERR_UNSUPPORTED
     with pytest.raises(sk.SkError) as err:
-        sk.sk_set_kernels(plan2, 7)
+        sk.sk_set_kernels(plan1, 7)
     assert err.value.status == sk.SK_ERR_ARG
+    assert sk.sk_plan_info(plan1)["tensor_cores"] == 0
+    plan2 = plan_for(wl.uniform_ball(100, 2, 0.2, 43), wl.uniform_ball(90, 2, 0.2, 44), precision=sk.SK_FP32)
+    assert sk.sk_plan_info(plan2)["tensor_cores"] == 1
+    sk.sk_set_kernels(plan2, sk.SK_KERNELS_SIMT)
+    assert sk.sk_plan_info(plan2)["tensor_cores"] == 0
 
 
 # --------------------------------------------------------- kernel products
