@@ -81,6 +81,25 @@ __global__ void k_near_tasks(const int* __restrict__ start, int ncells, int* __r
     if (start[c + 1] > start[c]) tasks[atomicAdd(ntasks, 1)] = c;
 }
 
+// FP32 plans take the hardware's approximate base-2 exponential and
+// reciprocal square root (PTX ex2.approx / rsqrt.approx, relative error about
+// 2^-22): a pair's term then carries an error of a few 1e-7 of K, below the
+// FP32 fast summation's own.  FP64 plans use the full-precision functions.
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float exp2_pair(float x) { return ex2_fast(x); }
+__device__ __forceinline__ double exp2_pair(double x) { return exp2(x); }
+__device__ __forceinline__ float rsqrt_pair(float x) { return rsqrt_fast(x); }
+__device__ __forceinline__ double rsqrt_pair(double x) { return rsqrt(x); }
+
 // Per-pair correction v (K(rho) - K_I(rho)) for |du|^2 = d2 < r2max (else 0).
 // Everything here is FP32 (or FP64 for FP64 plans); the parameters were
 // converted once per thread.  For r = 1 the distance is d2 * rsqrt(d2).
@@ -88,11 +107,11 @@ template <typename T, bool R1, int NP>
 __device__ __forceinline__ T pair_term(T d2, T w, T r2max, T inv_r2, T kc, T half_r, const T (&ki)[kMaxP]) {
     T rho_r;
     if (R1) {
-        rho_r = d2 > T(0) ? d2 * rsqrt(d2) : T(0);
+        rho_r = d2 > T(0) ? d2 * rsqrt_pair(d2) : T(0);
     } else {
         rho_r = pow(d2, half_r);
     }
-    const T kv = exp2(-kc * rho_r);
+    const T kv = exp2_pair(-kc * rho_r);
     const T s = d2 * inv_r2;
     T kin = ki[NP - 1];
 #pragma unroll
@@ -194,12 +213,19 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
 #pragma unroll 2
                     for (int j = copy; j < cnt; j += copies) {
                         const V sv = src[j];
+                        T d2[kNearPerThread];
+                        bool near = false;
 #pragma unroll
                         for (int q = 0; q < kNearPerThread; ++q) {
                             const T dx = xt[q][0] - sv.x, dy = xt[q][1] - sv.y, dz = xt[q][2] - sv.z;
-                            const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                            part[q] += pair_term<T, R1, NP>(d2, sv.w, r2max, inv_r2, kc, half_r, ki);
+                            d2[q] = fma(dx, dx, fma(dy, dy, dz * dz));
+                            near = near || d2[q] < r2max;
                         }
+                        // a source no lane of the warp is close to costs only its distances
+                        if (!__any_sync(__activemask(), near)) continue;
+#pragma unroll
+                        for (int q = 0; q < kNearPerThread; ++q)
+                            part[q] += pair_term<T, R1, NP>(d2[q], sv.w, r2max, inv_r2, kc, half_r, ki);
                     }
 #pragma unroll
                     for (int q = 0; q < kNearPerThread; ++q) acc[q] += double(part[q]);
