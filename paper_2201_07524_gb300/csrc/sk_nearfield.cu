@@ -119,6 +119,33 @@ __device__ __forceinline__ T pair_term(T d2, T w, T r2max, T inv_r2, T kc, T hal
     return d2 < r2max ? w * (kv - kin) : T(0);
 }
 
+// The same correction for a thread's two FP32 targets against one source,
+// in packed FP32x2 arithmetic (one instruction for both pairs, the
+// exponential and reciprocal square root per pair).
+template <bool R1, int NP>
+__device__ __forceinline__ float2 pair_terms2(float2 d2, float w, float r2max, float inv_r2, float kc, float half_r,
+                                              const float (&ki)[kMaxP]) {
+    float2 rho;
+    if (R1) {
+        rho.x = d2.x > 0.f ? rsqrt_fast(d2.x) : 0.f;
+        rho.y = d2.y > 0.f ? rsqrt_fast(d2.y) : 0.f;
+        rho = __fmul2_rn(rho, d2);
+    } else {
+        rho.x = powf(d2.x, half_r);
+        rho.y = powf(d2.y, half_r);
+    }
+    const float2 arg = __fmul2_rn(rho, make_float2(-kc, -kc));
+    const float2 kv = make_float2(ex2_fast(arg.x), ex2_fast(arg.y));
+    const float2 s = __fmul2_rn(d2, make_float2(inv_r2, inv_r2));
+    float2 kin = make_float2(ki[NP - 1], ki[NP - 1]);
+#pragma unroll
+    for (int k = NP - 2; k >= 0; --k) kin = __ffma2_rn(kin, s, make_float2(ki[k], ki[k]));
+    float2 t = __fmul2_rn(__ffma2_rn(kin, make_float2(-1.f, -1.f), kv), make_float2(w, w));
+    t.x = d2.x < r2max ? t.x : 0.f;
+    t.y = d2.y < r2max ? t.y : 0.f;
+    return t;
+}
+
 // NP: polynomial length of K_I (the plan's p; kMaxP covers every p with zero padding).
 // A pass over a cell's targets has 512 work items (kNearThreads threads x
 // kNearPerThread): `slots` target slots (the pass's targets rounded up to a
@@ -210,6 +237,25 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
                     T part[kNearPerThread];
 #pragma unroll
                     for (int q = 0; q < kNearPerThread; ++q) part[q] = T(0);
+                    if constexpr (std::is_same<T, float>::value && kNearPerThread == 2) {
+                        const float2 X0 = make_float2(xt[0][0], xt[1][0]);
+                        const float2 X1 = make_float2(xt[0][1], xt[1][1]);
+                        const float2 X2 = make_float2(xt[0][2], xt[1][2]);
+                        float2 part2 = make_float2(0.f, 0.f);
+#pragma unroll 2
+                        for (int j = copy; j < cnt; j += copies) {
+                            const V sv = src[j];
+                            const float2 dx = __fadd2_rn(X0, make_float2(-sv.x, -sv.x));
+                            const float2 dy = __fadd2_rn(X1, make_float2(-sv.y, -sv.y));
+                            const float2 dz = __fadd2_rn(X2, make_float2(-sv.z, -sv.z));
+                            const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                            const bool near = d2.x < r2max || d2.y < r2max;
+                            if (!__any_sync(__activemask(), near)) continue;
+                            part2 = __fadd2_rn(part2, pair_terms2<R1, NP>(d2, sv.w, r2max, inv_r2, kc, half_r, ki));
+                        }
+                        part[0] = part2.x;
+                        part[1] = part2.y;
+                    } else {
 #pragma unroll 2
                     for (int j = copy; j < cnt; j += copies) {
                         const V sv = src[j];
@@ -226,6 +272,7 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
 #pragma unroll
                         for (int q = 0; q < kNearPerThread; ++q)
                             part[q] += pair_term<T, R1, NP>(d2[q], sv.w, r2max, inv_r2, kc, half_r, ki);
+                    }
                     }
 #pragma unroll
                     for (int q = 0; q < kNearPerThread; ++q) acc[q] += double(part[q]);
