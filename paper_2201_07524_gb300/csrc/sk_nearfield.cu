@@ -237,24 +237,40 @@ __global__ void __launch_bounds__(kNearThreads) k_nearfield(NearArgs a) {
                     T part[kNearPerThread];
 #pragma unroll
                     for (int q = 0; q < kNearPerThread; ++q) part[q] = T(0);
-                    if constexpr (std::is_same<T, float>::value && kNearPerThread == 2) {
-                        const float2 X0 = make_float2(xt[0][0], xt[1][0]);
-                        const float2 X1 = make_float2(xt[0][1], xt[1][1]);
-                        const float2 X2 = make_float2(xt[0][2], xt[1][2]);
-                        float2 part2 = make_float2(0.f, 0.f);
+                    if constexpr (std::is_same<T, float>::value && kNearPerThread % 2 == 0) {
+                        constexpr int H = kNearPerThread / 2;
+                        float2 X0[H], X1[H], X2[H], part2[H];
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            X0[h] = make_float2(xt[2 * h][0], xt[2 * h + 1][0]);
+                            X1[h] = make_float2(xt[2 * h][1], xt[2 * h + 1][1]);
+                            X2[h] = make_float2(xt[2 * h][2], xt[2 * h + 1][2]);
+                            part2[h] = make_float2(0.f, 0.f);
+                        }
 #pragma unroll 2
                         for (int j = copy; j < cnt; j += copies) {
                             const V sv = src[j];
-                            const float2 dx = __fadd2_rn(X0, make_float2(-sv.x, -sv.x));
-                            const float2 dy = __fadd2_rn(X1, make_float2(-sv.y, -sv.y));
-                            const float2 dz = __fadd2_rn(X2, make_float2(-sv.z, -sv.z));
-                            const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-                            const bool near = d2.x < r2max || d2.y < r2max;
+                            float2 d2[H];
+                            bool near = false;
+#pragma unroll
+                            for (int h = 0; h < H; ++h) {
+                                const float2 dx = __fadd2_rn(X0[h], make_float2(-sv.x, -sv.x));
+                                const float2 dy = __fadd2_rn(X1[h], make_float2(-sv.y, -sv.y));
+                                const float2 dz = __fadd2_rn(X2[h], make_float2(-sv.z, -sv.z));
+                                d2[h] = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                                near = near || d2[h].x < r2max || d2[h].y < r2max;
+                            }
                             if (!__any_sync(__activemask(), near)) continue;
-                            part2 = __fadd2_rn(part2, pair_terms2<R1, NP>(d2, sv.w, r2max, inv_r2, kc, half_r, ki));
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                part2[h] = __fadd2_rn(part2[h],
+                                                      pair_terms2<R1, NP>(d2[h], sv.w, r2max, inv_r2, kc, half_r, ki));
                         }
-                        part[0] = part2.x;
-                        part[1] = part2.y;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            part[2 * h] = part2[h].x;
+                            part[2 * h + 1] = part2[h].y;
+                        }
                     } else {
 #pragma unroll 2
                     for (int j = copy; j < cnt; j += copies) {
