@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Sinkhorn iters/s at n=m=1e6,d=3 (NFFT vs direct on same GB300, ≤1e-5 rel err)"
+METRIC_OTHER = "Sinkhorn iters/s, workload %s (NFFT vs direct on same GB300)"
 UNIT = "iters/s"
 L2_FLUSH_BYTES = 512 * 1024 * 1024
 
@@ -98,14 +99,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle legs
-def _oracle_sample_job(n_rows, seed):
+def _oracle_sample_job(n_rows, seed, workload="headline"):
     """Runs in a spawned process with one thread: times the oracle's exact
     kernel products (Eq. (matexp)/(matexpt)) on n_rows sampled rows and columns
-    of the headline workload; returns seconds per full Sinkhorn iteration."""
+    of the workload; returns seconds per full Sinkhorn iteration."""
     import numpy as np
     from oracle import sinkhorn as osk
     from paper_2201_07524_gb300 import workloads as wl
-    w = wl.HEADLINE_3D
+    w = _workloads(wl)[workload]
     x, y = w.points()
     rng = np.random.default_rng(seed)
     rows = rng.choice(w.n, n_rows, replace=False)
@@ -124,7 +125,11 @@ def _oracle_sample_job(n_rows, seed):
     return dt * (w.n + w.m) / (2.0 * n_rows)
 
 
-def cpu_oracle_sample(n_rows, seed=0):
+def _workloads(wl):
+    return {"headline": wl.HEADLINE_3D, "gmm2d": wl.GMM_2D, "r1": wl.BALL3D_R1}
+
+
+def cpu_oracle_sample(n_rows, seed=0, workload="headline"):
     import multiprocessing as mp
     env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     old = {k: os.environ.get(k) for k in env_keys}
@@ -134,7 +139,7 @@ def cpu_oracle_sample(n_rows, seed=0):
         ctx = mp.get_context("spawn")
         with ctx.Pool(1) as pool:
             t0 = time.perf_counter()
-            sec_per_iter = pool.apply(_oracle_sample_job, (n_rows, seed))
+            sec_per_iter = pool.apply(_oracle_sample_job, (n_rows, seed, workload))
             wall = time.perf_counter() - t0
     finally:
         for k, v in old.items():
@@ -235,10 +240,10 @@ def whole_job_rate(ms_max, steps, world):
 
 
 def replica_workload(w, rank):
-    """Rank r solves its own problem: the same workload with seeds shifted by 1000 r."""
-    from paper_2201_07524_gb300 import workloads as wl
-    return wl.Workload(w.name, w.d, w.n, w.m, w.eps, w.r, w.iters, w.N, w.m_w, w.sigma, w.precision,
-                       seed_x=w.seed_x + 1000 * rank, seed_y=w.seed_y + 1000 * rank)
+    """Rank r solves its own problem: the same workload (every field kept)
+    with seeds shifted by 1000 r."""
+    import dataclasses
+    return dataclasses.replace(w, seed_x=w.seed_x + 1000 * rank, seed_y=w.seed_y + 1000 * rank)
 
 
 def fp32_alu_peak_tflops(pk):
@@ -258,11 +263,14 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     # each rank solves its own independent problem (replicas; seeds offset by rank)
-    w = replica_workload(wl.HEADLINE_3D, rank)
+    base = _workloads(wl)[args.workload]
+    w = replica_workload(base, rank)
     x, y = w.points()
     a, b = w.marginals()
     T = lambda z: torch.as_tensor(z, dtype=torch.float64, device=dev)
     prm = sk.sk_default_params(N=w.N, m_w=w.m_w, sigma=w.sigma, precision=sk.SK_FP32)
+    if "eps_I" in w.extra:
+        prm.eps_I = w.extra["eps_I"]
     plan = sk.sk_init(T(x), T(a), T(y), T(b), w.eps, w.r, prm)
     info = sk.sk_plan_info(plan)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -363,7 +371,7 @@ def run_ours(args, rank, world):
     alu_peak = fp32_alu_peak_tflops(pk)
     achieved = flops / dur_s / 1e12
     stage_report = {}
-    for k in ("spread", "fft", "interp", "other"):
+    for k in ("spread", "fft", "interp", "near", "other"):
         if stages[k][1]:
             ent = {"ms_per_launch": per_launch[k], "launches": stages[k][1],
                    "share": stages[k][0] / max(1e-12, sum(v[0] for v in stages.values()))}
@@ -382,20 +390,24 @@ def run_ours(args, rank, world):
         efs_sample = float(np.max(np.abs(got - exact)) / np.max(np.abs(exact)))
     cpu = None
     if rank == 0 and world == 1 and args.cpu_rows > 0:
-        sec, wall_cpu = cpu_oracle_sample(args.cpu_rows)
+        sec, wall_cpu = cpu_oracle_sample(args.cpu_rows, workload=args.workload)
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d sampled rows of K v and %d columns of K^T u (exact FP64 numpy sums over all "
-                         "1e6 points, one thread), scaled to one full iteration; %.1f s wall" %
-                         (args.cpu_rows, args.cpu_rows, wall_cpu)}
+                         "%.0e points, one thread), scaled to one full iteration; %.1f s wall" %
+                         (args.cpu_rows, args.cpu_rows, float(w.n), wall_cpu)}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if args.workload == "headline" else METRIC_OTHER % w.name, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "n": w.n, "m": w.m, "d": w.d, "r": w.r, "eps": w.eps, "N": w.N,
                        "sigma": w.sigma, "m_w": w.m_w, "fast_summation": "fp32", "updates": "fp64",
-                       "points": "uniform in radius-0.2 ball, seeds 1/2 (+1000*rank)",
+                       "points": ("source: 8-component Gaussian mixture (sigma 0.03, means uniform in a radius-0.15 "
+                                  "ball), target: uniform in a radius-0.2 ball" if w.source == "gmm"
+                                  else "uniform in radius-0.2 ball") + ", weights " + w.weights
+                                 + ", seeds %d/%d (+1000*rank)" % (base.seed_x, base.seed_y),
                        "l2": "flushed between timed steps (512 MB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
@@ -512,8 +524,9 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=200)
     ap.add_argument("--ref-rows", type=int, default=64)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch"],
-                    help="headline: the 1e6-point 3-D workload; batch: --batch independent problems")
+    ap.add_argument("--workload", default="headline", choices=["headline", "gmm2d", "r1", "batch"],
+                    help="headline: the 1e6-point 3-D workload; gmm2d: the 1e6-point 2-D Gaussian mixture; "
+                         "r1: the 4e6-point 3-D workload with r = 1 (near field); batch: --batch independent problems")
     ap.add_argument("--batch", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:

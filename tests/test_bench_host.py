@@ -58,3 +58,19 @@ def test_replica_problems_differ_by_rank():
     x0, _ = w0.points()
     x1, _ = w1.points()
     assert not (x0 == x1).all()
+
+
+@pytest.mark.parametrize("name", ["GMM_2D", "BALL3D_R1", "HEADLINE_3D"])
+def test_replica_keeps_every_workload_field(name):
+    # a replica differs from its workload only in the seeds: the point source,
+    # weights and extra parameters (the near-field radius) carry over
+    import dataclasses
+    import bench
+    from paper_2201_07524_gb300 import workloads as wl
+    w = getattr(wl, name)
+    r = bench.replica_workload(w, 3)
+    for f in dataclasses.fields(w):
+        if f.name in ("seed_x", "seed_y"):
+            assert getattr(r, f.name) == getattr(w, f.name) + 3000
+        else:
+            assert getattr(r, f.name) == getattr(w, f.name), f.name
