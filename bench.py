@@ -197,11 +197,16 @@ def algorithmic_counts(w, n_os):
 
 
 def kernel_name(stage, w, tensor_cores):
-    if w.d != 3:
-        return None
-    if stage == "interp" and tensor_cores:
-        return "k_interp3_tc<%d>" % (2 * w.m_w)
-    return "k_%s3_col<%d, float>" % (stage, 2 * w.m_w)
+    W = 2 * w.m_w
+    if w.d == 3:
+        if stage == "interp" and tensor_cores:
+            return "k_interp3_tc<%d>" % W
+        return "k_%s3_col<%d, float>" % (stage, W)
+    if w.d == 2:
+        if stage == "interp" and tensor_cores:
+            return "k_interp2_tc<%d>" % W
+        return "k_%s2_strip<%d, float>" % (stage, W)
+    return None
 
 
 def measured_traffic(kname):
