@@ -347,12 +347,11 @@ struct Tc2 {
     static constexpr int LBO = 128, SBO = KC * 128;
     static constexpr int A_BYTES = 16 * SBO;
     static constexpr int B_BYTES = (N / 8) * SBO;
-    static constexpr int HS = 36;                // floats per thread's H row (16-byte rows, staggered banks)
-    static constexpr int H_BYTES = 128 * HS * 4;
-    static constexpr int OPERANDS = 2 * A_BYTES + 2 * B_BYTES + H_BYTES;
+    static constexpr int OPERANDS = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int COLS = 32;
     static constexpr int BLOCKS_PER_SM = 8;
     static_assert(M_W >= 2 && M_W <= 8, "window widths 4..16");
+    static_assert(2 * KC >= N / 4, "a thread's operand row holds its N results");
 };
 
 template <int W>
@@ -364,7 +363,6 @@ __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
     unsigned char* a_lo = a_hi + S::A_BYTES;
     unsigned char* b_hi = a_lo + S::A_BYTES;
     unsigned char* b_lo = b_hi + S::B_BYTES;
-    float* hrow = reinterpret_cast<float*>(b_lo + S::B_BYTES) + threadIdx.x * S::HS;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int task, abort_flag;
@@ -477,16 +475,24 @@ __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
                 if (e.status) atomicOr(e.status, 4);
             }
             tc_fence_after();
+            // the MMA has read the A operand, so the thread's own row of it (6
+            // chunks of 4 in the hi part, 6 in the lo part) holds its 32 results:
+            // element e in chunk e / 4, chunks 6 and 7 in the lo part
             {
                 float h[32];
                 tmem_ld32(tlane, h);
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
-                    *reinterpret_cast<float4*>(hrow + 4 * c) = make_float4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                    *reinterpret_cast<float4*>((c < S::KC ? row_hi + c * S::LBO : row_lo + (c - S::KC) * S::LBO)) =
+                        make_float4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
             }
             float tv = 0.f;
 #pragma unroll
-            for (int q = 0; q < W; ++q) tv = fmaf(wx[q], hrow[dx + q], tv);
+            for (int q = 0; q < W; ++q) {
+                const int el = dx + q, c = el >> 2;
+                const unsigned char* at = c < S::KC ? row_hi + c * S::LBO : row_lo + (c - S::KC) * S::LBO;
+                tv = fmaf(wx[q], *reinterpret_cast<const float*>(at + (el & 3) * 4), tv);
+            }
             if (ok && !failed) epi_point_pre(e, p, double(tv), ep.q, ep.a, sq, bad, dot);
             tc_fence_before();
         }
