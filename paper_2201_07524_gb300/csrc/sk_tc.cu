@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
 // H = Wy Gᵀ is one 128 x 32 x 24 product per tile (N = 32 box rows, 32
 // tensor-memory columns).  The point's x-offset in the strip spans 33 - W
 // values, too many for register selects, so each thread parks its 32 H
-// values in its own shared-memory row and reads back the W of its window.
+// values in its own row of the A operand (free once the MMA has completed)
+// and reads back the W of its window.
 template <int W>
 struct Tc2 {
     static constexpr int M_W = W / 2;
