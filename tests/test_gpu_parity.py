@@ -242,6 +242,29 @@ def test_kernel_selection_errors():
     assert sk.sk_plan_info(plan2)["tensor_cores"] == 0
 
 
+@pytest.mark.parametrize("kind", ["tensor", "simt"])
+@pytest.mark.parametrize("d,N", [(2, 32), (3, 16)])
+def test_nfft_points_at_the_edges_of_the_valid_region(d, N, kind):
+    # points filling the whole region whose windows stay on the grid
+    # (cells m-1 .. n_os-1-m along every axis), so the bins' boxes reach the
+    # grid's first and last cells: interpolation against the NDFT
+    h, n_os, m = N // 2, 2 * N, 4
+    lo, hi = (m - 1 + 0.01) / n_os, (n_os - m - 0.01) / n_os
+    rng = np.random.default_rng(71 + d)
+    x = rng.uniform(lo, hi, (300, d)) - 0.5
+    y = rng.uniform(lo, hi, (700, d)) - 0.5
+    y[:d] = np.diag(np.full(d, lo - 0.5)) + (hi - 0.5) * (1 - np.eye(d))   # corners of the region
+    plan = plan_for(x, y, N=N, precision=sk.SK_FP32)
+    sk.sk_set_kernels(plan, sk.SK_KERNELS_TENSOR if kind == "tensor" else sk.SK_KERNELS_SIMT)
+    A = rng.standard_normal((2 * h + 1,) * d) + 1j * rng.standard_normal((2 * h + 1,) * d)
+    F = 0.5 * (A + np.conj(A[tuple([slice(None, None, -1)] * d)]))
+    buf = np.stack([F.real, F.imag], axis=-1).reshape(-1).copy()
+    got = np.zeros(len(y))
+    sk.sk_nfft(plan, sk.SK_SET_Y, buf, got)
+    want = ofs.ndft(y + 0.5, _common(F, h, d), N).real
+    assert np.max(np.abs(got - want)) / np.sum(np.abs(F)) <= TOL_FS[sk.SK_FP32]
+
+
 # --------------------------------------------------------- kernel products
 @pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
 @pytest.mark.parametrize("d,n,m,N,eps", [(1, 1000, 777, 64, 0.05), (2, 2000, 1337, 64, 0.05),
