@@ -54,6 +54,7 @@ enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / in
 enum { SK_METHOD_NFFT = 0, SK_METHOD_DIRECT = 1 };
 enum { SK_DOMAIN_SCALING = 0, SK_DOMAIN_LOG = 1 };   /* state of the iteration: Alg. 3 or Alg. 4 */
 enum { SK_KERNELS_SIMT = 0, SK_KERNELS_TENSOR = 1 };   /* interpolation on CUDA cores or tensor cores */
+enum { SK_FAULT_NONE = 0, SK_FAULT_TC_WAIT = 1 };      /* sk_inject_fault (test hook) */
 enum { SK_SET_X = 0, SK_SET_Y = 1 };        /* which point cloud a stage entry point acts on */
 
 typedef struct sk_plan sk_plan;
@@ -192,6 +193,20 @@ int sk_set_domain(sk_plan* plan, int domain);
  * return SK_ERR_TIMEOUT when they read results back.
  */
 int sk_set_kernels(sk_plan* plan, int kernels);
+
+/*
+ * Test hook for the failure path of the tensor-core kernels.  With
+ * SK_FAULT_TC_WAIT the plan's tensor-core interpolation skips its MMA group,
+ * so the bounded wait for the group's completion (about a second) runs out:
+ * the kernel sets its status bit, stops, releases its tensor memory and
+ * returns, the GPU context stays usable, and sk_solve / sk_solve_batch return
+ * SK_ERR_TIMEOUT when they read results back (the state of that solve is not
+ * meaningful).  SK_FAULT_NONE restores normal operation.  Nothing faults or
+ * hangs either way.
+ * Errors: SK_ERR_ARG for a NULL plan or an unknown kind; SK_ERR_UNSUPPORTED
+ * for SK_FAULT_TC_WAIT when the plan does not interpolate on tensor cores.
+ */
+int sk_inject_fault(sk_plan* plan, int kind);
 
 /*
  * One kernel-vector product (Eqs. (matexp), (matexpt)):

@@ -23,6 +23,7 @@ struct sk_plan {
     int near_sub = 2;           // near-field cells per eps_I (2, or 4 for dense clouds)
     bool tc_ok = false;         // the tensor-core (tcgen05) interpolation supports this plan
     bool tc = false;            // ... and is selected
+    int inject = 0;             // SK_FAULT_* test hook (sk_inject_fault)
     double* shift = nullptr;    // log domain: max of the Y ([0]) and X ([1]) dual variables
     int N = 0, h = 0, n_os = 0, log2n = 0, W = 0, B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 0, bvol = 1;
     int64_t nkeys = 0;
@@ -814,6 +815,7 @@ void interp_from_grid(sk_plan* P, Cloud& dst, const Epilogue& e) {
     a.nstasks = dst.nstasks;
     a.ttasks = dst.ttasks;
     a.nttasks = dst.nttasks;
+    a.inject = P->inject == SK_FAULT_TC_WAIT ? 1 : 0;
     a.queue = P->ticket + 2;
     a.grid = P->fft.grid_out;
     a.wp = P->wp;
@@ -1461,6 +1463,16 @@ int sk_set_kernels(sk_plan* P, int kernels) {
     if (tc != P->tc) {
         destroy_graph(P);
         P->tc = tc;
+    }
+    return SK_OK;
+}
+
+int sk_inject_fault(sk_plan* P, int kind) {
+    if (!P || (kind != SK_FAULT_NONE && kind != SK_FAULT_TC_WAIT)) return SK_ERR_ARG;
+    if (kind == SK_FAULT_TC_WAIT && !P->tc) return SK_ERR_UNSUPPORTED;
+    if (kind != P->inject) {
+        destroy_graph(P);
+        P->inject = kind;
     }
     return SK_OK;
 }

@@ -165,6 +165,7 @@ struct InterpArgs {
     int nstasks;
     const int* ttasks;     // tensor-core runs: (bin, first point, end point), most points first
     int nttasks;
+    int inject;            // test hook: 1 = the tensor-core kernels skip their MMA, so its bounded wait runs out
     unsigned* queue;       // [0] next queue entry, [1] warps finished; zero between launches
     int nb[3];
     int n_os;

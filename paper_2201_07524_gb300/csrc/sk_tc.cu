@@ -93,10 +93,18 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 
 // Wait for the completion of the barrier's phase with parity `phase`, giving
-// up after a bounded number of tries.
-constexpr int kTcWaitTries = 1 << 20;
+// up after about a second (the global timer) or 2^24 tries, whichever comes
+// first; an MMA group completes in microseconds.
+constexpr unsigned long long kTcWaitNs = 1000000000ull;
+constexpr int kTcWaitTries = 1 << 24;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
     const uint32_t addr = smem_addr(bar);
+    unsigned long long t0 = 0;
     for (int it = 0; it < kTcWaitTries; ++it) {
         uint32_t done;
         asm volatile(
@@ -105,6 +113,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
             : "r"(addr), "r"(phase)
             : "memory");
         if (done) return true;
+        if ((it & 255) == 0) {
+            const unsigned long long now = global_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > kTcWaitNs) return false;
+        }
     }
     return false;
 }
@@ -261,7 +274,7 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
             tc_fence_before();
             __syncthreads();
             if (abort_flag) break;
-            if (tid == 0) {
+            if (tid == 0 && !a.inject) {
                 tc_fence_after();
                 const uint32_t ah = smem_addr(a_hi), al = smem_addr(a_lo), bh = smem_addr(b_hi), bl = smem_addr(b_lo);
 #pragma unroll
@@ -456,7 +469,7 @@ __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
             tc_fence_before();
             __syncthreads();
             if (abort_flag) break;
-            if (tid == 0) {
+            if (tid == 0 && !a.inject) {
                 tc_fence_after();
                 const uint32_t ah = smem_addr(a_hi), al = smem_addr(a_lo), bh = smem_addr(b_hi), bl = smem_addr(b_lo);
 #pragma unroll

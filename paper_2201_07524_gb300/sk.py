@@ -26,6 +26,7 @@ SK_FP32, SK_FP64 = 0, 1
 SK_METHOD_NFFT, SK_METHOD_DIRECT = 0, 1
 SK_DOMAIN_SCALING, SK_DOMAIN_LOG = 0, 1
 SK_KERNELS_SIMT, SK_KERNELS_TENSOR = 0, 1
+SK_FAULT_NONE, SK_FAULT_TC_WAIT = 0, 1
 SK_SET_X, SK_SET_Y = 0, 1
 SK_STAGE_SPREAD, SK_STAGE_FFT, SK_STAGE_INTERP, SK_STAGE_OTHER, SK_STAGE_DIRECT, SK_STAGE_NEAR = 0, 1, 2, 3, 4, 5
 SK_NSTAGES = 6
@@ -66,6 +67,7 @@ _SIGS = {
     "sk_set_method": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_set_domain": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_set_kernels": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sk_inject_fault": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
     "sk_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D,
                                 ctypes.POINTER(sk_result), _S]),
@@ -208,6 +210,10 @@ def sk_set_domain(plan, domain):
 
 def sk_set_kernels(plan, kernels):
     _check(_lib.sk_set_kernels(plan.handle, int(kernels)), "sk_set_kernels")
+
+
+def sk_inject_fault(plan, kind):
+    _check(_lib.sk_inject_fault(plan.handle, int(kind)), "sk_inject_fault")
 
 
 def sk_kernel_apply(plan, transpose, vin, out, stream=None):

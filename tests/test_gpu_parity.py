@@ -221,6 +221,30 @@ def test_2d_tensor_core_interpolation_matches_exact_sums_and_cuda_cores(m_w):
         assert np.max(np.abs(a - b)) <= TOL_FS[sk.SK_FP32] * np.max(np.abs(b))
 
 
+def test_tensor_core_wait_gives_up_and_the_plan_recovers():
+    # the failure path of the tensor-core kernels, made on purpose without a
+    # fault: the MMA group is skipped, the bounded wait (about a second) runs
+    # out, the solve reports SK_ERR_TIMEOUT; afterwards the same plan solves
+    # normally
+    x = wl.uniform_ball(1200, 3, 0.2, 81)
+    y = wl.uniform_ball(900, 3, 0.2, 82)
+    a, b = wl.uniform_weights(1200), wl.uniform_weights(900)
+    plan = plan_for(x, y, a, b, eps=0.02, precision=sk.SK_FP32, user_geometry=False)
+    sk.sk_inject_fault(plan, sk.SK_FAULT_TC_WAIT)
+    st, _ = sk.sk_solve(plan, 1, raise_on_error=False)
+    assert st == sk.SK_ERR_TIMEOUT
+    sk.sk_inject_fault(plan, sk.SK_FAULT_NONE)
+    sk.sk_set_state(plan)                       # u = v = 1 again
+    st, res = sk.sk_solve(plan, 30)
+    assert st == sk.SK_OK
+    ref = osk.sinkhorn_dense(x, a, y, b, 0.02, 2.0, 30)
+    assert abs(res["s"] - ref["s"]) <= 1e-5 * abs(ref["s"])
+    plan64 = plan_for(x, y, a, b, eps=0.02, precision=sk.SK_FP64)
+    with pytest.raises(sk.SkError) as err:
+        sk.sk_inject_fault(plan64, sk.SK_FAULT_TC_WAIT)
+    assert err.value.status == sk.SK_ERR_UNSUPPORTED
+
+
 def test_kernel_selection_errors():
     x = wl.uniform_ball(100, 3, 0.2, 40)
     plan64 = plan_for(x, x, precision=sk.SK_FP64, N=16)
