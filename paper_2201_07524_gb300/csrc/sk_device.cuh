@@ -22,9 +22,37 @@ template <> __device__ __forceinline__ double poly_coef<double>(const WindowPoly
 }
 
 // The W window weights of one coordinate (taps starting at cell f - (m-1)),
-// by Horner's rule on the piecewise polynomial; `scale` multiplies them.
+// by Horner's rule on the piecewise polynomial; `scale` multiplies them.  The
+// window is even, so tap W-1-k is tap k's polynomial at -s: with
+// P_k(s) = E_k(s^2) + s O_k(s^2), w[k] = E + s O and w[W-1-k] = E - s O, one
+// pair of taps for the cost of one polynomial.
 template <int W, typename T>
 __device__ __forceinline__ void window_poly(T u, const WindowPoly& wp, T scale, int& f, T* w) {
+    constexpr int DEG = PolyDeg<T>::D;
+    constexpr int DE = DEG / 2;          // even coefficients c0, c2, ..., c(2 DE)
+    constexpr int DO = (DEG - 1) / 2;    // odd coefficients c1, c3, ..., c(2 DO + 1)
+    const T fl = floor(u);
+    f = int(fl);
+    const T s = T(2) * (u - fl) - T(1);
+    const T s2 = s * s;
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+        T e = poly_coef<T>(wp, k, 2 * DE);
+#pragma unroll
+        for (int j = DE - 1; j >= 0; --j) e = fma(e, s2, poly_coef<T>(wp, k, 2 * j));
+        T o = poly_coef<T>(wp, k, 2 * DO + 1);
+#pragma unroll
+        for (int j = DO - 1; j >= 0; --j) o = fma(o, s2, poly_coef<T>(wp, k, 2 * j + 1));
+        const T so = s * o;
+        w[k] = (e + so) * scale;
+        w[W - 1 - k] = (e - so) * scale;
+    }
+}
+
+// The same weights with one Horner polynomial per tap: more arithmetic than
+// window_poly, fewer values live at once (for kernels near a register limit).
+template <int W, typename T>
+__device__ __forceinline__ void window_poly_per_tap(T u, const WindowPoly& wp, T scale, int& f, T* w) {
     constexpr int DEG = PolyDeg<T>::D;
     const T fl = floor(u);
     f = int(fl);

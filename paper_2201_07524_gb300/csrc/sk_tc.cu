@@ -246,9 +246,11 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
             ep.load(e, p, ok);
             if (ok) {
                 int fx, fy, fz;
-                window_poly<W, float>(c0[p], a.wp, 1.f, fx, wx);
-                window_poly<W, float>(c1[p], a.wp, 1.f, fy, wy);
-                window_poly<W, float>(c2[p], a.wp, 1.f, fz, wz);
+                // per-tap polynomials: the paired evaluation raises this kernel
+                // past the registers of 4 blocks per SM
+                window_poly_per_tap<W, float>(c0[p], a.wp, 1.f, fx, wx);
+                window_poly_per_tap<W, float>(c1[p], a.wp, 1.f, fy, wy);
+                window_poly_per_tap<W, float>(c2[p], a.wp, 1.f, fz, wz);
                 dx = min(max(fx - x0, 0), 3);
                 dy = min(max(fy - y0, 0), 3);
                 k0 = min(max(fz - z0 + S::ZLEAD - (m - 1), 0), S::KZ - W);
