@@ -240,23 +240,20 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
         for (int base = start; base < end; base += 128) {
             const int p = base + tid;
             const bool ok = p < end;
-            float wx[W], wy[W], wz[W];
-            int dx = 0, dy = 0, k0 = 0;
+            // only the z-weights feed the MMA; the x- and y-weights are evaluated
+            // while it runs
+            float wz[W];
+            int k0 = 0;
             EpiPrefetch ep;
             ep.load(e, p, ok);
+            const float ux = ok ? c0[p] : 0.f, uy = ok ? c1[p] : 0.f;
             if (ok) {
-                int fx, fy, fz;
-                // per-tap polynomials: the paired evaluation raises this kernel
-                // past the registers of 4 blocks per SM
-                window_poly_per_tap<W, float>(c0[p], a.wp, 1.f, fx, wx);
-                window_poly_per_tap<W, float>(c1[p], a.wp, 1.f, fy, wy);
-                window_poly_per_tap<W, float>(c2[p], a.wp, 1.f, fz, wz);
-                dx = min(max(fx - x0, 0), 3);
-                dy = min(max(fy - y0, 0), 3);
+                int fz;
+                window_poly<W, float>(c2[p], a.wp, 1.f, fz, wz);
                 k0 = min(max(fz - z0 + S::ZLEAD - (m - 1), 0), S::KZ - W);
             } else {
 #pragma unroll
-                for (int k = 0; k < W; ++k) wx[k] = wy[k] = wz[k] = 0.f;
+                for (int k = 0; k < W; ++k) wz[k] = 0.f;
             }
             // the point's operand row: zero, then its W z-weights from entry k0
 #pragma unroll
@@ -287,6 +284,18 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
                     tc_mma_tf32(tmem, tc_desc(al + o, S::LBO, S::SBO), tc_desc(bh + o, S::LBO, S::SBO), idesc, 1u);
                 }
                 tc_commit(&bar);
+            }
+            float wx[W], wy[W];
+            int dx = 0, dy = 0;
+            if (ok) {
+                int fx, fy;
+                window_poly<W, float>(ux, a.wp, 1.f, fx, wx);
+                window_poly<W, float>(uy, a.wp, 1.f, fy, wy);
+                dx = min(max(fx - x0, 0), 3);
+                dy = min(max(fy - y0, 0), 3);
+            } else {
+#pragma unroll
+                for (int k = 0; k < W; ++k) wx[k] = wy[k] = 0.f;
             }
             // padded weights over the box rows (zero outside the point's window)
             float wxf[S::X], wyf[S::Y];
