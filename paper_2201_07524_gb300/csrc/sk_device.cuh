@@ -49,23 +49,6 @@ __device__ __forceinline__ void window_poly(T u, const WindowPoly& wp, T scale, 
     }
 }
 
-// The same weights with one Horner polynomial per tap: more arithmetic than
-// window_poly, fewer values live at once (for kernels near a register limit).
-template <int W, typename T>
-__device__ __forceinline__ void window_poly_per_tap(T u, const WindowPoly& wp, T scale, int& f, T* w) {
-    constexpr int DEG = PolyDeg<T>::D;
-    const T fl = floor(u);
-    f = int(fl);
-    const T s = T(2) * (u - fl) - T(1);
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-        T acc = poly_coef<T>(wp, k, DEG);
-#pragma unroll
-        for (int i = DEG - 1; i >= 0; --i) acc = fma(acc, s, poly_coef<T>(wp, k, i));
-        w[k] = acc * scale;
-    }
-}
-
 // Next entry of a persistent launch's task queue for this warp (lane 0 takes
 // it; every lane gets it).
 __device__ __forceinline__ int queue_take(unsigned* q, int lane) {

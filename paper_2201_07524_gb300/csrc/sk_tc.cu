@@ -1,5 +1,6 @@
-// Tensor-core (tcgen05) interpolation for 3-D FP32 plans: the NFFT step of
-// Eq. (fastsum) that evaluates the grid at the target points.
+// Tensor-core (tcgen05) interpolation for FP32 plans, 3-D and (further down)
+// 2-D: the NFFT step of Eq. (fastsum) that evaluates the grid at the target
+// points.
 //
 // Points are sorted by bin (4 x 4 x 8 cells).  Every window of a point of a
 // bin lies in the bin's box of X x Y x Z grid cells (X = Y = 3 + W,
