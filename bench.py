@@ -478,6 +478,10 @@ def run_batch(args):
         grids.append((info["N"], info["m_w"]))
     torch.cuda.synchronize(dev)
     build_s = time.perf_counter() - t0
+    # the autotuner keeps, per problem, the faster interpolation kernel kind
+    t0 = time.perf_counter()
+    chosen = [sk.sk_autotune(p) for p in plans] if args.autotune else []
+    tune_s = time.perf_counter() - t0
 
     def timed(fn):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -514,6 +518,8 @@ def run_batch(args):
                        "speedup_batch": per_iter_seq / per_iter_batch},
         "capture_ms": b1 - k1 * per_iter_batch,
         "plan_build_s": build_s,
+        "autotune": ({"s": tune_s, "tensor_cores": sum(1 for c in chosen if c == sk.SK_KERNELS_TENSOR),
+                      "cuda_cores": sum(1 for c in chosen if c == sk.SK_KERNELS_SIMT)} if args.autotune else None),
         "all_finite": bool(all(np.isfinite(r["s"]) for r in res)),
     }
     print(json.dumps(line), flush=True)
@@ -533,6 +539,8 @@ def main():
                     help="headline: the 1e6-point 3-D workload; gmm2d: the 1e6-point 2-D Gaussian mixture; "
                          "r1: the 4e6-point 3-D workload with r = 1 (near field); batch: --batch independent problems")
     ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch: let sk_autotune pick each plan's interpolation kernels (measured no faster)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -195,6 +195,18 @@ int sk_set_domain(sk_plan* plan, int domain);
 int sk_set_kernels(sk_plan* plan, int kernels);
 
 /*
+ * Autotuner for the interpolation kernels: times one product K v (three
+ * repetitions after a warm-up, CUDA events on the plan's stream, the current
+ * v as weights, output into plan scratch) with each kernel kind the plan
+ * supports and keeps the faster, as sk_set_kernels would.  The plan's state
+ * (u, v, iteration count) is unchanged.  chosen (host, optional) receives the
+ * SK_KERNELS_* value kept.  Plans with one kind only, or in SK_METHOD_DIRECT,
+ * keep their current choice.  Synchronizes the stream.
+ * Errors: SK_ERR_ARG for a NULL plan; SK_ERR_CUDA.
+ */
+int sk_autotune(sk_plan* plan, int* chosen, void* stream);
+
+/*
  * Test hook for the failure path of the tensor-core kernels.  With
  * SK_FAULT_TC_WAIT the plan's tensor-core interpolation skips its MMA group,
  * so the bounded wait for the group's completion (about a second) runs out:

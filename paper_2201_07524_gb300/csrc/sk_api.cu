@@ -879,6 +879,27 @@ void product(sk_plan* P, Cloud& src, const double* w, Cloud& dst, const Epilogue
     interp_from_grid<T>(P, dst, ee);
 }
 
+// Average time (ms) of `reps` products K v of the plan with its current
+// interpolation kernels: weights = the current v, output into scratch.
+template <typename T>
+double time_products(sk_plan* P, int reps) {
+    Epilogue e = make_epilogue(P, EPI_APPLY, P->X, 0, P->X.stage);
+    product<T>(P, P->Y, P->Y.scal, P->X, e);   // warm-up
+    cudaEvent_t t0, t1;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    CK(cudaEventRecord(t0, P->ps));
+    for (int r = 0; r < reps; ++r) product<T>(P, P->Y, P->Y.scal, P->X, e);
+    CK(cudaEventRecord(t1, P->ps));
+    CK(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, t0, t1));
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return double(ms) / reps;
+}
+
+
 template <typename T>
 void iteration(sk_plan* P) {
     // odd half-step: u = a ./ (K v)  (log domain: beta = eps (log a - log t + 1/2))
@@ -1463,6 +1484,32 @@ int sk_set_kernels(sk_plan* P, int kernels) {
     if (tc != P->tc) {
         destroy_graph(P);
         P->tc = tc;
+    }
+    return SK_OK;
+}
+
+int sk_autotune(sk_plan* P, int* chosen, void* stream) {
+    if (!P) return SK_ERR_ARG;
+    try {
+        enter(P, stream);
+        int best = P->tc ? SK_KERNELS_TENSOR : SK_KERNELS_SIMT;
+        if (P->tc_ok && P->method == SK_METHOD_NFFT) {
+            const bool was = P->tc;
+            const int64_t launches = P->launches;
+            double ms[2] = {0.0, 0.0};
+            for (int k = 0; k < 2; ++k) {
+                P->tc = k == SK_KERNELS_TENSOR;
+                ms[k] = P->precision == SK_FP32 ? time_products<float>(P, 3) : time_products<double>(P, 3);
+            }
+            P->launches = launches;   // tuning launches are not the caller's work
+            best = ms[SK_KERNELS_TENSOR] <= ms[SK_KERNELS_SIMT] ? SK_KERNELS_TENSOR : SK_KERNELS_SIMT;
+            P->tc = best == SK_KERNELS_TENSOR;
+            if (P->tc != was) destroy_graph(P);
+        }
+        if (chosen) *chosen = best;
+        leave(P, stream);
+    } catch (const Fail& f) {
+        return fail_code(f);
     }
     return SK_OK;
 }

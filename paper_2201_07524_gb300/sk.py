@@ -68,6 +68,7 @@ _SIGS = {
     "sk_set_domain": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_set_kernels": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_inject_fault": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sk_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _S]),
     "sk_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
     "sk_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D,
                                 ctypes.POINTER(sk_result), _S]),
@@ -210,6 +211,13 @@ def sk_set_domain(plan, domain):
 
 def sk_set_kernels(plan, kernels):
     _check(_lib.sk_set_kernels(plan.handle, int(kernels)), "sk_set_kernels")
+
+
+def sk_autotune(plan, stream=None):
+    """Keeps the faster interpolation kernel kind for the plan; returns it."""
+    chosen = ctypes.c_int(0)
+    _check(_lib.sk_autotune(plan.handle, ctypes.byref(chosen), _stream(stream)), "sk_autotune")
+    return chosen.value
 
 
 def sk_inject_fault(plan, kind):

@@ -88,5 +88,6 @@ def test_null_plan_calls_are_rejected():
     assert L.sk_plan_info(None, None) == sk.SK_ERR_ARG
     assert L.sk_set_kernels(None, 0) == sk.SK_ERR_ARG
     assert L.sk_inject_fault(None, 0) == sk.SK_ERR_ARG
+    assert L.sk_autotune(None, None, None) == sk.SK_ERR_ARG
     assert L.sk_launch_count(None) == -1
     L.sk_destroy(None)

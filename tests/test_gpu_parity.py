@@ -245,6 +245,23 @@ def test_tensor_core_wait_gives_up_and_the_plan_recovers():
     assert err.value.status == sk.SK_ERR_UNSUPPORTED
 
 
+def test_autotune_keeps_a_valid_kind_and_the_state():
+    x = wl.uniform_ball(3000, 3, 0.2, 91)
+    y = wl.uniform_ball(2500, 3, 0.2, 92)
+    plan = plan_for(x, y, eps=0.02, precision=sk.SK_FP32, user_geometry=False)
+    sk.sk_solve(plan, 5, result=False)
+    u0, v0 = np.zeros(3000), np.zeros(2500)
+    it0 = sk.sk_get_state(plan, u0, v0)
+    chosen = sk.sk_autotune(plan)
+    assert chosen in (sk.SK_KERNELS_TENSOR, sk.SK_KERNELS_SIMT)
+    assert sk.sk_plan_info(plan)["tensor_cores"] == (1 if chosen == sk.SK_KERNELS_TENSOR else 0)
+    u1, v1 = np.zeros(3000), np.zeros(2500)
+    assert sk.sk_get_state(plan, u1, v1) == it0
+    assert np.array_equal(u0, u1) and np.array_equal(v0, v1)
+    plan64 = plan_for(x, y, eps=0.02, precision=sk.SK_FP64)
+    assert sk.sk_autotune(plan64) == sk.SK_KERNELS_SIMT
+
+
 def test_kernel_selection_errors():
     x = wl.uniform_ball(100, 3, 0.2, 40)
     plan64 = plan_for(x, x, precision=sk.SK_FP64, N=16)
