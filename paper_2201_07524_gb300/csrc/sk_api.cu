@@ -885,17 +885,21 @@ template <typename T>
 double time_products(sk_plan* P, int reps) {
     Epilogue e = make_epilogue(P, EPI_APPLY, P->X, 0, P->X.stage);
     product<T>(P, P->Y, P->Y.scal, P->X, e);   // warm-up
-    cudaEvent_t t0, t1;
-    CK(cudaEventCreate(&t0));
-    CK(cudaEventCreate(&t1));
-    CK(cudaEventRecord(t0, P->ps));
+    struct Events {   // released on every exit, including a failed CUDA call
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t v : ev)
+                if (v) cudaEventDestroy(v);
+        }
+    } t;
+    CK(cudaEventCreate(&t.ev[0]));
+    CK(cudaEventCreate(&t.ev[1]));
+    CK(cudaEventRecord(t.ev[0], P->ps));
     for (int r = 0; r < reps; ++r) product<T>(P, P->Y, P->Y.scal, P->X, e);
-    CK(cudaEventRecord(t1, P->ps));
-    CK(cudaEventSynchronize(t1));
+    CK(cudaEventRecord(t.ev[1], P->ps));
+    CK(cudaEventSynchronize(t.ev[1]));
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, t0, t1));
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
+    CK(cudaEventElapsedTime(&ms, t.ev[0], t.ev[1]));
     return double(ms) / reps;
 }
 
