@@ -121,7 +121,7 @@ typedef struct {
     int N, n_os, m_w, p, precision, nearfield;
     double eps, r, eps_scaled;   /* eps_scaled = eps * scale^r: the kernel in torus coordinates */
     double center[3], scale, eps_B, eps_I;
-    int n_subproblems_x, n_subproblems_y;
+    int n_subproblems_x, n_subproblems_y;   /* work items of the per-point spreading kernels (1-D; 3-D with m_w > 5) */
     int64_t device_bytes;        /* device memory the plan holds */
     int tensor_cores;            /* 1: interpolation runs on tensor cores (sk_set_kernels) */
 } sk_info;
