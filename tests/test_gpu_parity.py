@@ -161,6 +161,34 @@ def test_2d_nfft_stages_every_window_width(m_w, precision):
     assert err <= tol, (err, tol)
 
 
+@pytest.mark.parametrize("precision", [sk.SK_FP64, sk.SK_FP32])
+@pytest.mark.parametrize("m_w", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("d,N", [(1, 64), (3, 32)])
+def test_1d_3d_nfft_stages_every_window_width(d, N, m_w, precision):
+    # every window width in 1-D and 3-D: the 3-D column kernels (m <= 5, both
+    # precisions; tensor-core interpolation in FP32) and the per-point kernels
+    # (m >= 6), against the adjoint NDFT and the NDFT
+    h = N // 2
+    rng = np.random.default_rng(101 + 10 * d + m_w)
+    x = np.concatenate([wl.uniform_ball(401, d, 0.2, 102 + m_w), 0.01 * rng.standard_normal((300, d))])
+    y = wl.uniform_ball(333, d, 0.2, 103 + m_w)
+    plan = plan_for(x, y, N=N, m_w=m_w, precision=precision)
+    tol = max(kb_window_bound(m_w), FLOOR_NFFT[precision])
+    w = rng.standard_normal(len(x))
+    out = np.zeros(((2 * h + 1),) * d + (2,))
+    sk.sk_adjoint_nfft(plan, sk.SK_SET_X, w, out.reshape(-1))
+    got = out[..., 0] + 1j * out[..., 1]
+    err = np.max(np.abs(_common(got, h, d) - ofs.adjoint_ndft(x + 0.5, w, N))) / np.sum(np.abs(w))
+    assert err <= tol, (err, tol)
+    A = rng.standard_normal((2 * h + 1,) * d) + 1j * rng.standard_normal((2 * h + 1,) * d)
+    F = 0.5 * (A + np.conj(A[tuple([slice(None, None, -1)] * d)]))
+    buf = np.stack([F.real, F.imag], axis=-1).reshape(-1).copy()
+    t = np.zeros(len(y))
+    sk.sk_nfft(plan, sk.SK_SET_Y, buf, t)
+    err = np.max(np.abs(t - ofs.ndft(y + 0.5, _common(F, h, d), N).real)) / np.sum(np.abs(F))
+    assert err <= tol, (err, tol)
+
+
 @pytest.mark.parametrize("m_w", [2, 3, 4, 5])
 def test_3d_tensor_core_interpolation_matches_exact_sums_and_cuda_cores(m_w):
     # the tcgen05 interpolation (default for 3-D FP32) against the exact sums and
