@@ -74,3 +74,29 @@ def test_replica_keeps_every_workload_field(name):
             assert getattr(r, f.name) == getattr(w, f.name) + 3000
         else:
             assert getattr(r, f.name) == getattr(w, f.name), f.name
+
+
+def test_roofline_kernel_names_follow_dimension_and_kernel_kind():
+    import bench
+    from paper_2201_07524_gb300 import workloads as wl
+    assert bench.kernel_name("interp", wl.HEADLINE_3D, 1) == "k_interp3_tc<8>"
+    assert bench.kernel_name("interp", wl.HEADLINE_3D, 0) == "k_interp3_col<8, float>"
+    assert bench.kernel_name("spread", wl.HEADLINE_3D, 1) == "k_spread3_col<8, float>"
+    assert bench.kernel_name("interp", wl.GMM_2D, 1) == "k_interp2_tc<12>"
+    assert bench.kernel_name("spread", wl.GMM_2D, 1) == "k_spread2_strip<12, float>"
+    # every name the bench can look up is one the traffic record may hold
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")))
+    for stage, w in (("spread", wl.HEADLINE_3D), ("interp", wl.HEADLINE_3D), ("spread", wl.GMM_2D),
+                     ("interp", wl.GMM_2D)):
+        assert bench.kernel_name(stage, w, 1) in rec
+
+
+def test_bench_workload_table():
+    import bench
+    from paper_2201_07524_gb300 import workloads as wl
+    table = bench._workloads(wl)
+    assert table["headline"] is wl.HEADLINE_3D
+    assert table["gmm2d"].source == "gmm" and table["gmm2d"].weights == "dirichlet"
+    assert table["r1"].r == 1.0 and table["r1"].extra["eps_I"] == 1.0 / 32
