@@ -62,7 +62,29 @@ def build(verbose=False, force=False, extra_flags=()):
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
+    build_example()
     return LIB
+
+
+EXAMPLE_SRC = os.path.join(HERE, "examples", "sk_example.c")
+EXAMPLE = os.path.join(OUT, "sk_example")
+
+
+def build_example():
+    """The plain-C example of the ABI (host compiler, linked against the
+    library, found next to it at run time)."""
+    if not _newer(EXAMPLE, [EXAMPLE_SRC, LIB, os.path.join(INCLUDE, "sk.h")]):
+        return EXAMPLE
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler for the example")
+    cmd = [cc, "-O2", "-std=c11", "-Wall", "-I", INCLUDE, EXAMPLE_SRC, "-L", OUT, "-lsk", "-Wl,-rpath,$ORIGIN",
+           "-o", EXAMPLE]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("example build failed")
+    return EXAMPLE
 
 
 if __name__ == "__main__":
