@@ -91,3 +91,14 @@ def test_null_plan_calls_are_rejected():
     assert L.sk_autotune(None, None, None) == sk.SK_ERR_ARG
     assert L.sk_launch_count(None) == -1
     L.sk_destroy(None)
+
+
+def test_c_example_builds_and_checks_its_arguments(lib):
+    # the plain-C example links against the library and rejects bad
+    # arguments before touching the GPU
+    import subprocess
+    from paper_2201_07524_gb300 import build
+    exe = build.build_example()
+    assert os.path.exists(exe)
+    assert subprocess.run([exe], capture_output=True).returncode == 2
+    assert subprocess.run([exe, "4", "10", "10", "0.05", "3"], capture_output=True).returncode == 2
