@@ -99,82 +99,120 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle legs
-def _oracle_sample_job(n_rows, seed, workload="headline"):
-    """Runs in a spawned process with one thread: times the oracle's exact
-    kernel products (Eq. (matexp)/(matexpt)) on n_rows sampled rows and columns
-    of the workload; returns seconds per full Sinkhorn iteration."""
-    import numpy as np
-    from oracle import sinkhorn as osk
+_POOL_STATE = {}
+
+
+def _oracle_pool_init(workload):
+    """Per-process set-up outside the timed region: one thread, the
+    workload's points and weights generated once."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     from paper_2201_07524_gb300 import workloads as wl
     w = _workloads(wl)[workload]
     x, y = w.points()
+    a, b = w.marginals()
+    _POOL_STATE.update(w=w, x=x, y=y, a=a, b=b)
+
+
+def _oracle_rows_job(args):
+    """The oracle's exact kernel products (Eqs. (matexp)/(matexpt)) and FP64
+    updates for `rows` sampled rows of K v and `rows` columns of K^T u, from
+    u = v = 1; returns the number of rows and columns done."""
+    import numpy as np
+    from oracle import sinkhorn as osk
+    rows, seed = args
+    w, x, y, a, b = (_POOL_STATE[k] for k in ("w", "x", "y", "a", "b"))
     rng = np.random.default_rng(seed)
-    rows = rng.choice(w.n, n_rows, replace=False)
-    cols = rng.choice(w.m, n_rows, replace=False)
-    v = np.ones(w.m)
-    u = np.ones(w.n)
+    ri = rng.choice(w.n, rows, replace=False)
+    ci = rng.choice(w.m, rows, replace=False)
+    u_new = a[ri] / osk.kernel_apply(x[ri], y, np.ones(w.m), w.eps, w.r, chunk=4)
+    v_new = b[ci] / osk.kernel_apply(y[ci], x, np.ones(w.n), w.eps, w.r, chunk=4)
+    assert np.all(np.isfinite(u_new)) and np.all(np.isfinite(v_new))
+    return 2 * rows
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: one single-threaded process per
+    core (spawned, so no CUDA state is inherited), each with the workload's
+    points already generated."""
+
+    def __init__(self, workload):
+        import multiprocessing as mp
+        self.cores = os.cpu_count() or 1
+        self.workload = workload
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_pool_init, initargs=(workload,))
+        self.pool.map(_oracle_rows_job, [(1, 10_000 + k) for k in range(self.cores)])   # warm-up
+
+    def sample(self, rows_per_core, seed):
+        """Wall seconds for rows_per_core rows and as many columns on every
+        core, and the full-iteration time they extrapolate to."""
+        from paper_2201_07524_gb300 import workloads as wl
+        w = _workloads(wl)[self.workload]
+        t0 = time.perf_counter()
+        done = sum(self.pool.map(_oracle_rows_job, [(rows_per_core, seed * 1000 + k) for k in range(self.cores)]))
+        wall = time.perf_counter() - t0
+        return wall, wall * (w.n + w.m) / done, done
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _full_small_run():
+    """The smallest workload (2000 points per side, 2-D, 100 iterations,
+    dense FP64 oracle, Alg. 1), run in full; returns seconds."""
+    from oracle import sinkhorn as osk
+    from paper_2201_07524_gb300 import workloads as wl
+    w = wl.SMALL_2D
+    x, y = w.points()
     a, b = w.marginals()
     t0 = time.perf_counter()
-    t = osk.kernel_apply(x[rows], y, v, w.eps, w.r, chunk=4)
-    u_new = a[rows] / t
-    tt = osk.kernel_apply(y[cols], x, u, w.eps, w.r, chunk=4)
-    v_new = b[cols] / tt
-    dt = time.perf_counter() - t0
-    assert np.all(np.isfinite(u_new)) and np.all(np.isfinite(v_new))
-    # the full iteration does n rows and m columns
-    return dt * (w.n + w.m) / (2.0 * n_rows)
+    out = osk.sinkhorn_dense(x, a, y, b, w.eps, w.r, w.iters)
+    return time.perf_counter() - t0, out["s"]
 
 
 def _workloads(wl):
     return {"headline": wl.HEADLINE_3D, "gmm2d": wl.GMM_2D, "r1": wl.BALL3D_R1}
 
 
-def cpu_oracle_sample(n_rows, seed=0, workload="headline"):
-    import multiprocessing as mp
-    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
-    old = {k: os.environ.get(k) for k in env_keys}
-    for k in env_keys:
-        os.environ[k] = "1"
-    try:
-        ctx = mp.get_context("spawn")
-        with ctx.Pool(1) as pool:
-            t0 = time.perf_counter()
-            sec_per_iter = pool.apply(_oracle_sample_job, (n_rows, seed, workload))
-            wall = time.perf_counter() - t0
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-    return sec_per_iter, wall
-
-
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    rows = args.ref_rows
-    samples = []
-    for _ in range(args.warmup):
-        cpu_oracle_sample(rows, seed=len(samples) + 100)
-    t_all = time.perf_counter()
-    for k in range(args.steps):
-        s, _ = cpu_oracle_sample(rows, seed=k)
-        samples.append(s)
-    wall = time.perf_counter() - t_all
-    sec = sum(samples) / len(samples)
+    from paper_2201_07524_gb300 import workloads as wl
+    w = _workloads(wl)[args.workload]
+    pool = OraclePool(args.workload)
+    try:
+        for k in range(args.warmup):
+            pool.sample(args.ref_rows, 100 + k)
+        walls, secs, done = [], [], 0
+        t_all = time.perf_counter()
+        for k in range(args.steps):
+            wall, sec, dn = pool.sample(args.ref_rows, k)
+            walls.append(wall)
+            secs.append(sec)
+            done += dn
+        wall_all = time.perf_counter() - t_all
+    finally:
+        pool.close()
+    sec = sum(secs) / len(secs)
     value = 1.0 / sec
+    frac = done / args.steps / (w.n + w.m)
+    sample = ("each step: %d sampled rows of K v and %d columns of K^T u on each of %d host cores (exact FP64 "
+              "numpy sums over all %.0e points, one thread per core), a fraction %.2e of one iteration; value "
+              "extrapolated to a full iteration, ms_per_step is the measured step" %
+              (args.ref_rows, args.ref_rows, pool.cores, float(w.n), frac))
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "ball3d_n1e6_eps0.02_fp32", "n": 1000000, "m": 1000000, "d": 3, "r": 2,
-                   "eps": 0.02, "kernel": "exact FP64 sums (oracle)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d sampled rows of K v and %d columns of K^T u per step (exact FP64 "
-                                   "numpy sums over all 1e6 points), scaled to a full iteration" % (rows, rows)},
+        "impl": "reference", "metric": METRIC if args.workload == "headline" else METRIC_OTHER % w.name,
+        "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "m": w.m, "d": w.d, "r": w.r, "eps": w.eps,
+                   "kernel": "exact FP64 sums (oracle)",
+                   "extrapolated": "value from %d sampled rows + columns per step (fraction %.2e of an iteration)"
+                                   % (done // args.steps, frac)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s": wall,
+        "wall_s": wall_all,
     }
     print(json.dumps(line), flush=True)
 
@@ -251,10 +289,44 @@ def replica_workload(w, rank):
     return dataclasses.replace(w, seed_x=w.seed_x + 1000 * rank, seed_y=w.seed_y + 1000 * rank)
 
 
-def fp32_alu_peak_tflops(pk):
-    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
-    mhz = float(pk.get("sm_max_mhz", 2070.0))
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+def fp32_peak(sk):
+    """The FP32 roofline denominator, measured on this GPU (sk_fp32_peak: FMA
+    chains on every SM, scalar and packed FP32x2 forms); the larger of the two
+    is the peak.  Returns (peak TFLOP/s, record)."""
+    scalar, sms = sk.sk_fp32_peak(False, 200000)
+    packed, _ = sk.sk_fp32_peak(True, 100000)
+    rec = {"scalar_tflops": scalar, "packed_tflops": packed, "sms": sms,
+           "method": "sk_fp32_peak: 8 independent FMA chains per thread, every SM filled, CUDA events"}
+    return max(scalar, packed), rec
+
+
+def small_full_run(sk, T, dev, stream):
+    """The smallest workload, ball2d_n2000_eps0.05_fp64 (2000 points per side,
+    2-D, r = 2, eps = 0.05, 100 iterations, FP64 fast summation), run in full
+    on the GPU and by the dense FP64 oracle on the host (Alg. 1, numpy with its
+    default threads); both values and times."""
+    import torch
+    from paper_2201_07524_gb300 import workloads as wl
+    w = wl.SMALL_2D
+    x, y = w.points()
+    a, b = w.marginals()
+    prm = sk.sk_default_params(N=w.N, m_w=w.m_w, sigma=w.sigma, precision=sk.SK_FP64)
+    plan = sk.sk_init(T(x), T(a), T(y), T(b), w.eps, w.r, prm)
+    sk.sk_solve(plan, 2, result=False)                      # warm-up (graph capture)
+    sk.sk_set_state(plan)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    sk.sk_solve(plan, w.iters, result=False)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    gpu_ms = ev0.elapsed_time(ev1)
+    _, res = sk.sk_solve(plan, 0)
+    plan.close()
+    cpu_s, s_oracle = _full_small_run()
+    return {"workload": w.name, "iters": w.iters, "gpu_ms": gpu_ms, "cpu_oracle_s": cpu_s,
+            "cpu_cores": os.cpu_count(), "s_gpu": res["s"], "s_oracle": s_oracle,
+            "s_rel_err": abs(res["s"] - s_oracle) / abs(s_oracle)}
 
 
 def run_ours(args, rank, world):
@@ -319,30 +391,40 @@ def run_ours(args, rank, world):
     stages = sk.sk_stage_times(plan, 0)
     torch.cuda.synchronize(dev)
 
-    # accuracy of this run's value against exact sums (a sampled check of one product)
+    # equal-accuracy comparison with the direct-summation Sinkhorn (Eqs. (matexp),
+    # (matexpt) summed exactly, FP32 kernel values, FP64 across tiles) on the
+    # same GPU and plan: both methods run the same number of iterations from
+    # u = v = 1, and the values s (Alg. 3 result line) are compared
+    K = max(2, args.direct_iters)
+    sk.sk_set_state(plan)
+    _, res_nfft = sk.sk_solve(plan, K)
     v_test = wl.positive_vector(w.m, 36)
     t_gpu = torch.zeros(w.n, dtype=torch.float64, device=dev)
     sk.sk_kernel_apply(plan, 0, T(v_test), t_gpu)
-    _, res = sk.sk_solve(plan, 0)
-
-    # direct summation Sinkhorn on the same GPU, same plan, timed the same way
     direct = None
-    if args.direct_steps > 0:
+    t_dir = None
+    if args.direct_iters > 0:
         sk.sk_set_state(plan)
         sk.sk_set_method(plan, sk.SK_METHOD_DIRECT)
-        sk.sk_solve(plan, 1, result=False)
+        sk.sk_solve(plan, 1, result=False)            # iteration 1 of K, untimed (graph capture)
         torch.cuda.synchronize(dev)
-        ds = [torch.cuda.Event(enable_timing=True) for _ in range(args.direct_steps)]
-        de = [torch.cuda.Event(enable_timing=True) for _ in range(args.direct_steps)]
-        for k in range(args.direct_steps):
+        ds = [torch.cuda.Event(enable_timing=True) for _ in range(K - 1)]
+        de = [torch.cuda.Event(enable_timing=True) for _ in range(K - 1)]
+        for k in range(K - 1):
             ds[k].record(stream)
             sk.sk_solve(plan, 1, result=False)
             de[k].record(stream)
         torch.cuda.synchronize(dev)
-        dms = sum(s.elapsed_time(e) for s, e in zip(ds, de)) / args.direct_steps
-        direct = {"value": 1e3 / dms, "unit": UNIT, "ms_per_step": dms, "steps": args.direct_steps,
-                  "speedup_nfft_over_direct": (value / world) / (1e3 / dms)}
+        dms = sum(s0.elapsed_time(e0) for s0, e0 in zip(ds, de)) / (K - 1)
+        _, res_dir = sk.sk_solve(plan, 0)                 # value of the state after K iterations
+        t_dir = torch.zeros(w.n, dtype=torch.float64, device=dev)
+        sk.sk_kernel_apply(plan, 0, T(v_test), t_dir)
         sk.sk_set_method(plan, sk.SK_METHOD_NFFT)
+        rel = abs(res_nfft["s"] - res_dir["s"]) / abs(res_dir["s"])
+        direct = {"value": 1e3 / dms, "unit": UNIT, "ms_per_step": dms, "steps": K - 1,
+                  "speedup_nfft_over_direct": (value / world) / (1e3 / dms),
+                  "s_after_iters": res_dir["s"], "marg_err_after_iters": res_dir["marg_err"]}
+    res = res_nfft
 
     # end to end through the C ABI with host buffers: pinned inputs -> sk_init
     # (copies, sort, tables) -> K iterations -> u, v, result read back to the host
@@ -373,7 +455,7 @@ def run_ours(args, rank, world):
     kname = kernel_name(dominant, w, info.get("tensor_cores", 0))
     flops, bytes_ = counts[dominant]
     dur_s = per_launch[dominant] / 1e3
-    alu_peak = fp32_alu_peak_tflops(pk)
+    alu_peak, peak_rec = fp32_peak(sk)
     achieved = flops / dur_s / 1e12
     stage_report = {}
     for k in ("spread", "fft", "interp", "near", "other"):
@@ -386,20 +468,35 @@ def run_ours(args, rank, world):
                 ent["hbm_frac"] = ent["gbs"] / pk["hbm_gbs"]
             stage_report[k] = ent
 
-    # sampled accuracy of the product used in this run
+    # sampled accuracy of the products used in this run: exact FP64 sums of
+    # the oracle on 32 rows
     if rank == 0:
         from oracle import sinkhorn as osk
         rows = np.random.default_rng(37).choice(w.n, 32, replace=False)
         exact = osk.kernel_apply(x[rows], y, v_test, w.eps, w.r, chunk=4)
-        got = t_gpu.cpu().numpy()[rows]
-        efs_sample = float(np.max(np.abs(got - exact)) / np.max(np.abs(exact)))
+        efs = lambda t: float(np.max(np.abs(t.cpu().numpy()[rows] - exact)) / np.max(np.abs(exact)))
+        efs_sample = efs(t_gpu)
+        efs_direct = efs(t_dir) if t_dir is not None else None
+    accuracy = {"efs_sampled_rows": efs_sample if rank == 0 else None, "iters_compared": K,
+                "s_nfft": res_nfft["s"], "marg_err_nfft": res_nfft["marg_err"]}
+    if direct is not None:
+        accuracy.update({"s_direct": direct["s_after_iters"], "s_rel_err_vs_direct": rel,
+                         "s_rel_err_gate": 1e-5, "s_rel_err_ok": bool(rel <= 1e-5),
+                         "efs_direct_sampled_rows": efs_direct if rank == 0 else None})
     cpu = None
+    small = None
     if rank == 0 and world == 1 and args.cpu_rows > 0:
-        sec, wall_cpu = cpu_oracle_sample(args.cpu_rows, workload=args.workload)
-        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d sampled rows of K v and %d columns of K^T u (exact FP64 numpy sums over all "
-                         "%.0e points, one thread), scaled to one full iteration; %.1f s wall" %
-                         (args.cpu_rows, args.cpu_rows, float(w.n), wall_cpu)}
+        pool = OraclePool(args.workload)
+        try:
+            wall_cpu, sec, done = pool.sample(args.cpu_rows, 7)
+        finally:
+            pool.close()
+        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+               "sample": "%d sampled rows of K v and %d columns of K^T u on each of %d host cores (exact FP64 numpy "
+                         "sums over all %.0e points, one thread per core, %d rows + columns in %.2f s wall), "
+                         "extrapolated to one full iteration" %
+                         (args.cpu_rows, args.cpu_rows, pool.cores, float(w.n), done, wall_cpu)}
+        small = small_full_run(sk, T, dev, stream)
 
     if rank == 0:
         line = {
@@ -421,16 +518,16 @@ def run_ours(args, rank, world):
             "roofline": {"bound": "alu", "kernel": kname or dominant, "achieved": achieved,
                          "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                          "traffic": measured_traffic(kname),
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s peaks file)"
-                                        % (float(pk.get("sm_max_mhz", 2070.0)), pk_kind),
+                         "peak_source": "measured on this GPU (FP32 FMA chains; of measured)",
+                         "peak_measurement": peak_rec,
                          "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
-                         "hbm_frac": bytes_ / dur_s / 1e9 / pk["hbm_gbs"]},
+                         "hbm_frac": bytes_ / dur_s / 1e9 / pk["hbm_gbs"], "hbm_peak_source": pk_kind},
             "stages": stage_report,
             "direct": direct,
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "accuracy": {"efs_sampled_rows": efs_sample, "s_after_run": res["s"],
-                         "marg_err_after_run": res["marg_err"]},
+            "accuracy": accuracy,
+            "small_full_run": small,
             "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
@@ -531,9 +628,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--direct-steps", type=int, default=2)
-    ap.add_argument("--cpu-rows", type=int, default=200)
-    ap.add_argument("--ref-rows", type=int, default=64)
+    ap.add_argument("--direct-iters", type=int, default=10,
+                    help="iterations of the NFFT and the direct method compared from u = v = 1 (direct timed)")
+    ap.add_argument("--cpu-rows", type=int, default=8, help="oracle rows (and columns) per host core")
+    ap.add_argument("--ref-rows", type=int, default=8, help="reference arm: oracle rows (and columns) per core")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--workload", default="headline", choices=["headline", "gmm2d", "r1", "batch"],
                     help="headline: the 1e6-point 3-D workload; gmm2d: the 1e6-point 2-D Gaussian mixture; "

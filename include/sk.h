@@ -54,7 +54,7 @@ enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / in
 enum { SK_METHOD_NFFT = 0, SK_METHOD_DIRECT = 1 };
 enum { SK_DOMAIN_SCALING = 0, SK_DOMAIN_LOG = 1 };   /* state of the iteration: Alg. 3 or Alg. 4 */
 enum { SK_KERNELS_SIMT = 0, SK_KERNELS_TENSOR = 1 };   /* interpolation on CUDA cores or tensor cores */
-enum { SK_FAULT_NONE = 0, SK_FAULT_TC_WAIT = 1 };      /* sk_inject_fault (test hook) */
+enum { SK_FAULT_NONE = 0, SK_FAULT_TC_WAIT = 1, SK_FAULT_FFT_WAIT = 2 };   /* sk_inject_fault (test hook) */
 enum { SK_SET_X = 0, SK_SET_Y = 1 };        /* which point cloud a stage entry point acts on */
 
 typedef struct sk_plan sk_plan;
@@ -124,6 +124,8 @@ typedef struct {
     int n_subproblems_x, n_subproblems_y;   /* work items of the per-point spreading kernels (1-D; 3-D with m_w > 5) */
     int64_t device_bytes;        /* device memory the plan holds */
     int tensor_cores;            /* 1: interpolation runs on tensor cores (sk_set_kernels) */
+    int fft_persistent;          /* 1: a product's five FFT passes run as one cooperative launch (3-D
+                                    FP32 plans with n_os <= 256, outside sk_solve_batch) */
 } sk_info;
 
 /* Text for a status code (static storage, never NULL). */
@@ -215,8 +217,15 @@ int sk_autotune(sk_plan* plan, int* chosen, void* stream);
  * SK_ERR_TIMEOUT when they read results back (the state of that solve is not
  * meaningful).  SK_FAULT_NONE restores normal operation.  Nothing faults or
  * hangs either way.
+ * SK_FAULT_FFT_WAIT does the same for the persistent 3-D FFT (one cooperative
+ * launch for the five passes of a product, whose blocks meet at grid-wide
+ * barriers): its first barrier waits for one arrival more than the grid has,
+ * so every block's bounded wait (about a second) runs out, the kernel skips
+ * its remaining passes, and sk_solve returns SK_ERR_TIMEOUT.
  * Errors: SK_ERR_ARG for a NULL plan or an unknown kind; SK_ERR_UNSUPPORTED
- * for SK_FAULT_TC_WAIT when the plan does not interpolate on tensor cores.
+ * for SK_FAULT_TC_WAIT when the plan does not interpolate on tensor cores, and
+ * for SK_FAULT_FFT_WAIT when its products do not use the persistent FFT
+ * (sk_info.fft_persistent = 0, or the direct method).
  */
 int sk_inject_fault(sk_plan* plan, int kind);
 
@@ -337,6 +346,31 @@ int sk_adjoint_nfft(sk_plan* plan, int set, const double* w, double* fhat, void*
  * real part of the paper's sum over I_N. */
 int sk_nfft(sk_plan* plan, int set, const double* fhat, double* f, void* stream);
 
+/* ------------------------------------------------ sharded products ---------
+ * One product split over several plans (for example one per GPU) by the
+ * linearity of the inner sum of Eq. (fastsum): every plan holds a shard of the
+ * sources and of the targets, all plans share one torus geometry (params with
+ * user_geometry = 1 and the same center, scale, N, sigma, m_w, p, eps_B, eps,
+ * r), each computes the spectrum of its own sources, the spectra are summed
+ * across the plans (an all-reduce), and each plan evaluates the product at its
+ * own targets from the sum:
+ *   (K w)_i = Re sum_{k in I_N} b_k (sum over shards of spec_k) exp(2 pi i k.z_i).
+ * The near-field correction of kernels that are not smooth at 0 (r not an
+ * even integer) is not part of this split; such plans are refused
+ * (SK_ERR_UNSUPPORTED).
+ *
+ * sk_spectrum: the adjoint NFFT (inner sum of Eq. (fastsum)) of weights w
+ * (caller order) on cloud `set`, spec[k] = sum_j w_j exp(-2 pi i k.z_j) for
+ * k in {-N/2..N/2}^d, as in sk_adjoint_nfft: (N+1)^d complex values,
+ * interleaved (re, im) doubles, row-major with index k_t + N/2.
+ * sk_apply_spectrum: out (caller order, n or m values) = the outer sum above
+ * at the points of cloud `set`, for a Hermitian spec (spec[-k] = conj
+ * spec[k]; every sum of sk_spectrum outputs is one).  Both: host or device
+ * pointers; SK_ERR_ARG for NULL arguments or an unknown set.
+ */
+int sk_spectrum(sk_plan* plan, int set, const double* w, double* spec, void* stream);
+int sk_apply_spectrum(sk_plan* plan, int set, const double* spec, double* out, void* stream);
+
 /* Per-stage device times.  enable = 1 turns on CUDA-event timing of every
  * stage on the plan's stream (and disables graph replay); enable = 0 turns it
  * off.  ms_out (may be NULL) receives SK_NSTAGES accumulated milliseconds,
@@ -349,6 +383,18 @@ int sk_stage_times(sk_plan* plan, int enable, double* ms_out, int64_t* counts_ou
 /* Number of kernels this plan has launched (graph replays count every kernel node). */
 int64_t sk_launch_count(const sk_plan* plan);
 
+/* -------------------------------------------------------- measurement ------
+ * FP32 arithmetic rate of the current device, measured: every thread of a grid
+ * that fills every SM runs 8 independent FMA chains for `iters` steps
+ * (packed = 0: scalar FP32 FMAs; packed = 1: packed FMAs on float2 pairs, two
+ * per instruction), timed with CUDA events on `stream` after one untimed
+ * launch.  *tflops receives 2 flops x FMAs / time in TFLOP/s; *sms (may be
+ * NULL) the device's SM count.  It is the denominator of the roofline of the
+ * kernels bound by FP32 arithmetic.  Synchronizes `stream`.
+ * Errors: SK_ERR_ARG (tflops NULL, iters < 1, packed not 0 or 1); SK_ERR_CUDA.
+ */
+int sk_fp32_peak(int packed, int iters, double* tflops, int* sms, void* stream);
+
 /* ---------------------------------------------- no-allocation entry point --
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory (code running under a framework whose memory pool
@@ -359,19 +405,22 @@ int64_t sk_launch_count(const sk_plan* plan);
  *
  * Computes, by direct FP32 kernel evaluation with FP64 accumulation across
  * 1024-source tiles (the direct method of sk_set_method),
- *   t_out[i]     = sum_j v_j exp(-||x_i - y_j||^r / eps)            (Eq. (matexp))
- *   stats_out[0] = sum_i (u_i t_out[i] - a_i)^2   (squared row term of Eq. (Error))
- *   stats_out[1] = sum_i u_i t_out[i]             (u^T K v)
+ *   t_out[i]     = sum_j v_j exp(-||x_i - y_j||^r / eps)
+ *   stats_out[0] = sum_i (u_i t_out[i] - a_i)^2
+ *   stats_out[1] = sum_i u_i t_out[i]
  * x: n-by-d, y: m-by-d row-major; u, a: n; v: m; t_out: n; stats_out: 2.
- * Every pointer must be device (or managed) memory, else SK_ERR_ARG.  The call
- * is asynchronous on `stream`.
+ * Every pointer must be device memory of the current device (or managed
+ * memory), else SK_ERR_ARG.  t_out and stats_out may not overlap an input or
+ * each other (other blocks still read the inputs while t_out is written),
+ * else SK_ERR_ARG.  The call is asynchronous on `stream`.
  *
  * Scratch: the per-block partial sums live in one file-scope device array of
  * 64 KB + 256 B, present on every GPU that loads the library until the process
  * exits.  It bounds n <= 2,097,152 (4096 blocks of 512 targets); larger n
  * returns SK_ERR_TOO_LARGE before any GPU work.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress), so make the
- * first call on each device before any stream capture.  All calls share the
+ * looks up that array's device address (cudaGetSymbolAddress) and keeps it,
+ * so make the first call on each device before any stream capture, and do not
+ * reset the device after it (the array may then move).  All calls share the
  * array: calls whose kernels overlap on the GPU (concurrent streams or host
  * threads on one device) race and return wrong sums, so serialize them. */
 int sk_direct_residual_noalloc(int d, int64_t n, const double* x, const double* u, const double* a,

@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsk.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["sk_api.cu", "sk_plan_kernels.cu", "sk_spread.cu", "sk_spread3.cu", "sk_fft.cu", "sk_direct.cu", "sk_nearfield.cu", "sk_noalloc.cu", "sk_tc.cu"]
+SOURCES = ["sk_api.cu", "sk_plan_kernels.cu", "sk_spread.cu", "sk_spread3.cu", "sk_fft.cu", "sk_direct.cu", "sk_nearfield.cu", "sk_noalloc.cu", "sk_tc.cu", "sk_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

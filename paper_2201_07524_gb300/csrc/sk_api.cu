@@ -36,6 +36,7 @@ struct sk_plan {
     FftPlan fft;
     size_t grid_elems = 0;
     double* bk = nullptr;       // N^d FP64
+    double* spec_tmp = nullptr; // (N+1)^d complex FP64 scratch of sk_apply_spectrum (allocated on first use)
     double* psihat = nullptr;   // 2h+1 FP64
     double* partial = nullptr;  // reduction partials
     int partial_blocks = 0;
@@ -724,6 +725,15 @@ void prepare_kernels(sk_plan* P) {
         ia.nttasks = 0;
         CK(launch_interp_tc(P->d, P->W, ia, Epilogue{}, P->ps));
     }
+    // the persistent 3-D convolution where it applies; its first launch runs
+    // on the zero grid, and a launch the device refuses leaves the pass kernels
+    P->fft.bar = P->ticket + 6;
+    P->fft.status = P->status;
+    P->fft.coop_blocks = fft_coop_blocks<T>(P->fft);
+    if (P->fft.coop_blocks > 0 && launch_fft_convolve<T>(P->fft, P->ps, nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        P->fft.coop_blocks = 0;
+    }
     CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
 }
 
@@ -1274,7 +1284,7 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         const int64_t nmax = std::max(n, m);
         P->partial_blocks = std::max<int64_t>(interp_blocks<double>(nmax), kRedBlocks);
         P->partial = static_cast<double*>(dalloc(P, size_t(P->partial_blocks) * 8 * sizeof(double)));
-        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 8));   // [0] reductions, [2..3] interpolation queue, [4..5] spreading queue
+        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 8));   // [0] reductions, [2..3] interpolation queue, [4..5] spreading queue, [6..7] FFT grid barrier
         P->stats = static_cast<double*>(dalloc(P, sizeof(double) * (3 * NSLOTS + 8)));
         P->status = static_cast<int*>(dalloc(P, sizeof(int) * 4));
         P->shift = static_cast<double*>(dalloc(P, sizeof(double) * 2));
@@ -1519,11 +1529,14 @@ int sk_autotune(sk_plan* P, int* chosen, void* stream) {
 }
 
 int sk_inject_fault(sk_plan* P, int kind) {
-    if (!P || (kind != SK_FAULT_NONE && kind != SK_FAULT_TC_WAIT)) return SK_ERR_ARG;
+    if (!P || (kind != SK_FAULT_NONE && kind != SK_FAULT_TC_WAIT && kind != SK_FAULT_FFT_WAIT)) return SK_ERR_ARG;
     if (kind == SK_FAULT_TC_WAIT && !P->tc) return SK_ERR_UNSUPPORTED;
+    if (kind == SK_FAULT_FFT_WAIT && (P->fft.coop_blocks <= 0 || P->method != SK_METHOD_NFFT))
+        return SK_ERR_UNSUPPORTED;
     if (kind != P->inject) {
         destroy_graph(P);
         P->inject = kind;
+        P->fft.inject = kind == SK_FAULT_FFT_WAIT ? 1 : 0;
     }
     return SK_OK;
 }
@@ -1655,7 +1668,17 @@ int sk_solve_batch(sk_plan* const* plans, int count, int max_iter, sk_result* re
                     sk_plan* P = plans[i];
                     CK(cudaStreamWaitEvent(P->ps, fork, 0));
                     const int64_t before = P->launches;
-                    run_iteration(P);
+                    // the branches run side by side: the persistent FFT, which
+                    // wants every SM, gives way to the pass kernels here
+                    const int coop = P->fft.coop_blocks;
+                    P->fft.coop_blocks = 0;
+                    try {
+                        run_iteration(P);
+                    } catch (...) {
+                        P->fft.coop_blocks = coop;
+                        throw;
+                    }
+                    P->fft.coop_blocks = coop;
                     kernels[size_t(i)] = P->launches - before;
                     P->launches = before;
                     CK(cudaEventRecord(join[size_t(i)], P->ps));
@@ -1885,6 +1908,7 @@ int sk_plan_info(const sk_plan* P, sk_info* info) {
     info->n_subproblems_y = P->Y.nsub;
     info->device_bytes = P->bytes;
     info->tensor_cores = P->tc ? 1 : 0;
+    info->fft_persistent = P->fft.coop_blocks > 0 ? 1 : 0;
     return SK_OK;
 }
 
@@ -1933,13 +1957,38 @@ int sk_adjoint_nfft(sk_plan* P, int set, const double* w, double* fhat, void* st
     return SK_OK;
 }
 
+namespace {
+// The NFFT of a device-resident Hermitian coefficient array `din` at cloud c
+// into f (host or device, caller order).
+void nfft_device(sk_plan* P, Cloud& c, const double* din, double* f) {
+    const bool host_out = !is_device_ptr(f);
+    Epilogue e = make_epilogue(P, EPI_APPLY, c, 0, host_out ? c.stage : f);
+    if (P->precision == SK_FP32) {
+        CK(launch_fft_forward<float>(P->fft, din, P->ps, &P->launches));
+        interp_from_grid<float>(P, c, e);
+    } else {
+        CK(launch_fft_forward<double>(P->fft, din, P->ps, &P->launches));
+        interp_from_grid<double>(P, c, e);
+    }
+    if (host_out) {
+        CK(cudaMemcpyAsync(f, c.stage, size_t(c.n) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
+        CK(cudaStreamSynchronize(P->ps));
+    }
+}
+
+int64_t spectrum_size(const sk_plan* P) {
+    int64_t total = 1;
+    for (int t = 0; t < P->d; ++t) total *= (2 * P->h + 1);
+    return total;
+}
+}  // namespace
+
 int sk_nfft(sk_plan* P, int set, const double* fhat, double* f, void* stream) {
     if (!P || !fhat || !f || (set != SK_SET_X && set != SK_SET_Y)) return SK_ERR_ARG;
     try {
         enter(P, stream);
         Cloud& c = set == SK_SET_X ? P->X : P->Y;
-        int64_t total = 1;
-        for (int t = 0; t < P->d; ++t) total *= (2 * P->h + 1);
+        const int64_t total = spectrum_size(P);
         const double* din = fhat;
         double* tmp = nullptr;
         if (!is_device_ptr(fhat)) {
@@ -1947,20 +1996,38 @@ int sk_nfft(sk_plan* P, int set, const double* fhat, double* f, void* stream) {
             CK(cudaMemcpyAsync(tmp, fhat, size_t(2 * total) * sizeof(double), cudaMemcpyHostToDevice, P->ps));
             din = tmp;
         }
-        const bool host_out = !is_device_ptr(f);
-        Epilogue e = make_epilogue(P, EPI_APPLY, c, 0, host_out ? c.stage : f);
-        if (P->precision == SK_FP32) {
-            CK(launch_fft_forward<float>(P->fft, din, P->ps, &P->launches));
-            interp_from_grid<float>(P, c, e);
-        } else {
-            CK(launch_fft_forward<double>(P->fft, din, P->ps, &P->launches));
-            interp_from_grid<double>(P, c, e);
-        }
+        nfft_device(P, c, din, f);
         if (tmp) CK(cudaFreeAsync(tmp, P->ps));
-        if (host_out) {
-            CK(cudaMemcpyAsync(f, c.stage, size_t(c.n) * sizeof(double), cudaMemcpyDeviceToHost, P->ps));
-            CK(cudaStreamSynchronize(P->ps));
+        leave(P, stream);
+    } catch (const Fail& f2) {
+        return fail_code(f2);
+    }
+    return SK_OK;
+}
+
+int sk_spectrum(sk_plan* P, int set, const double* w, double* spec, void* stream) {
+    if (P && P->nearfield) return SK_ERR_UNSUPPORTED;
+    return sk_adjoint_nfft(P, set, w, spec, stream);
+}
+
+int sk_apply_spectrum(sk_plan* P, int set, const double* spec, double* out, void* stream) {
+    if (!P || !spec || !out || (set != SK_SET_X && set != SK_SET_Y)) return SK_ERR_ARG;
+    if (P->nearfield) return SK_ERR_UNSUPPORTED;
+    try {
+        enter(P, stream);
+        Cloud& c = set == SK_SET_X ? P->X : P->Y;
+        const int64_t total = spectrum_size(P);
+        if (!P->spec_tmp) P->spec_tmp = static_cast<double*>(dalloc(P, size_t(2 * total) * sizeof(double)));
+        const double* din = spec;
+        if (!is_device_ptr(spec)) {
+            CK(cudaMemcpyAsync(P->spec_tmp, spec, size_t(2 * total) * sizeof(double), cudaMemcpyHostToDevice,
+                               P->ps));
+            din = P->spec_tmp;
         }
+        k_times_bk<<<nblk(total), 256, 0, P->ps>>>(din, P->bk, P->d, P->h, P->spec_tmp);
+        CK(cudaGetLastError());
+        ++P->launches;
+        nfft_device(P, c, P->spec_tmp, out);
         leave(P, stream);
     } catch (const Fail& f2) {
         return fail_code(f2);

@@ -16,6 +16,7 @@
 // the library and lives until the process exits.  Every call shares it, so
 // calls whose kernels overlap on the GPU (different streams, or different host
 // threads on one device) race and give wrong sums; serialize them.
+#include <cstdint>
 #include <mutex>
 
 #include "sk_internal.cuh"
@@ -132,28 +133,39 @@ k_direct_residual_noalloc(const double* __restrict__ x, const double* __restrict
     }
 }
 
-bool on_device(const void* p) {
+// True when p is memory the kernel may read on the current device: device
+// memory of that device, or managed memory.  Device memory of another GPU is
+// refused: without peer access a kernel that reads it faults.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
-// Device address of g_noalloc_scratch for the current device, looked up once
-// per device (the first call on a device does this set-up).
-cudaError_t scratch_address(double** out) {
+// True when the byte ranges [p, p + pn) and [q, q + qn) share a byte.
+bool overlaps(const void* p, size_t pn, const void* q, size_t qn) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p), b = reinterpret_cast<uintptr_t>(q);
+    return a < b + qn && b < a + pn;
+}
+
+// Device address of g_noalloc_scratch on device `dev` (the current device),
+// looked up once per device: the first call on a device does this set-up, so
+// that call has to come before any stream capture.  The address is kept for
+// the life of the process; a device reset (cudaDeviceReset, or a reset of the
+// primary context) after that first call is not supported, because the
+// library's module, and the array with it, may then sit at another address.
+cudaError_t scratch_address(int dev, double** out) {
     static std::mutex mu;
     static double* addr[64] = {nullptr};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
     if (!addr[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         addr[dev] = static_cast<double*>(p);
     }
@@ -192,16 +204,33 @@ extern "C" int sk_direct_residual_noalloc(int d, int64_t n, const double* x, con
         return fail(SK_ERR_ARG, "eps must be > 0 and r >= 1");
     if (n > int64_t(kNoAllocMaxBlocks) * kNoAllocTargetsPerBlock)
         return fail(SK_ERR_TOO_LARGE, "n exceeds the fixed scratch of sk_direct_residual_noalloc (n <= 2097152)");
-    const void* ptrs[7] = {x, u, a, y, v, t_out, stats_out};
-    for (const void* p : ptrs)
-        if (!p || !on_device(p)) return fail(SK_ERR_ARG, "all arrays must be device (or managed) memory");
-    double* scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(SK_ERR_CUDA, cudaGetErrorString(e));
     }
+    const void* ptrs[7] = {x, u, a, y, v, t_out, stats_out};
+    for (const void* p : ptrs)
+        if (!p || !on_device(p, dev))
+            return fail(SK_ERR_ARG, "all arrays must be device memory of the current device (or managed)");
+    // outputs may not share memory with any input or with each other: other
+    // blocks still read the inputs while t_out is written
+    const size_t nb = size_t(n) * sizeof(double), mb = size_t(m) * sizeof(double);
+    const void* in_p[5] = {x, u, a, y, v};
+    const size_t in_n[5] = {nb * size_t(d), nb, nb, mb * size_t(d), mb};
+    for (int k = 0; k < 5; ++k)
+        if (overlaps(t_out, nb, in_p[k], in_n[k]) || overlaps(stats_out, 2 * sizeof(double), in_p[k], in_n[k]))
+            return fail(SK_ERR_ARG, "t_out and stats_out must not overlap an input");
+    if (overlaps(t_out, nb, stats_out, 2 * sizeof(double)))
+        return fail(SK_ERR_ARG, "t_out and stats_out must not overlap");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* scratch = nullptr;
+    e = scratch_address(dev, &scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SK_ERR_CUDA, cudaGetErrorString(e));
+    }
     // the ticket must start at zero; an earlier call leaves it at zero, but a
     // call that was cut short may not have
     e = cudaMemsetAsync(scratch, 0, kNoAllocTicketDoubles * sizeof(double), s);

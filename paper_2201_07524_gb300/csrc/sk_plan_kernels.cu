@@ -501,6 +501,26 @@ void launch_gather_points(const int* perm, int64_t n, int d, T* const in[3], T* 
                                                                  out[2]);
 }
 
+__global__ void k_times_bk(const double* __restrict__ spec, const double* __restrict__ bk, int d, int h,
+                           double* __restrict__ out) {
+    const int K = 2 * h + 1, N = 2 * h;
+    int64_t total = 1;
+    for (int t = 0; t < d; ++t) total *= K;
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int64_t rem = idx, b = 0, stride = 1;
+    for (int t = d - 1; t >= 0; --t) {
+        int kt = int(rem % K) - h;
+        rem /= K;
+        if (kt == h) kt = -h;
+        b += int64_t(kt + h) * stride;
+        stride *= N;
+    }
+    const double f = bk[b];
+    out[2 * idx] = spec[2 * idx] * f;
+    out[2 * idx + 1] = spec[2 * idx + 1] * f;
+}
+
 template <typename T>
 void launch_build_mult(T* M, int d, int h, const double* bk, double inv_norm, const double* psihat,
                        int64_t total, cudaStream_t s) {

@@ -54,6 +54,11 @@ void launch_build_mult(T* M, int d, int h, const double* bk, double inv_norm, co
 template <typename T>
 void launch_twiddles(void* tw, int n, cudaStream_t s);
 
+// spec[k] *= b_k over k in {-h..h}^d (interleaved complex, row-major with
+// index k_t + h), b_k taken from the N^d table over I_N; the kernel is even in
+// every coordinate, so b at k_t = +h is b at k_t = -h.
+__global__ void k_times_bk(const double* spec, const double* bk, int d, int h, double* out);
+
 __global__ void k_init_bounds(int* out);
 template <typename T>
 void launch_cell_bounds(void* const u[3], int64_t n, int d, int* out, cudaStream_t s);

@@ -34,7 +34,13 @@
 // MMA group per tile of 128 points.  Tensor memory is shared by the blocks of
 // an SM, so the launch pads its shared memory to keep at most 512 / columns
 // blocks on an SM.  Every wait on the MMA's completion is bounded: a wait that
-// gives up sets bit 2 of the epilogue's status word, and the block stops.
+// gives up (on any lane of a warp) sets bit 2 of the epilogue's status word,
+// the warp skips that tile's tensor-memory loads, and the block stops after
+// the tile.  Before releasing its tensor memory the block waits once more
+// (bounded) for the MMA group; if that wait gives up too, the columns are
+// released all the same, because a kernel may not exit holding tensor memory:
+// an MMA that is still running could then write into columns another block
+// allocates next, and the solve that reported the timeout is not meaningful.
 #include <algorithm>
 #include <cstdint>
 
@@ -314,7 +320,9 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
                 wxf[i] = vx;
                 wyf[i] = vy;
             }
-            const bool done = mbar_wait(&bar, phase);
+            // warp-uniform: a warp whose wait gave up on any lane skips the
+            // (warp-collective) tensor-memory loads of this tile
+            const bool done = __all_sync(0xffffffffu, mbar_wait(&bar, phase));
             phase ^= 1u;
             if (!done) {
                 failed = true;
@@ -327,6 +335,7 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
             for (int i = 0; i < S::X; ++i) rs[i] = 0.f;
 #pragma unroll
             for (int ch = 0; ch < S::NCH; ++ch) {
+                if (failed) break;
                 float h[32];
                 tmem_ld32(tlane + uint32_t(ch * 32), h);
 #pragma unroll
@@ -493,7 +502,9 @@ __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
                 }
                 tc_commit(&bar);
             }
-            const bool done = mbar_wait(&bar, phase);
+            // warp-uniform: a warp whose wait gave up on any lane skips the
+            // (warp-collective) tensor-memory loads of this tile
+            const bool done = __all_sync(0xffffffffu, mbar_wait(&bar, phase));
             phase ^= 1u;
             if (!done) {
                 failed = true;
@@ -504,7 +515,7 @@ __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
             // the MMA has read the A operand, so the thread's own row of it (6
             // chunks of 4 in the hi part, 6 in the lo part) holds its 32 results:
             // element e in chunk e / 4, chunks 6 and 7 in the lo part
-            {
+            if (!failed) {
                 float h[32];
                 tmem_ld32(tlane, h);
 #pragma unroll

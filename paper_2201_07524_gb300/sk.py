@@ -26,7 +26,7 @@ SK_FP32, SK_FP64 = 0, 1
 SK_METHOD_NFFT, SK_METHOD_DIRECT = 0, 1
 SK_DOMAIN_SCALING, SK_DOMAIN_LOG = 0, 1
 SK_KERNELS_SIMT, SK_KERNELS_TENSOR = 0, 1
-SK_FAULT_NONE, SK_FAULT_TC_WAIT = 0, 1
+SK_FAULT_NONE, SK_FAULT_TC_WAIT, SK_FAULT_FFT_WAIT = 0, 1, 2
 SK_SET_X, SK_SET_Y = 0, 1
 SK_STAGE_SPREAD, SK_STAGE_FFT, SK_STAGE_INTERP, SK_STAGE_OTHER, SK_STAGE_DIRECT, SK_STAGE_NEAR = 0, 1, 2, 3, 4, 5
 SK_NSTAGES = 6
@@ -51,7 +51,8 @@ class sk_info(ctypes.Structure):
                 ("nearfield", ctypes.c_int), ("eps", ctypes.c_double), ("r", ctypes.c_double),
                 ("eps_scaled", ctypes.c_double), ("center", ctypes.c_double * 3), ("scale", ctypes.c_double),
                 ("eps_B", ctypes.c_double), ("eps_I", ctypes.c_double), ("n_subproblems_x", ctypes.c_int),
-                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("tensor_cores", ctypes.c_int)]
+                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("tensor_cores", ctypes.c_int),
+                ("fft_persistent", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -83,9 +84,13 @@ _SIGS = {
     "sk_fourier_coefficients": (ctypes.c_int, [_P, _D, _S]),
     "sk_adjoint_nfft": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
     "sk_nfft": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
+    "sk_spectrum": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
+    "sk_apply_spectrum": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
     "sk_stage_times": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64)]),
     "sk_launch_count": (ctypes.c_int64, [_P]),
+    "sk_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int), _S]),
     "sk_direct_residual_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _D, _D, _D, ctypes.c_int64, _D, _D,
                                                   ctypes.c_double, ctypes.c_double, _D, _D, _S]),
 }
@@ -324,6 +329,28 @@ def sk_nfft(plan, which, fhat, f, stream=None):
     return f
 
 
+def spectrum_size(plan):
+    """Number of complex values of a spectrum of this plan, (N+1)^d."""
+    info = sk_plan_info(plan)
+    return (info["N"] + 1) ** info["d"]
+
+
+def sk_spectrum(plan, which, w, spec, stream=None):
+    """Adjoint NFFT of w on cloud `which` into spec ((N+1)^d interleaved complex); see include/sk.h."""
+    n = plan.n if which == SK_SET_X else plan.m
+    _check(_lib.sk_spectrum(plan.handle, int(which), _ptr(w, n, "w"), _ptr(spec, 2 * spectrum_size(plan), "spec"),
+                            _stream(stream)), "sk_spectrum")
+    return spec
+
+
+def sk_apply_spectrum(plan, which, spec, out, stream=None):
+    """Outer sum of Eq. (fastsum) with the plan's b_k, from a (summed) spectrum, at cloud `which`."""
+    n = plan.n if which == SK_SET_X else plan.m
+    _check(_lib.sk_apply_spectrum(plan.handle, int(which), _ptr(spec, 2 * spectrum_size(plan), "spec"),
+                                  _ptr(out, n, "out"), _stream(stream)), "sk_apply_spectrum")
+    return out
+
+
 def sk_stage_times(plan, enable):
     ms = (ctypes.c_double * SK_NSTAGES)()
     cnt = (ctypes.c_int64 * SK_NSTAGES)()
@@ -333,6 +360,15 @@ def sk_stage_times(plan, enable):
 
 def sk_launch_count(plan):
     return int(_lib.sk_launch_count(plan.handle))
+
+
+def sk_fp32_peak(packed=False, iters=20000, stream=None):
+    """Measured FP32 FMA rate of the current device: (TFLOP/s, SM count)."""
+    tf = ctypes.c_double(0.0)
+    sms = ctypes.c_int(0)
+    _check(_lib.sk_fp32_peak(int(bool(packed)), int(iters), ctypes.byref(tf), ctypes.byref(sms), _stream(stream)),
+           "sk_fp32_peak")
+    return tf.value, sms.value
 
 
 def sk_direct_residual_noalloc(x, u, a, y, v, eps, r, t_out, stats_out, stream=None):

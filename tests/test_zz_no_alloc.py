@@ -35,9 +35,12 @@ def _call(x, u, a, y, v, eps, r, t_out, stats):
                                               v.data_ptr(), eps, r, t_out.data_ptr(), stats.data_ptr(), None)
 
 
-@pytest.mark.parametrize("d,r", [(3, 2.0), (2, 1.0)])
-def test_noalloc_matches_plan_direct_method_twice(d, r):
-    n, m, eps = 3001, 2499, 0.02
+@pytest.mark.parametrize("d,r,n,m", [(3, 2.0, 3001, 2499), (2, 1.0, 3001, 2499), (1, 2.0, 3001, 2499),
+                                     (3, 1.5, 3001, 2499),
+                                     # n at the scratch limit: 4096 blocks share the ticket and the partials
+                                     (3, 2.0, 2097152, 300)])
+def test_noalloc_matches_plan_direct_method_twice(d, r, n, m):
+    eps = 0.02
     xh = wl.uniform_ball(n, d, 0.2, 91)
     yh = wl.uniform_ball(m, d, 0.2, 92)
     ah, bh = wl.uniform_weights(n), wl.uniform_weights(m)
@@ -80,4 +83,27 @@ def test_noalloc_rejects_oversize_and_host_buffers():
     host = np.zeros(8)
     st = lib.sk_direct_residual_noalloc(2, 4, host.ctypes.data, one.data_ptr(), one.data_ptr(), 4, x.data_ptr(),
                                         one.data_ptr(), 0.05, 2.0, t_out.data_ptr(), stats.data_ptr(), None)
+    assert st == sk.SK_ERR_ARG
+
+
+def test_noalloc_rejects_overlapping_outputs():
+    n, m = 64, 32
+    x = _dev(wl.uniform_ball(n, 2, 0.2, 5))
+    y = _dev(wl.uniform_ball(m, 2, 0.2, 6))
+    u, a = _dev(np.ones(n)), _dev(np.full(n, 1.0 / n))
+    v = _dev(np.ones(m))
+    t_out = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stats = torch.zeros(2, dtype=torch.float64, device="cuda")
+    lib = sk._lib
+    # t_out on top of u, then stats_out inside t_out: refused on the host, nothing launched
+    st = lib.sk_direct_residual_noalloc(2, n, x.data_ptr(), u.data_ptr(), a.data_ptr(), m, y.data_ptr(),
+                                        v.data_ptr(), 0.05, 2.0, u.data_ptr(), stats.data_ptr(), None)
+    assert st == sk.SK_ERR_ARG
+    st = lib.sk_direct_residual_noalloc(2, n, x.data_ptr(), u.data_ptr(), a.data_ptr(), m, y.data_ptr(),
+                                        v.data_ptr(), 0.05, 2.0, t_out.data_ptr(), t_out.data_ptr() + 8, None)
+    assert st == sk.SK_ERR_ARG
+    # pinned host memory is not device memory either
+    pinned = torch.zeros(n, dtype=torch.float64).pin_memory()
+    st = lib.sk_direct_residual_noalloc(2, n, x.data_ptr(), u.data_ptr(), a.data_ptr(), m, y.data_ptr(),
+                                        v.data_ptr(), 0.05, 2.0, pinned.data_ptr(), stats.data_ptr(), None)
     assert st == sk.SK_ERR_ARG
