@@ -55,5 +55,7 @@ def test_value_at_2e4_matches_fp64_oracle(golden, method):
     # the state itself: the first scaling values in caller order
     assert np.allclose(u[:8], g["u_head"], rtol=1e-4, atol=0)
     assert np.allclose(v[:8], g["v_head"], rtol=1e-4, atol=0)
-    # Eq. (Error) residuals of the returned state agree with the oracle's
-    assert res["err_row"] == pytest.approx(g["err_row"], rel=1e-3, abs=1e-9)
+    # the oracle's state is converged (row residual of Eq. (Error) ~1e-14 of
+    # ||a||); the GPU state is too, to the precision of its FP32 sums
+    assert g["err_row"] <= 1e-10 * np.linalg.norm(a)
+    assert res["err_row"] <= 1e-5 * np.linalg.norm(a)
