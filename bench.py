@@ -622,6 +622,127 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_grad(args):
+    """The differentiation workload: Sinkhorn divergence S = s(x, y) - s(x, x)/2
+    - s(y, y)/2 and its gradient with respect to the weights and positions
+    (sk_divergence, FP32 fast summation), n = m = 2^18 points of two
+    8-component Gaussian mixtures in R^3 (sigma 0.03, means in a radius-0.15
+    ball), uniform weights, r = 2, eps = 0.02, 200 iterations per solve.
+
+    The gradient is the envelope gradient of the dual at the final state (the
+    gradient of the converged value).  It is checked by central differences
+    with step 1e-4 on 64 random position coordinates: each difference solves
+    s(x', y) and s(x', x') with FP64 fast summation from the unperturbed
+    converged state until the row residual is below 1e-13, all plans on one
+    fixed torus geometry.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2201_07524_gb300 import sk
+    from paper_2201_07524_gb300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    T = lambda z: torch.as_tensor(np.ascontiguousarray(z), dtype=torch.float64, device=dev)
+    n, d, eps, r, iters, h, ncoord = 2 ** 18, 3, 0.02, 2.0, 200, 1e-4, 64
+    x = wl.gaussian_mixture(n, d, 8, 0.03, 0.15, 11)
+    y = wl.gaussian_mixture(n, d, 8, 0.03, 0.15, 12)
+    a, b = wl.uniform_weights(n), wl.uniform_weights(n)
+    # one geometry for every plan, with room for the perturbed points
+    pts = np.concatenate([x, y])
+    c = 0.5 * (pts.min(0) + pts.max(0))
+    scale = (0.25 - 0.05) / (np.max(np.linalg.norm(pts - c, axis=1)) + 1e-3)
+
+    def params(precision):
+        prm = sk.sk_default_params(N=64, m_w=4, precision=precision)
+        prm.user_geometry = 1
+        prm.scale = float(scale)
+        for t in range(3):
+            prm.center[t] = float(c[t])
+        return prm
+
+    xd, yd, ad, bd = T(x), T(y), T(a), T(b)
+    grads = {}
+
+    def divergence(precision):
+        ga, gb = torch.zeros(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev)
+        gx, gy = torch.zeros((n, d), dtype=torch.float64, device=dev), torch.zeros((n, d), dtype=torch.float64,
+                                                                                  device=dev)
+        out = sk.sk_divergence(xd, ad, yd, bd, eps, r, iters, 0.0, params(precision), grad_a=ga, grad_b=gb,
+                               grad_x=gx, grad_y=gy)
+        return out, gx, ga
+
+    divergence(sk.SK_FP32)                                        # warm-up
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps)
+    t_wall = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(reps):
+        out32, gx32, ga32 = divergence(sk.SK_FP32)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall
+    ms = ev0.elapsed_time(ev1) / reps
+    t0 = time.perf_counter()
+    out64, gx64, ga64 = divergence(sk.SK_FP64)
+    torch.cuda.synchronize(dev)
+    fp64_s = time.perf_counter() - t0
+
+    # the converged FP64 states of the two terms that depend on x
+    def solve(xp, yp, u0=None, v0=None, tol=0.0, max_iter=iters):
+        pl = sk.sk_init(T(xp), ad, T(yp), bd if yp is y else ad, eps, r, params(sk.SK_FP64))
+        if u0 is not None:
+            sk.sk_set_state(pl, u0, v0)
+        st, res = sk.sk_solve(pl, max_iter, tol=tol, check_every=5)
+        u, v = np.zeros(n), np.zeros(n)
+        sk.sk_get_state(pl, u, v)
+        pl.close()
+        return res, u, v
+
+    res_xy, u_xy, v_xy = solve(x, y)
+    res_xx, u_xx, v_xx = solve(x, x)
+    rng = np.random.default_rng(13)
+    coords = [(int(i), int(t)) for i, t in zip(rng.choice(n, ncoord, replace=False), rng.integers(0, d, ncoord))]
+    fd = []
+    t0 = time.perf_counter()
+    for i, t in coords:
+        vals = []
+        for sgn in (1.0, -1.0):
+            xp = x.copy()
+            xp[i, t] += sgn * h
+            rxy, _, _ = solve(xp, y, u_xy, v_xy, tol=1e-13, max_iter=400)
+            rxx, _, _ = solve(xp, xp, u_xx, v_xx, tol=1e-13, max_iter=400)
+            vals.append(rxy["s"] - 0.5 * rxx["s"])                 # s(y, y) does not depend on x
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd_s = time.perf_counter() - t0
+    fd = np.array(fd)
+    g64 = np.array([gx64[i, t].item() for i, t in coords])
+    g32 = np.array([gx32[i, t].item() for i, t in coords])
+    scale_g = np.max(np.abs(fd))
+    line = {
+        "metric": "Sinkhorn divergence + gradient evaluations/s (n=m=2^18, d=3, 200 iterations per solve)",
+        "value": 1e3 / ms, "unit": "evals/s", "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "grad_gmm3d_n2^18_eps0.02", "n": n, "m": n, "d": d, "r": r, "eps": eps,
+                   "iters": iters, "N": 64, "m_w": 4,
+                   "points": "8-component Gaussian mixtures (sigma 0.03, means uniform in a radius-0.15 ball), "
+                             "seeds 11 (x) and 12 (y), uniform weights"},
+        "iterations_per_s": 3 * iters * 1e3 / ms,
+        "value_fp32": out32[0], "value_fp64": out64[0],
+        "value_rel_err_fp32_vs_fp64": abs(out32[0] - out64[0]) / abs(out64[0]),
+        "residual_after_200": {"s_xy_err_row": res_xy["err_row"], "s_xx_err_row": res_xx["err_row"],
+                               "norm_a": float(np.linalg.norm(a))},
+        "fd": {"coords": ncoord, "step": h, "solves": 4 * ncoord, "seconds": fd_s,
+               "max_abs_fd": float(scale_g),
+               "max_err_fp64_grad": float(np.max(np.abs(g64 - fd)) / scale_g),
+               "max_err_fp32_grad": float(np.max(np.abs(g32 - fd)) / scale_g),
+               "errors_relative_to": "max |finite difference| over the 64 coordinates"},
+        "grad_fp32_vs_fp64": {"x_max_rel": float((gx32 - gx64).abs().max().item() / gx64.abs().max().item()),
+                              "a_max_rel": float((ga32 - ga64).abs().max().item() / ga64.abs().max().item())},
+        "fp64_divergence_s": fp64_s, "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,9 +754,10 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=8, help="oracle rows (and columns) per host core")
     ap.add_argument("--ref-rows", type=int, default=8, help="reference arm: oracle rows (and columns) per core")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
-    ap.add_argument("--workload", default="headline", choices=["headline", "gmm2d", "r1", "batch"],
+    ap.add_argument("--workload", default="headline", choices=["headline", "gmm2d", "r1", "batch", "grad"],
                     help="headline: the 1e6-point 3-D workload; gmm2d: the 1e6-point 2-D Gaussian mixture; "
-                         "r1: the 4e6-point 3-D workload with r = 1 (near field); batch: --batch independent problems")
+                         "r1: the 4e6-point 3-D workload with r = 1 (near field); batch: --batch independent problems; "
+                         "grad: Sinkhorn divergence and its gradient at 2^18 points, checked by finite differences")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--autotune", action="store_true",
                     help="batch: let sk_autotune pick each plan's interpolation kernels (measured no faster)")
@@ -655,6 +777,9 @@ def main():
         elif args.workload == "batch":
             if rank == 0:
                 run_batch(args)
+        elif args.workload == "grad":
+            if rank == 0:
+                run_grad(args)
         else:
             run_ours(args, rank, world)
     finally:

@@ -650,7 +650,9 @@ __global__ void __launch_bounds__(kCoopWarps * 32, 1) k_fft3_convolve_coop(FftPl
     C* buf = tw + n / 2 + warp * P * ns;
     load_twiddles(tw, static_cast<const C*>(f.tw), n);
     __syncthreads();
-    const int64_t gw = int64_t(blockIdx.x) * kCoopWarps + warp, nw = int64_t(gridDim.x) * kCoopWarps;
+    // units go round-robin over the blocks first, so a pass with fewer units
+    // than warps still spreads them over every SM
+    const int64_t gw = int64_t(warp) * gridDim.x + blockIdx.x, nw = int64_t(gridDim.x) * kCoopWarps;
     const int64_t H = f.h + 1, K = 2 * f.h + 1;
     const int64_t xlo = f.lo[0], xcnt = f.hi[0] - f.lo[0] + 1;
     const int ylo = f.lo[1] & ~1, ycnt = (f.hi[1] | 1) - ylo + 1;

@@ -563,7 +563,10 @@ def test_launch_count_and_stage_timing():
     sk.sk_solve(plan, 4, result=False)
     torch.cuda.synchronize()
     per_iter = (sk.sk_launch_count(plan) - c0) / 4
-    assert per_iter == 2 * (1 + 5 + 1)        # spread, 5 FFT passes, interp per half-step (3-D)
+    # per half-step: spread, the FFT (one persistent launch for the five passes
+    # of a 3-D FP32 plan with n_os <= 256), interp
+    assert sk.sk_plan_info(plan)["fft_persistent"] == 1
+    assert per_iter == 2 * (1 + 1 + 1)
     sk.sk_stage_times(plan, 1)
     sk.sk_solve(plan, 3, result=False)
     times = sk.sk_stage_times(plan, 0)
