@@ -54,7 +54,7 @@ enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / in
 enum { SK_METHOD_NFFT = 0, SK_METHOD_DIRECT = 1 };
 enum { SK_DOMAIN_SCALING = 0, SK_DOMAIN_LOG = 1 };   /* state of the iteration: Alg. 3 or Alg. 4 */
 enum { SK_KERNELS_SIMT = 0, SK_KERNELS_TENSOR = 1 };   /* interpolation on CUDA cores or tensor cores */
-enum { SK_FAULT_NONE = 0, SK_FAULT_TC_WAIT = 1, SK_FAULT_FFT_WAIT = 2 };   /* sk_inject_fault (test hook) */
+enum { SK_FAULT_NONE = 0, SK_FAULT_TC_WAIT = 1 };      /* sk_inject_fault (test hook) */
 enum { SK_SET_X = 0, SK_SET_Y = 1 };        /* which point cloud a stage entry point acts on */
 
 typedef struct sk_plan sk_plan;
@@ -124,8 +124,6 @@ typedef struct {
     int n_subproblems_x, n_subproblems_y;   /* work items of the per-point spreading kernels (1-D; 3-D with m_w > 5) */
     int64_t device_bytes;        /* device memory the plan holds */
     int tensor_cores;            /* 1: interpolation runs on tensor cores (sk_set_kernels) */
-    int fft_persistent;          /* 1: a product's five FFT passes run as one cooperative launch (3-D
-                                    FP32 plans with n_os <= 256, outside sk_solve_batch) */
 } sk_info;
 
 /* Text for a status code (static storage, never NULL). */
@@ -217,15 +215,8 @@ int sk_autotune(sk_plan* plan, int* chosen, void* stream);
  * SK_ERR_TIMEOUT when they read results back (the state of that solve is not
  * meaningful).  SK_FAULT_NONE restores normal operation.  Nothing faults or
  * hangs either way.
- * SK_FAULT_FFT_WAIT does the same for the persistent 3-D FFT (one cooperative
- * launch for the five passes of a product, whose blocks meet at grid-wide
- * barriers): its first barrier waits for one arrival more than the grid has,
- * so every block's bounded wait (about a second) runs out, the kernel skips
- * its remaining passes, and sk_solve returns SK_ERR_TIMEOUT.
  * Errors: SK_ERR_ARG for a NULL plan or an unknown kind; SK_ERR_UNSUPPORTED
- * for SK_FAULT_TC_WAIT when the plan does not interpolate on tensor cores, and
- * for SK_FAULT_FFT_WAIT when its products do not use the persistent FFT
- * (sk_info.fft_persistent = 0, or the direct method).
+ * for SK_FAULT_TC_WAIT when the plan does not interpolate on tensor cores.
  */
 int sk_inject_fault(sk_plan* plan, int kind);
 

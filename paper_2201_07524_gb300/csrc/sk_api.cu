@@ -725,15 +725,6 @@ void prepare_kernels(sk_plan* P) {
         ia.nttasks = 0;
         CK(launch_interp_tc(P->d, P->W, ia, Epilogue{}, P->ps));
     }
-    // the persistent 3-D convolution where it applies; its first launch runs
-    // on the zero grid, and a launch the device refuses leaves the pass kernels
-    P->fft.bar = P->ticket + 6;
-    P->fft.status = P->status;
-    P->fft.coop_blocks = fft_coop_blocks<T>(P->fft);
-    if (P->fft.coop_blocks > 0 && launch_fft_convolve<T>(P->fft, P->ps, nullptr) != cudaSuccess) {
-        cudaGetLastError();
-        P->fft.coop_blocks = 0;
-    }
     CK(launch_fft_convolve<T>(P->fft, P->ps, nullptr));   // runs once on the zero grid
 }
 
@@ -1284,7 +1275,7 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         const int64_t nmax = std::max(n, m);
         P->partial_blocks = std::max<int64_t>(interp_blocks<double>(nmax), kRedBlocks);
         P->partial = static_cast<double*>(dalloc(P, size_t(P->partial_blocks) * 8 * sizeof(double)));
-        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 8));   // [0] reductions, [2..3] interpolation queue, [4..5] spreading queue, [6..7] FFT grid barrier
+        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 8));   // [0] reductions, [2..3] interpolation queue, [4..5] spreading queue
         P->stats = static_cast<double*>(dalloc(P, sizeof(double) * (3 * NSLOTS + 8)));
         P->status = static_cast<int*>(dalloc(P, sizeof(int) * 4));
         P->shift = static_cast<double*>(dalloc(P, sizeof(double) * 2));
@@ -1529,14 +1520,11 @@ int sk_autotune(sk_plan* P, int* chosen, void* stream) {
 }
 
 int sk_inject_fault(sk_plan* P, int kind) {
-    if (!P || (kind != SK_FAULT_NONE && kind != SK_FAULT_TC_WAIT && kind != SK_FAULT_FFT_WAIT)) return SK_ERR_ARG;
+    if (!P || (kind != SK_FAULT_NONE && kind != SK_FAULT_TC_WAIT)) return SK_ERR_ARG;
     if (kind == SK_FAULT_TC_WAIT && !P->tc) return SK_ERR_UNSUPPORTED;
-    if (kind == SK_FAULT_FFT_WAIT && (P->fft.coop_blocks <= 0 || P->method != SK_METHOD_NFFT))
-        return SK_ERR_UNSUPPORTED;
     if (kind != P->inject) {
         destroy_graph(P);
         P->inject = kind;
-        P->fft.inject = kind == SK_FAULT_FFT_WAIT ? 1 : 0;
     }
     return SK_OK;
 }
@@ -1668,17 +1656,7 @@ int sk_solve_batch(sk_plan* const* plans, int count, int max_iter, sk_result* re
                     sk_plan* P = plans[i];
                     CK(cudaStreamWaitEvent(P->ps, fork, 0));
                     const int64_t before = P->launches;
-                    // the branches run side by side: the persistent FFT, which
-                    // wants every SM, gives way to the pass kernels here
-                    const int coop = P->fft.coop_blocks;
-                    P->fft.coop_blocks = 0;
-                    try {
-                        run_iteration(P);
-                    } catch (...) {
-                        P->fft.coop_blocks = coop;
-                        throw;
-                    }
-                    P->fft.coop_blocks = coop;
+                    run_iteration(P);
                     kernels[size_t(i)] = P->launches - before;
                     P->launches = before;
                     CK(cudaEventRecord(join[size_t(i)], P->ps));
@@ -1908,7 +1886,6 @@ int sk_plan_info(const sk_plan* P, sk_info* info) {
     info->n_subproblems_y = P->Y.nsub;
     info->device_bytes = P->bytes;
     info->tensor_cores = P->tc ? 1 : 0;
-    info->fft_persistent = P->fft.coop_blocks > 0 ? 1 : 0;
     return SK_OK;
 }
 

@@ -68,10 +68,26 @@ struct RowPairs {
     int64_t npairs;
 };
 
-__device__ __forceinline__ int64_t pair_row(const RowPairs& rp, int64_t q) {
-    const int64_t o = rp.olo + q / rp.npo;
-    return o * rp.ostride + rp.ylo + 2 * (q % rp.npo);
+__device__ __forceinline__ int64_t pair_row(const RowPairs& rp, int q) {
+    const int qo = q / rp.npo;   // 32-bit: the row pairs of a grid fit in an int
+    return (rp.olo + qo) * rp.ostride + rp.ylo + 2 * (q - qo * rp.npo);
 }
+
+// pair_row of row pair q, recomputed only when q changes (the elements a
+// thread visits come in non-decreasing pair order).
+struct PairRowCache {
+    int q = -1;
+    int64_t row = 0;
+    __device__ __forceinline__ int64_t get(const RowPairs& rp, int qn) {
+        if (qn != q) {
+            q = qn;
+            row = pair_row(rp, qn);
+        }
+        return row;
+    }
+};
+
+__device__ __forceinline__ int ilog2(int p) { return __ffs(p) - 1; }   // p a power of two
 
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
@@ -161,13 +177,9 @@ __device__ __forceinline__ void dft8(C* x) {
     }
 }
 
-// Barriers of an FFT unit: a whole block (the pass kernels), or one warp (a
-// unit of 32 threads inside the persistent kernel).
+// The barrier of an FFT unit (the block of a pass kernel).
 struct SyncBlock {
     __device__ __forceinline__ static void sync() { __syncthreads(); }
-};
-struct SyncWarp {
-    __device__ __forceinline__ static void sync() { __syncwarp(); }
 };
 
 // One Stockham stage of radix R on the thread's E elements (E/R butterflies):
@@ -254,35 +266,38 @@ __device__ __forceinline__ void load_twiddles(C* dst, const C* __restrict__ src,
 constexpr int kFftLoadsPerRound = 8;
 
 // The passes below are written for one FFT unit: `nthr` threads (a block of a
-// pass kernel, or a warp of the persistent kernel) that transform the P
-// pencils starting at pencil (or row pair) q0, thread `tid` of the unit,
-// staging in `buf` (P pencils of fft_stride(n) slots).  Data written by an
-// earlier pass is loaded with ld.global.cg (L2, not L1), so a persistent
-// kernel that runs several passes never reads a stale line from L1.
+// pass kernel) that transform the P pencils starting at pencil (or row pair)
+// q0, thread `tid` of the unit, staging in `buf` (P pencils of fft_stride(n)
+// slots), with its barrier S::sync().  Data written by the previous pass is
+// read once, with ld.global.cg (cached in L2 only).  Index arithmetic is
+// 32-bit and free of divisions in the per-element loops (the pencil a thread
+// works on is fixed per unit, the pencil count P is a power of two): a 64-bit
+// division per element had made every pass several microseconds slower.
 
 // Two real rows of length n -> two half spectra of length h+1 (output rows
 // are the same row indices in A1).  The input rows are zeroed after reading.
 template <typename T, class S>
 __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
                                          const RowPairs& rp, int n, int log2n, int h,
-                                         const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf, int64_t q0,
+                                         const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf, int q0,
                                          int tid, int nthr) {
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n);
     const int ns = fft_stride(n);
     S::sync();   // the unit's previous pencils have been read out of buf
+    PairRowCache rc;
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * nthr) {
         C z[kFftLoadsPerRound];
         int64_t at[kFftLoadsPerRound];
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = e0 + j * nthr + tid;
-            const int64_t q = q0 + (e >> log2n);
+            const int q = q0 + (e >> log2n);
             z[j].x = T(0);
             z[j].y = T(0);
             at[j] = -1;
             if (e < P * n && q < rp.npairs) {
-                at[j] = pair_row(rp, q) * n + (e & (n - 1));
+                at[j] = rc.get(rp, q) * n + (e & (n - 1));
                 z[j].x = __ldcg(g + at[j]);
                 z[j].y = __ldcg(g + at[j] + n);
             }
@@ -300,21 +315,29 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
     }
     fft_stockham<T, false, S>(buf, ns, n, log2n, tw, tid);
     const int H = h + 1;
+    // element e = p H + k of the output, walked without a division per element
+    int p = tid / H, k = tid - (tid / H) * H;
+    const int kstep = nthr % H, pstep = nthr / H;
     for (int e = tid; e < P * H; e += nthr) {
-        const int p = e / H;
-        const int k = e - p * H;
-        const int64_t q = q0 + p;
-        if (q >= rp.npairs) continue;
-        const int64_t r0 = pair_row(rp, q);
-        const C zk = buf[p * ns + pidx(k)];
-        const C zm = buf[p * ns + pidx((n - k) & (n - 1))];
-        C A, Bv;
-        A.x = (zk.x + zm.x) * T(0.5);
-        A.y = (zk.y - zm.y) * T(0.5);
-        Bv.x = (zk.y + zm.y) * T(0.5);
-        Bv.y = (zm.x - zk.x) * T(0.5);
-        out[r0 * H + k] = A;
-        out[(r0 + 1) * H + k] = Bv;
+        const int q = q0 + p;
+        if (q < rp.npairs) {
+            const int64_t r0 = rc.get(rp, q);
+            const C zk = buf[p * ns + pidx(k)];
+            const C zm = buf[p * ns + pidx((n - k) & (n - 1))];
+            C A, Bv;
+            A.x = (zk.x + zm.x) * T(0.5);
+            A.y = (zk.y - zm.y) * T(0.5);
+            Bv.x = (zk.y + zm.y) * T(0.5);
+            Bv.y = (zm.x - zk.x) * T(0.5);
+            out[r0 * H + k] = A;
+            out[(r0 + 1) * H + k] = Bv;
+        }
+        k += kstep;
+        p += pstep;
+        if (k >= H) {
+            k -= H;
+            ++p;
+        }
     }
 }
 
@@ -322,13 +345,14 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
 template <typename T, class S>
 __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
                                          const RowPairs& rp, int n, int log2n, int h,
-                                         const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf, int64_t q0,
+                                         const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf, int q0,
                                          int tid, int nthr) {
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n);
     const int ns = fft_stride(n);
     S::sync();   // the unit's previous pencils have been read out of buf
     const int H = h + 1;
+    PairRowCache rc;
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * nthr) {
         C A[kFftLoadsPerRound], Bv[kFftLoadsPerRound];
         int sgn[kFftLoadsPerRound];   // +1: k in 0..h, -1: -k in 1..h, 0: outside (zero)
@@ -336,12 +360,12 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = e0 + j * nthr + tid;
             const int pos = e & (n - 1);
-            const int64_t q = q0 + (e >> log2n);
+            const int q = q0 + (e >> log2n);
             const int k = pos <= (n >> 1) ? pos : pos - n;
             sgn[j] = 0;
             A[j].x = A[j].y = Bv[j].x = Bv[j].y = T(0);
             if (e < P * n && q < rp.npairs && k >= -h && k <= h) {
-                const int64_t r0 = pair_row(rp, q);
+                const int64_t r0 = rc.get(rp, q);
                 const int ka = k >= 0 ? k : -k;
                 sgn[j] = k >= 0 ? 1 : -1;
                 A[j] = __ldcg(in + r0 * H + ka);
@@ -375,9 +399,9 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
     for (int e = tid; e < P * n; e += nthr) {
         const int p = e >> log2n;
         const int l = e & (n - 1);
-        const int64_t q = q0 + p;
+        const int q = q0 + p;
         if (q >= rp.npairs) continue;
-        const int64_t r0 = pair_row(rp, q);
+        const int64_t r0 = rc.get(rp, q);
         const C v = buf[p * ns + pidx(l)];
         g[r0 * n + l] = v.x;
         g[(r0 + 1) * n + l] = v.y;
@@ -391,19 +415,27 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
 // k in [klo, klo + kcnt).
 template <typename T, int INM, int OUTM, bool INV, class S>
 __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restrict__ in,
-                                          typename Cplx<T>::type* __restrict__ out, int64_t olo, int64_t ocnt,
-                                          int64_t I, int klo, int kcnt, int n, int log2n, int h,
-                                          const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf, int64_t q0,
-                                          int tid, int nthr) {
+                                          typename Cplx<T>::type* __restrict__ out, int olo, int ocnt, int I, int klo,
+                                          int kcnt, int n, int log2n, int h, const typename Cplx<T>::type* tw,
+                                          typename Cplx<T>::type* buf, int q0, int tid, int nthr) {
     using C = typename Cplx<T>::type;
-    const int P = fft_pencils(n);
+    const int P = fft_pencils(n), lp = ilog2(P);
     const int ns = fft_stride(n);
-    S::sync();   // the unit's previous pencils have been read out of buf
-    const int64_t Q = ocnt * I;
+    const int Q = ocnt * I;
     const int Lin = INM == FULL ? n : 2 * h + 1;
     const int Lout = OUTM == FULL ? n : 2 * h + 1;
     const int k0 = OUTM == FULL ? klo : 0;
     const int kn = OUTM == FULL ? kcnt : Lout;
+    S::sync();   // the unit's previous pencils have been read out of buf
+    // the unit's threads are a multiple of P, so a thread always works on
+    // pencil pl = tid mod P of the unit: pencil (o, i), o = olo + q / I
+    const int pl = tid & (P - 1);
+    const int q = q0 + pl;
+    const bool qok = q < Q;
+    const int qo = qok ? q / I : 0;
+    const int64_t o = olo + qo, i = q - qo * I;
+    const C* src = in + o * Lin * I + i;
+    C* dst = out + o * Lout * I + i;
     if (INM == CENTERED) {
         for (int e = tid; e < P * ns; e += nthr) {
             buf[e].x = T(0);
@@ -417,30 +449,25 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = e0 + j * nthr + tid;
-            const int k = e / P;
-            const int64_t q = q0 + (e - k * P);
-            ok[j] = e < P * Lin && q < Q;
-            if (ok[j]) v[j] = __ldcg(in + ((olo + q / I) * Lin + k) * I + q % I);
+            const int k = e >> lp;
+            ok[j] = e < P * Lin && qok;
+            if (ok[j]) v[j] = __ldcg(src + int64_t(k) * I);
         }
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             if (!ok[j]) continue;
             const int e = e0 + j * nthr + tid;
-            const int k = e / P;
+            const int k = e >> lp;
             const int pos = INM == FULL ? k : ((k - h) & (n - 1));
-            buf[(e - k * P) * ns + pidx(pos)] = v[j];
+            buf[pl * ns + pidx(pos)] = v[j];
         }
     }
     fft_stockham<T, INV, S>(buf, ns, n, log2n, tw, tid);
+    if (!qok) return;
     for (int e = tid; e < P * kn; e += nthr) {
-        const int kk = e / P;
-        const int pl = e - kk * P;
-        const int64_t q = q0 + pl;
-        if (q >= Q) continue;
-        const int k = k0 + kk;
-        const int64_t o = olo + q / I, i = q % I;
+        const int k = k0 + (e >> lp);
         const int pos = OUTM == FULL ? k : ((k - h) & (n - 1));
-        out[(o * Lout + k) * I + i] = buf[pl * ns + pidx(pos)];
+        dst[int64_t(k) * I] = buf[pl * ns + pidx(pos)];
     }
 }
 
@@ -449,12 +476,12 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
 // Only axis-0 positions in [xlo, xlo + xcnt) are loaded (the rest are zero)
 // and stored (the rest are never read).
 template <typename T, class S>
-__device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict__ data, int64_t I, int xlo, int xcnt,
+__device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict__ data, int I, int xlo, int xcnt,
                                               int n, int log2n, int h, const T* __restrict__ mult,
                                               const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf,
-                                              int64_t q0, int tid, int nthr) {
+                                              int q0, int tid, int nthr) {
     using C = typename Cplx<T>::type;
-    const int P = fft_pencils(n);
+    const int P = fft_pencils(n), lp = ilog2(P);
     const int ns = fft_stride(n);
     S::sync();   // the unit's previous pencils have been read out of buf
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * nthr) {
@@ -462,8 +489,8 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = e0 + j * nthr + tid;
-            const int k = e / P;
-            const int64_t q = q0 + (e - k * P);
+            const int k = e >> lp;
+            const int q = q0 + (e & (P - 1));
             v[j].x = T(0);
             v[j].y = T(0);
             if (e < P * n && q < I && k >= xlo && k < xlo + xcnt) v[j] = __ldcg(data + int64_t(k) * I + q);
@@ -472,8 +499,8 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = e0 + j * nthr + tid;
             if (e >= P * n) continue;
-            const int k = e / P;
-            buf[(e - k * P) * ns + pidx(k)] = v[j];
+            const int k = e >> lp;
+            buf[(e & (P - 1)) * ns + pidx(k)] = v[j];
         }
     }
     // when one round covers the unit, the multiplier of each element this
@@ -484,8 +511,8 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
 #pragma unroll
     for (int j = 0; j < kFftLoadsPerRound; ++j) {
         const int e = j * nthr + tid;
-        const int pos = e / P;
-        const int64_t q = q0 + (e - pos * P);
+        const int pos = e >> lp;
+        const int q = q0 + (e & (P - 1));
         const int k = pos <= (n >> 1) ? pos : pos - n;
         mv[j] = (one_round && e < P * n && q < I && k >= -h && k <= h) ? mult[int64_t(k + h) * I + q] : T(0);
     }
@@ -495,16 +522,16 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = j * nthr + tid;
             if (e >= P * n) continue;
-            const int pos = e / P;
-            C& v = buf[(e - pos * P) * ns + pidx(pos)];
+            const int pos = e >> lp;
+            C& v = buf[(e & (P - 1)) * ns + pidx(pos)];
             v.x *= mv[j];
             v.y *= mv[j];
         }
     } else {
         for (int e = tid; e < P * n; e += nthr) {
-            const int pos = e / P;
-            const int pl = e - pos * P;
-            const int64_t q = q0 + pl;
+            const int pos = e >> lp;
+            const int pl = e & (P - 1);
+            const int q = q0 + pl;
             const int k = pos <= (n >> 1) ? pos : pos - n;
             C& v = buf[pl * ns + pidx(pos)];
             if (q < I && k >= -h && k <= h) {
@@ -519,9 +546,9 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
     }
     fft_stockham<T, true, S>(buf, ns, n, log2n, tw, tid);
     for (int e = tid; e < P * xcnt; e += nthr) {
-        const int k = xlo + e / P;
-        const int pl = e % P;
-        const int64_t q = q0 + pl;
+        const int k = xlo + (e >> lp);
+        const int pl = e & (P - 1);
+        const int q = q0 + pl;
         if (q < I) data[int64_t(k) * I + q] = buf[pl * ns + pidx(k)];
     }
 }
@@ -535,7 +562,7 @@ __global__ void __launch_bounds__(512) k_fft_r2c_rows(T* __restrict__ g, typenam
                                                       const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm(n);
     load_twiddles(sm.tw, twg, n);
-    r2c_unit<T, SyncBlock>(g, out, rp, n, log2n, h, sm.tw, sm.buf, int64_t(blockIdx.x) * fft_pencils(n),
+    r2c_unit<T, SyncBlock>(g, out, rp, n, log2n, h, sm.tw, sm.buf, int(blockIdx.x) * fft_pencils(n),
                            int(threadIdx.x), int(blockDim.x));
 }
 
@@ -545,7 +572,7 @@ __global__ void __launch_bounds__(512) k_fft_c2r_rows(const typename Cplx<T>::ty
                                                       const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm(n);
     load_twiddles(sm.tw, twg, n);
-    c2r_unit<T, SyncBlock>(in, g, rp, n, log2n, h, sm.tw, sm.buf, int64_t(blockIdx.x) * fft_pencils(n),
+    c2r_unit<T, SyncBlock>(in, g, rp, n, log2n, h, sm.tw, sm.buf, int(blockIdx.x) * fft_pencils(n),
                            int(threadIdx.x), int(blockDim.x));
 }
 
@@ -556,8 +583,8 @@ __global__ void __launch_bounds__(512) k_fft_axis(const typename Cplx<T>::type* 
                                                   const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm(n);
     load_twiddles(sm.tw, twg, n);
-    axis_unit<T, INM, OUTM, INV, SyncBlock>(in, out, olo, ocnt, I, klo, kcnt, n, log2n, h, sm.tw, sm.buf,
-                                            int64_t(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
+    axis_unit<T, INM, OUTM, INV, SyncBlock>(in, out, int(olo), int(ocnt), int(I), klo, kcnt, n, log2n, h, sm.tw, sm.buf,
+                                            int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
 
 template <typename T>
@@ -567,125 +594,8 @@ __global__ void __launch_bounds__(512) k_fft_axis0_convolve(typename Cplx<T>::ty
                                                             const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm(n);
     load_twiddles(sm.tw, twg, n);
-    convolve_unit<T, SyncBlock>(data, I, xlo, xcnt, n, log2n, h, mult, sm.tw, sm.buf,
-                                int64_t(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
-}
-
-// ------------------------------------------------------------ persistent 3-D convolution
-// All five passes of a 3-D product in one cooperative launch: one block of
-// kCoopWarps = 16 warps per SM (so a thread may hold up to 128 registers),
-// every warp an FFT unit (FP32 pencils of up to 256
-// points: 32 threads), the twiddles loaded once per block.  Between passes
-// the grid meets at a barrier; each pass's units are spread over all warps
-// of the grid.  Every barrier wait is bounded.
-constexpr int kCoopWarps = 16;
-
-__device__ __forceinline__ unsigned long long fft_global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Barrier number k (1, 2, ...): every block arrives once, then its first
-// thread waits until all blocks have arrived k times.  The wait gives up
-// after about a second (the global timer) or 2^24 polls: the block then sets
-// bit 2 of the status word and the barrier returns false, so the kernel skips
-// its remaining passes (the other blocks' waits run out the same way).
-__device__ __forceinline__ bool coop_barrier(const FftPlan& f, unsigned k) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(f.bar, 1u);
-        const unsigned target = k * gridDim.x + (f.inject ? 1u : 0u);
-        bool good = false;
-        unsigned long long t0 = 0ull;
-        for (int it = 0; it < (1 << 24); ++it) {
-            if (ld_acquire_gpu(f.bar) >= target) {
-                good = true;
-                break;
-            }
-            if ((it & 63) == 0) {
-                const unsigned long long now = fft_global_ns();
-                if (it == 0) t0 = now;
-                else if (now - t0 > 1000000000ull) break;
-            }
-        }
-        if (!good && f.status) atomicOr(f.status, 4);
-        __threadfence();
-        ok = good ? 1 : 0;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// The last block to finish resets the barrier counters for the next launch
-// (by then every block has left every wait).
-__device__ __forceinline__ void coop_exit(const FftPlan& f) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(f.bar + 1, 1u) == gridDim.x - 1u) {
-            atomicExch(f.bar, 0u);
-            atomicExch(f.bar + 1, 0u);
-            __threadfence();
-        }
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kCoopWarps * 32, 1) k_fft3_convolve_coop(FftPlan f, RowPairs rp) {
-    using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    const int n = f.n, log2n = f.log2n, h = f.h;
-    const int P = fft_pencils(n), ns = fft_stride(n);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C* buf = tw + n / 2 + warp * P * ns;
-    load_twiddles(tw, static_cast<const C*>(f.tw), n);
-    __syncthreads();
-    // units go round-robin over the blocks first, so a pass with fewer units
-    // than warps still spreads them over every SM
-    const int64_t gw = int64_t(warp) * gridDim.x + blockIdx.x, nw = int64_t(gridDim.x) * kCoopWarps;
-    const int64_t H = f.h + 1, K = 2 * f.h + 1;
-    const int64_t xlo = f.lo[0], xcnt = f.hi[0] - f.lo[0] + 1;
-    const int ylo = f.lo[1] & ~1, ycnt = (f.hi[1] | 1) - ylo + 1;
-    C* A1 = static_cast<C*>(f.A1);
-    C* A2 = static_cast<C*>(f.A2);
-    // pass 1: real rows (z) -> half spectra, the spread grid zeroed behind
-    for (int64_t u = gw; u * P < rp.npairs; u += nw)
-        r2c_unit<T, SyncWarp>(static_cast<T*>(f.grid), A1, rp, n, log2n, h, tw, buf, u * P, lane, 32);
-    // pass 2: y, keep -h..h
-    if (coop_barrier(f, 1)) {
-        for (int64_t u = gw; u * P < xcnt * H; u += nw)
-            axis_unit<T, FULL, CENTERED, false, SyncWarp>(A1, A2, xlo, xcnt, H, 0, 0, n, log2n, h, tw, buf, u * P,
-                                                         lane, 32);
-        // pass 3: x, forward, multiply, inverse
-        if (coop_barrier(f, 2)) {
-            for (int64_t u = gw; u * P < K * H; u += nw)
-                convolve_unit<T, SyncWarp>(A2, K * H, int(xlo), int(xcnt), n, log2n, h,
-                                           static_cast<const T*>(f.mult), tw, buf, u * P, lane, 32);
-            // pass 4: inverse y, the band's row pairs only
-            if (coop_barrier(f, 3)) {
-                for (int64_t u = gw; u * P < xcnt * H; u += nw)
-                    axis_unit<T, CENTERED, FULL, true, SyncWarp>(A2, A1, xlo, xcnt, H, ylo, ycnt, n, log2n, h, tw,
-                                                                buf, u * P, lane, 32);
-                // pass 5: half spectra -> real rows of the interpolation grid
-                if (coop_barrier(f, 4)) {
-                    for (int64_t u = gw; u * P < rp.npairs; u += nw)
-                        c2r_unit<T, SyncWarp>(A1, static_cast<T*>(f.grid_out), rp, n, log2n, h, tw, buf, u * P,
-                                              lane, 32);
-                }
-            }
-        }
-    }
-    coop_exit(f);
+    convolve_unit<T, SyncBlock>(data, int(I), xlo, xcnt, n, log2n, h, mult, sm.tw, sm.buf,
+                                int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
 
 // 1-D: multiply the half spectrum of row 0 by M[k], k = 0..h.
@@ -872,30 +782,6 @@ static cudaError_t run_axis0_convolve(const FftPlan& f, void* data, int64_t I, i
     return cudaGetLastError();
 }
 
-// Shared memory of the persistent kernel: the twiddles, then one unit's
-// pencils per warp.
-template <typename T>
-static size_t coop_smem_bytes(int n) {
-    return (size_t(n / 2) + size_t(kCoopWarps) * fft_pencils(n) * fft_stride(n)) * sizeof(typename Cplx<T>::type);
-}
-
-template <typename T>
-int fft_coop_blocks(const FftPlan& f) {
-    if constexpr (sizeof(T) != 4) {
-        return 0;   // FP64 pencils take 64 threads per unit: the pass kernels
-    }
-    if (f.d != 3 || fft_threads<T>(f.n) != 32 || !f.bar) return 0;
-    int dev = 0, sms = 0, per_sm = 0;
-    const size_t smem = coop_smem_bytes<T>(f.n);
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
-        cudaFuncSetAttribute(k_fft3_convolve_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft3_convolve_coop<T>, kCoopWarps * 32, smem)) {
-        cudaGetLastError();
-        return 0;
-    }
-    return per_sm >= 1 ? sms : 0;
-}
-
 template <typename T>
 cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches) {
     using C = typename Cplx<T>::type;
@@ -912,23 +798,6 @@ cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launc
         SK_TRY(run_r2c<T>(f, launches, s));
         SK_TRY(run_axis0_convolve<T>(f, f.A1, H, launches, s));
         return run_c2r<T>(f, launches, s);
-    }
-    if constexpr (sizeof(T) == 4) {
-      if (f.coop_blocks > 0) {
-        const RowPairs rp = row_pairs(f);
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(unsigned(f.coop_blocks));
-        cfg.blockDim = dim3(kCoopWarps * 32);
-        cfg.dynamicSmemBytes = coop_smem_bytes<T>(f.n);
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        if (launches) ++*launches;
-        return cudaLaunchKernelEx(&cfg, k_fft3_convolve_coop<T>, f, rp);
-      }
     }
     const int64_t xlo = f.lo[0], xcnt = f.hi[0] - f.lo[0] + 1;
     const int ylo = f.lo[1] & ~1, ycnt = (f.hi[1] | 1) - ylo + 1;   // the row pairs of the real passes
@@ -992,8 +861,6 @@ cudaError_t launch_fft_forward(const FftPlan& f, const double* fhat, cudaStream_
     return run_c2r<T>(f, launches, s);
 }
 
-template int fft_coop_blocks<float>(const FftPlan&);
-template int fft_coop_blocks<double>(const FftPlan&);
 template cudaError_t launch_fft_convolve<float>(const FftPlan&, cudaStream_t, int64_t*);
 template cudaError_t launch_fft_convolve<double>(const FftPlan&, cudaStream_t, int64_t*);
 template cudaError_t launch_fft_adjoint<float>(const FftPlan&, double*, cudaStream_t, int64_t*);

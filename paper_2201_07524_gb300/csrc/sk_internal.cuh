@@ -220,11 +220,6 @@ struct FftPlan {
     void* mult = nullptr;     // T*
     void* tw = nullptr;       // Cplx<T>*, n/2 twiddles exp(-2 pi i k / n)
     const double* psihat = nullptr;  // 2h+1 values psihat_n(k/n), k = -h..h (FP64)
-    // persistent 3-D convolution (one cooperative launch for all five passes)
-    int coop_blocks = 0;      // its grid (one block per SM), 0 = five pass launches
-    unsigned* bar = nullptr;  // [0] barrier arrivals, [1] blocks finished; zero between launches
-    int* status = nullptr;    // bit 2 set when a grid barrier's bounded wait gave up
-    int inject = 0;           // test hook: 1 = the first barrier waits for one arrival too many
 };
 
 // ----------------------------------------------------------------- launchers
@@ -250,11 +245,6 @@ cudaError_t launch_interp_tc(int d, int W, const InterpArgs& a, const Epilogue& 
 int interp_tc_blocks(int d, int W, int ntasks);
 void bin_shape(int d, int W, int B[3]);
 template <typename T> cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches);
-// Grid of the persistent convolution kernel for this plan's FFT (one block
-// per SM, every block resident), or 0 where it does not apply (d != 3, or
-// pencils whose FFT unit is not one warp).  Sets the kernel's shared-memory
-// limit on the current device.
-template <typename T> int fft_coop_blocks(const FftPlan& f);
 template <typename T> cudaError_t launch_fft_adjoint(const FftPlan& f, double* fhat, cudaStream_t s,
                                                      int64_t* launches);
 template <typename T> cudaError_t launch_fft_forward(const FftPlan& f, const double* fhat, cudaStream_t s,

@@ -23,7 +23,6 @@
 //     each point's 32 lane partials through shared memory, and runs the FP64
 //     epilogue with one lane per point.
 #include <algorithm>
-#include <type_traits>
 #include <utility>
 
 #include "sk_internal.cuh"
@@ -31,17 +30,7 @@
 
 namespace sk {
 
-// Spreading of FP32 points with W = 8 adds its z-taps with packed FP32x2 FMAs
-// (two z-cells per instruction): the lane's accumulators are pairs of
-// adjacent z-cells, a point whose z-offset is even adds the weight pairs
-// (w0, w1), ..., (w6, w7), one whose offset is odd adds (0, w0), (w1, w2),
-// ..., (w7, 0) -- a copy of its z-weights shifted by one, kept in its table
-// row after the other weights (WZS).
-template <int W, typename T> struct PackedSpread {
-    static constexpr bool value = std::is_same<T, float>::value && W == 8;
-};
-
-template <int W, typename T = float, bool PK = false> struct Col3 {
+template <int W, typename T = float> struct Col3 {
     static constexpr int BX = 4, BY = 4, BZ = 8;
     static constexpr int NCOL = BX * BY;
     static constexpr int SX = BX + W - 1, SY = BY + W - 1, SZ = BZ + W - 1;
@@ -52,11 +41,9 @@ template <int W, typename T = float, bool PK = false> struct Col3 {
     static constexpr int VEC = 16 / int(sizeof(T));    // entries per 16-byte vector
     static constexpr int WP = (W + VEC - 1) / VEC * VEC;
     static constexpr int WZ = 0, WX = WP, WY = 2 * WP;
-    static constexpr int WZS = 3 * WP;                 // packed spreading only: (0, wz, 0), padded
-    static constexpr int WSP = PK ? (W + 2 + VEC - 1) / VEC * VEC : 0;
     // an odd number of 16-byte vectors per row keeps the vector stores of 8
     // consecutive lanes on distinct banks
-    static constexpr int NV = (3 * WP + WSP) / VEC;
+    static constexpr int NV = (3 * WP) / VEC;
     static constexpr int STRIDE = (NV % 2 == 1 ? NV : NV + 1) * VEC;
     static constexpr int SUB = SX * SY * SZ;
     // 16-byte-aligned z-chunks covering a column window: the window starts
@@ -424,107 +411,10 @@ __device__ __forceinline__ T batch_sum(const T* rd, const T* row, int pos) {
     }
 }
 
-// ------------------------------------------------------------ packed spreading (FP32, W = 8)
-// Table row of a point for the packed spreading: as fill_row_sorted, plus the
-// shifted z-weights (0, w0 .. w7, 0) at WZS.
-template <int W>
-__device__ __forceinline__ void fill_row_packed(float* row, float u0, float u1, float u2, float scale,
-                                                const WindowPoly& wp) {
-    using G = Col3<W, float, true>;
-    int f;
-    float w[W];
-    window_poly<W, float>(u0, wp, 1.f, f, w);
-    float wpm[W];
-#pragma unroll
-    for (int i = 0; i < W; ++i) wpm[wx_slot<W, G::Q>(i)] = w[i];
-    store_vec<float, W>(row + G::WX, wpm);
-    window_poly<W, float>(u1, wp, 1.f, f, w);
-    store_vec<float, W>(row + G::WY, w);
-    window_poly<W, float>(u2, wp, scale, f, w);
-    store_vec<float, W>(row + G::WZ, w);
-    float sh[W + 2];
-    sh[0] = 0.f;
-#pragma unroll
-    for (int k = 0; k < W; ++k) sh[k + 1] = w[k];
-    sh[W + 1] = 0.f;
-    store_vec<float, W + 2>(row + G::WZS, sh);
-}
-
-// One point's W z-taps into the lane's Q rows of pair accumulators, from the
-// z-offset DZ0 (compile time): W/2 packed FMAs per row for an even offset,
-// W/2 + 1 for an odd one.
-template <int W, int Q, int E2, int DZ0>
-__device__ __forceinline__ void add_taps_packed(float2 (&acc)[Q][E2], const float (&av)[Q], const float* row) {
-    using G = Col3<W, float, true>;
-    constexpr int NP = DZ0 % 2 == 0 ? W / 2 : W / 2 + 1;
-    constexpr int P0 = DZ0 / 2;                   // first pair: DZ0 / 2 (even), (DZ0 - 1) / 2 (odd)
-    const float* src = row + (DZ0 % 2 == 0 ? G::WZ : G::WZS);
-    float2 wz[NP];
-#pragma unroll
-    for (int k = 0; k + 1 < NP; k += 2) {
-        const float4 v = *reinterpret_cast<const float4*>(src + 2 * k);
-        wz[k] = make_float2(v.x, v.y);
-        wz[k + 1] = make_float2(v.z, v.w);
-    }
-    if constexpr (NP % 2 == 1) wz[NP - 1] = *reinterpret_cast<const float2*>(src + 2 * (NP - 1));
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const float2 a2 = make_float2(av[q], av[q]);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) acc[q][P0 + k] = __ffma2_rn(a2, wz[k], acc[q][P0 + k]);
-    }
-}
-
-template <int W, int Q, int E2, int DZ0>
-__device__ __forceinline__ void spread_rows_packed(float2 (&acc)[Q][E2], const float* wt, int p, int pe, int i0,
-                                                   int j0) {
-    using G = Col3<W, float, true>;
-    for (; p + 1 < pe; p += 2) {
-        const float* r0 = wt + p * G::STRIDE;
-        const float* r1 = r0 + G::STRIDE;
-        float av0[Q], av1[Q];
-        load_wx<Q, float>(r0 + G::WX + i0 * Q, av0);
-        load_wx<Q, float>(r1 + G::WX + i0 * Q, av1);
-        const float wy0 = r0[G::WY + j0], wy1 = r1[G::WY + j0];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            av0[q] *= wy0;
-            av1[q] *= wy1;
-        }
-        add_taps_packed<W, Q, E2, DZ0>(acc, av0, r0);
-        add_taps_packed<W, Q, E2, DZ0>(acc, av1, r1);
-    }
-    if (p < pe) {
-        const float* r0 = wt + p * G::STRIDE;
-        float av0[Q];
-        load_wx<Q, float>(r0 + G::WX + i0 * Q, av0);
-        const float wy0 = r0[G::WY + j0];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) av0[q] *= wy0;
-        add_taps_packed<W, Q, E2, DZ0>(acc, av0, r0);
-    }
-}
-
-template <int W, int Q, int E2, int DZ0>
-__device__ __forceinline__ void spread_segment_packed(float2 (&acc)[Q][E2], const float* wt, int mydz, int& first,
-                                                      int i0, int j0) {
-    const int cnt = __popc(__ballot_sync(0xffffffffu, mydz == DZ0));
-    spread_rows_packed<W, Q, E2, DZ0>(acc, wt, first, first + cnt, i0, j0);
-    first += cnt;
-}
-
-template <int W, int Q, int E2, int... DZ>
-__device__ __forceinline__ void spread_packed(float2 (&acc)[Q][E2], const float* wt, int mydz, int i0, int j0,
-                                              std::integer_sequence<int, DZ...>) {
-    int first = 0;
-    (spread_segment_packed<W, Q, E2, DZ>(acc, wt, mydz, first, i0, j0), ...);
-}
-
 template <int W, typename T>
 __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 4 : 2) : (W <= 6 ? 2 : 1))
     k_spread3_col(SpreadArgs a) {
-    constexpr bool PK = PackedSpread<W, T>::value;
-    using G = Col3<W, T, PK>;
+    using G = Col3<W, T>;
     constexpr int Q = G::Q, E = G::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sub = reinterpret_cast<T*>(smem_raw);
@@ -553,58 +443,32 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 
         const int start = a.key_start[kbase + col * G::BZ];
         const int end = a.key_start[kbase + (col + 1) * G::BZ];
         if (start < end) {
-            T acc[PK ? 1 : Q][PK ? 1 : E];
-            // packed accumulation: pair e/2 holds z-cells e and e + 1
-            constexpr int E2 = (E + 1) / 2;
-            float2 acc2[PK ? Q : 1][PK ? E2 : 1];
-            if constexpr (PK) {
+            T acc[Q][E];
 #pragma unroll
-                for (int q = 0; q < Q; ++q)
+            for (int q = 0; q < Q; ++q)
 #pragma unroll
-                    for (int e = 0; e < E2; ++e) acc2[q][e] = make_float2(0.f, 0.f);
-            } else {
-#pragma unroll
-                for (int q = 0; q < Q; ++q)
-#pragma unroll
-                    for (int e = 0; e < E; ++e) acc[q][e] = T(0);
-            }
+                for (int e = 0; e < E; ++e) acc[q][e] = T(0);
             Prefetch<T> pf;
             pf.load(c0, c1, c2, a.w, start + lane, lane < end - start);
             for (int base = start; base < end; base += 32) {
                 const int cnt = min(32, end - base);
                 const int mydz = lane < cnt ? int(floor(pf.u2)) - z0 : -1;
                 const int pos = lane;   // a column's points are ordered by z-offset (the sort key)
-                if constexpr (PK) {
-                    if (lane < cnt)
-                        fill_row_packed<W>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, float(pf.w), a.wp);
-                } else {
-                    if (lane < cnt) fill_row_sorted<W, T>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp);
-                }
+                if (lane < cnt) fill_row_sorted<W, T>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp);
                 pf.load(c0, c1, c2, a.w, base + 32 + lane, base + 32 + lane < end);
                 __syncwarp();
-                if constexpr (PK)
-                    spread_packed<W, Q, E2>(acc2, wt, mydz, lane / W, lane % W,
-                                            std::make_integer_sequence<int, G::BZ>{});
-                else
-                    spread_sorted<W, Q, E, T>(acc, wt, mydz, lane / W, lane % W, ri, rj, rv,
-                                              std::make_integer_sequence<int, G::BZ>{});
+                spread_sorted<W, Q, E, T>(acc, wt, mydz, lane / W, lane % W, ri, rj, rv,
+                                          std::make_integer_sequence<int, G::BZ>{});
                 __syncwarp();
             }
-
             const int cx = col / G::BY, cy = col % G::BY;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 if (!rv[q]) continue;
                 T* srow = sub + ((cx + ri[q]) * G::SY + (cy + rj[q])) * G::SZ;
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    T v;
-                    if constexpr (PK)
-                        v = (e % 2 == 0) ? acc2[q][e / 2].x : acc2[q][e / 2].y;
-                    else
-                        v = acc[q][e];
-                    if (v != T(0)) atomicAdd(srow + e, v);
-                }
+                for (int e = 0; e < E; ++e)
+                    if (acc[q][e] != T(0)) atomicAdd(srow + e, acc[q][e]);
             }
         }
         int nxt = 0;
@@ -925,7 +789,7 @@ __global__ void __launch_bounds__(256) k_interp2_strip(InterpArgs a, Epilogue e)
 // ------------------------------------------------------------------ dispatch
 template <int W, typename T>
 size_t spread3_smem() {
-    using G = Col3<W, T, PackedSpread<W, T>::value>;
+    using G = Col3<W, T>;
     return (size_t((G::SUB + 3) / 4 * 4) + size_t(kSpreadWarps) * 32 * G::STRIDE) * sizeof(T);
 }
 

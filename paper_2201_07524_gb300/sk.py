@@ -26,7 +26,7 @@ SK_FP32, SK_FP64 = 0, 1
 SK_METHOD_NFFT, SK_METHOD_DIRECT = 0, 1
 SK_DOMAIN_SCALING, SK_DOMAIN_LOG = 0, 1
 SK_KERNELS_SIMT, SK_KERNELS_TENSOR = 0, 1
-SK_FAULT_NONE, SK_FAULT_TC_WAIT, SK_FAULT_FFT_WAIT = 0, 1, 2
+SK_FAULT_NONE, SK_FAULT_TC_WAIT = 0, 1
 SK_SET_X, SK_SET_Y = 0, 1
 SK_STAGE_SPREAD, SK_STAGE_FFT, SK_STAGE_INTERP, SK_STAGE_OTHER, SK_STAGE_DIRECT, SK_STAGE_NEAR = 0, 1, 2, 3, 4, 5
 SK_NSTAGES = 6
@@ -51,8 +51,7 @@ class sk_info(ctypes.Structure):
                 ("nearfield", ctypes.c_int), ("eps", ctypes.c_double), ("r", ctypes.c_double),
                 ("eps_scaled", ctypes.c_double), ("center", ctypes.c_double * 3), ("scale", ctypes.c_double),
                 ("eps_B", ctypes.c_double), ("eps_I", ctypes.c_double), ("n_subproblems_x", ctypes.c_int),
-                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("tensor_cores", ctypes.c_int),
-                ("fft_persistent", ctypes.c_int)]
+                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("tensor_cores", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

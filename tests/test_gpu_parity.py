@@ -273,33 +273,6 @@ def test_tensor_core_wait_gives_up_and_the_plan_recovers():
     assert err.value.status == sk.SK_ERR_UNSUPPORTED
 
 
-def test_fft_barrier_wait_gives_up_and_the_plan_recovers():
-    # the persistent 3-D FFT's grid barriers, made to run out on purpose
-    # without a fault: the first barrier waits for one arrival too many, every
-    # block gives up after about a second, the solve reports SK_ERR_TIMEOUT;
-    # afterwards the same plan solves normally, and the persistent FFT and the
-    # five pass kernels give the same products
-    x = wl.uniform_ball(1200, 3, 0.2, 83)
-    y = wl.uniform_ball(900, 3, 0.2, 84)
-    a, b = wl.uniform_weights(1200), wl.uniform_weights(900)
-    plan = plan_for(x, y, a, b, eps=0.02, precision=sk.SK_FP32, user_geometry=False)
-    assert sk.sk_plan_info(plan)["fft_persistent"] == 1
-    sk.sk_inject_fault(plan, sk.SK_FAULT_FFT_WAIT)
-    st, _ = sk.sk_solve(plan, 1, raise_on_error=False)
-    assert st == sk.SK_ERR_TIMEOUT
-    sk.sk_inject_fault(plan, sk.SK_FAULT_NONE)
-    sk.sk_set_state(plan)
-    st, res = sk.sk_solve(plan, 30)
-    assert st == sk.SK_OK
-    ref = osk.sinkhorn_dense(x, a, y, b, 0.02, 2.0, 30)
-    assert abs(res["s"] - ref["s"]) <= 1e-5 * abs(ref["s"])
-    plan64 = plan_for(x, y, a, b, eps=0.02, precision=sk.SK_FP64)
-    assert sk.sk_plan_info(plan64)["fft_persistent"] == 0
-    with pytest.raises(sk.SkError) as err:
-        sk.sk_inject_fault(plan64, sk.SK_FAULT_FFT_WAIT)
-    assert err.value.status == sk.SK_ERR_UNSUPPORTED
-
-
 def test_autotune_keeps_a_valid_kind_and_the_state():
     x = wl.uniform_ball(3000, 3, 0.2, 91)
     y = wl.uniform_ball(2500, 3, 0.2, 92)
@@ -563,10 +536,7 @@ def test_launch_count_and_stage_timing():
     sk.sk_solve(plan, 4, result=False)
     torch.cuda.synchronize()
     per_iter = (sk.sk_launch_count(plan) - c0) / 4
-    # per half-step: spread, the FFT (one persistent launch for the five passes
-    # of a 3-D FP32 plan with n_os <= 256), interp
-    assert sk.sk_plan_info(plan)["fft_persistent"] == 1
-    assert per_iter == 2 * (1 + 1 + 1)
+    assert per_iter == 2 * (1 + 5 + 1)        # spread, 5 FFT passes, interp per half-step (3-D)
     sk.sk_stage_times(plan, 1)
     sk.sk_solve(plan, 3, result=False)
     times = sk.sk_stage_times(plan, 0)
