@@ -4,8 +4,8 @@ Tolerances: kernel sums with automatically chosen N and m_w meet the same
 E_fs targets as the fixed-parameter tests (1e-5 FP32, 1e-6 FP64); a batched
 solve reproduces the solves of the same plans one by one to 1e-6 relative in
 s and 1e-5 in u, v (spreading adds with atomics, so FP32 results are not
-bit-identical run to run), and FP64 batches match the dense oracle's s to
-1e-5 relative.
+bit-identical run to run), and batches of FP64 and FP32 plans match the dense
+oracle's s to 1e-5 relative (u to 1e-4 per entry).
 """
 import numpy as np
 import pytest
@@ -92,6 +92,32 @@ def test_solve_batch_matches_oracle_fp64():
     for (x, y, a, b, eps), r in zip(probs, res2):
         ref = osk.sinkhorn_dense(x, a, y, b, eps, 2.0, 40)
         assert abs(r["s"] - ref["s"]) <= 1e-5 * abs(ref["s"])
+
+
+def test_solve_batch_fp32_and_mixed_d_match_oracle_per_problem():
+    # one batch of FP32 and FP64 plans in d = 1, 2, 3, uneven n and m, eps in
+    # [0.01, 0.1]: every problem's value and scaling vector against the dense
+    # FP64 oracle after the same iteration count (value to 1e-5 relative, the
+    # tolerance of the single solves; u to 1e-4 relative per entry)
+    rng = np.random.default_rng(181)
+    probs = []
+    for k, (d, precision) in enumerate([(1, sk.SK_FP32), (2, sk.SK_FP32), (3, sk.SK_FP32), (2, sk.SK_FP64),
+                                        (3, sk.SK_FP32), (1, sk.SK_FP64), (3, sk.SK_FP64), (2, sk.SK_FP32)]):
+        n, m = (int(np.exp(rng.uniform(np.log(300), np.log(2500)))) for _ in range(2))
+        eps = float(rng.uniform(0.01, 0.1))
+        x = wl.uniform_ball(n, d, 0.2, 1810 + 2 * k)
+        y = wl.uniform_ball(m, d, 0.2, 1811 + 2 * k)
+        a, b = wl.dirichlet_weights(n, 1850 + k), wl.uniform_weights(m)
+        probs.append((x, y, a, b, eps, precision))
+    plans = [auto_plan(x, y, a, b, eps, precision) for x, y, a, b, eps, precision in probs]
+    st, res = sk.sk_solve_batch(plans, 30)
+    assert st == sk.SK_OK
+    for (x, y, a, b, eps, precision), plan, r in zip(probs, plans, res):
+        ref = osk.sinkhorn_dense(x, a, y, b, eps, 2.0, 30)
+        assert abs(r["s"] - ref["s"]) <= 1e-5 * abs(ref["s"]), (x.shape, precision, r["s"], ref["s"])
+        u = np.zeros(len(x))
+        sk.sk_get_state(plan, u=u)
+        assert np.max(np.abs(u - ref["u"]) / ref["u"]) <= 1e-4, (x.shape, precision)
 
 
 def test_solve_batch_rejects_bad_arguments():

@@ -635,6 +635,38 @@ def test_nearfield_stage_timing_counts():
     assert times["near"][1] == 4 and times["near"][0] > 0
 
 
+def test_full_size_r1_efs_on_2e4_target_subsample():
+    # the r = 1 workload's prescribed check: E_fs of the FP32 fast summation
+    # (near field included) on 2e4 random targets against exact FP64 sums over
+    # all 4e6 sources.  The exact sums come from the FP64 direct method
+    # (Eq. (matexp) term by term, pinned to the oracle to 1e-12 per element in
+    # test_direct_method_matches_exact_sums) on a plan whose targets are the
+    # subsample: 8e10 FP64 kernel evaluations on the GPU.
+    work = wl.BALL3D_R1
+    x, y = work.points()
+    a, b = work.marginals()
+    prm = sk.sk_default_params(N=work.N, m_w=work.m_w, precision=sk.SK_FP32, eps_I=work.extra["eps_I"])
+    plan = sk.sk_init(cuda(x), cuda(a), cuda(y), cuda(b), work.eps, work.r, prm)
+    v = wl.positive_vector(work.m, 53)
+    t = torch.zeros(work.n, dtype=torch.float64, device=DEV)
+    sk.sk_kernel_apply(plan, 0, cuda(v), t)
+    plan.close()
+    rows = np.random.default_rng(54).choice(work.n, 20000, replace=False)
+    xs = x[rows]
+    ref_plan = sk.sk_init(cuda(xs), cuda(wl.uniform_weights(len(rows))), cuda(y), cuda(b), work.eps, work.r,
+                          sk.sk_default_params(precision=sk.SK_FP64, eps_I=work.extra["eps_I"]))
+    sk.sk_set_method(ref_plan, sk.SK_METHOD_DIRECT)
+    exact = torch.zeros(len(rows), dtype=torch.float64, device=DEV)
+    sk.sk_kernel_apply(ref_plan, 0, cuda(v), exact)
+    ref_plan.close()
+    got, exact = t.cpu().numpy()[rows], exact.cpu().numpy()
+    assert np.all(exact > 0)
+    # the direct reference itself, on a few rows, against the oracle
+    few = np.arange(8)
+    assert np.max(np.abs(exact[few] - _sampled_rows(xs, y, v, work.eps, work.r, few)) / exact[few]) <= 1e-12
+    assert np.max(np.abs(got - exact)) / np.max(exact) <= 1e-5
+
+
 def test_full_size_r1_kernel_apply_sampled_rows():
     work = wl.BALL3D_R1
     x, y = work.points()
