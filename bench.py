@@ -479,6 +479,20 @@ def run_ours(args, rank, world):
         efs_direct = efs(t_dir) if t_dir is not None else None
     accuracy = {"efs_sampled_rows": efs_sample if rank == 0 else None, "iters_compared": K,
                 "s_nfft": res_nfft["s"], "marg_err_nfft": res_nfft["marg_err"]}
+    if args.workload == "r1" and rank == 0:
+        # the r = 1 workload's check: E_fs on 2e4 random targets against exact
+        # FP64 sums over all sources (the FP64 direct method on a plan whose
+        # targets are the subsample)
+        sub = np.random.default_rng(54).choice(w.n, 20000, replace=False)
+        ref_plan = sk.sk_init(T(x[sub]), T(wl.uniform_weights(len(sub))), T(y), T(b), w.eps, w.r,
+                              sk.sk_default_params(precision=sk.SK_FP64, eps_I=w.extra["eps_I"]))
+        sk.sk_set_method(ref_plan, sk.SK_METHOD_DIRECT)
+        exact = torch.zeros(len(sub), dtype=torch.float64, device=dev)
+        sk.sk_kernel_apply(ref_plan, 0, T(v_test), exact)
+        ref_plan.close()
+        exact = exact.cpu().numpy()
+        accuracy["efs_2e4_subsample_vs_fp64_direct"] = float(
+            np.max(np.abs(t_gpu.cpu().numpy()[sub] - exact)) / np.max(exact))
     if direct is not None:
         accuracy.update({"s_direct": direct["s_after_iters"], "s_rel_err_vs_direct": rel,
                          "s_rel_err_gate": 1e-5, "s_rel_err_ok": bool(rel <= 1e-5),

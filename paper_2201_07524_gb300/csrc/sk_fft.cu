@@ -41,7 +41,7 @@ namespace sk {
 
 enum { FULL = 0, CENTERED = 1 };
 
-constexpr int kFftBlockElems = 256;
+constexpr int kFftBlockElems = 512;
 
 __host__ __device__ __forceinline__ int fft_pencils(int n) { return n >= kFftBlockElems ? 1 : kFftBlockElems / n; }
 
