@@ -638,8 +638,8 @@ void build_tables(sk_plan* P) {
     CK(cudaFreeAsync(tmp, P->ps));
     CK(cudaFreeAsync(costab, P->ps));
     // twiddles
-    P->fft.tw = dalloc(P, size_t(P->n_os / 2) * sizeof(typename Cplx<T>::type));
-    launch_twiddles<T>(P->fft.tw, P->n_os, P->ps);
+    P->fft.tw = dalloc(P, size_t(std::max(1, fft_twiddle_rows<T>(P->n_os))) * sizeof(typename Cplx<T>::type));
+    CK(launch_twiddle_rows<T>(P->fft.tw, P->n_os, P->ps));
     CK(cudaGetLastError());
 }
 

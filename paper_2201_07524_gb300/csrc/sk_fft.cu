@@ -186,9 +186,40 @@ struct SyncBlock {
 // butterfly jj reads x_q = X[jj + q n/R], scales it by w_L^(q k) (L = Ns R,
 // k = jj mod Ns), takes the R-point DFT and writes y_r to
 // X[(jj - k) R + k + r Ns].  All reads precede a barrier, then the writes.
+// The twiddles of one Stockham stage are tabulated per butterfly class: row
+// k (0 <= k < Ns) of a radix-R stage holds w_L^(q k), q = 1 .. R-1, L = Ns R,
+// w_L = exp(-2 pi i / L), padded to RW(R) entries, so a butterfly reads its
+// R-1 twiddles with vector loads (the table is a few KB, resident in L1);
+// the stages follow one another in the table, and the first stage (Ns = 1,
+// all twiddles 1) has none.
+__host__ __device__ constexpr int row_width(int R) { return R == 8 ? 8 : (R == 4 ? 4 : 2); }
+
+template <typename C, int RW>
+__device__ __forceinline__ void load_row(const C* __restrict__ row, C (&w)[RW]) {
+    if constexpr (sizeof(C) == 8) {
+#pragma unroll
+        for (int q = 0; q < RW; q += 2) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(row + q));
+            w[q].x = v.x;
+            w[q].y = v.y;
+            w[q + 1].x = v.z;
+            w[q + 1].y = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < RW; ++q) w[q] = __ldg(row + q);
+    }
+}
+
+// One Stockham stage of radix R on the thread's E elements (E/R butterflies):
+// butterfly jj reads x_q = X[jj + q n/R], scales it by w_L^(q k) (L = Ns R,
+// k = jj mod Ns), takes the R-point DFT and writes y_r to
+// X[(jj - k) R + k + r Ns].  All reads precede a barrier, then the writes.
+// `rows` is the stage's twiddle table (unused when Ns = 1).
 template <typename C, bool INV, int R, int E, class S>
-__device__ __forceinline__ void stockham_stage(C* pen, int n, int Ns, int t, const C* tw) {
+__device__ __forceinline__ void stockham_stage(C* pen, int n, int Ns, int t, const C* __restrict__ rows) {
     constexpr int B = E / R;
+    constexpr int RW = row_width(R);
     const int stride = n / R, per = n / E;
     C x[E];
 #pragma unroll
@@ -197,14 +228,25 @@ __device__ __forceinline__ void stockham_stage(C* pen, int n, int Ns, int t, con
 #pragma unroll
         for (int r = 0; r < R; ++r) x[b * R + r] = pen[pidx(jj + r * stride)];
     }
+    // the butterflies' twiddle rows, requested before the barrier
+    C w[B][RW];
+    if (Ns > 1) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) load_row<C, RW>(rows + ((t + b * per) & (Ns - 1)) * RW, w[b]);
+    }
     S::sync();
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int jj = t + b * per;
         const int k = jj & (Ns - 1);
-        const int step = k * (n / (Ns * R));
+        if (Ns > 1) {
 #pragma unroll
-        for (int q = 1; q < R; ++q) x[b * R + q] = cmul(x[b * R + q], twiddle<C, INV>(tw, q * step, n));
+            for (int q = 1; q < R; ++q) {
+                C wq = w[b][q - 1];
+                if (INV) wq.y = -wq.y;
+                x[b * R + q] = cmul(x[b * R + q], wq);
+            }
+        }
         if (R == 8) dft8<C, INV>(x + b * R);
         else if (R == 4) dft4<C, INV>(x + b * R);
         else dft2<C, INV>(x + b * R);
@@ -217,49 +259,101 @@ __device__ __forceinline__ void stockham_stage(C* pen, int n, int Ns, int t, con
 
 // Transform the unit's P pencils in place (natural order in and out; pencil
 // p at buf + p * ns, element e at pidx(e)); the unit has exactly
-// fft_threads<T>(n) threads, `tid` is the thread's index in it.  `tw` is the
-// block's shared copy of the n/2 twiddles.  Radix E = fft_ept stages while
+// fft_threads<T>(n) threads, `tid` is the thread's index in it.  `rows` is
+// the plan's table of stage twiddle rows.  Radix E = fft_ept stages while
 // they fit, then one of radix 4 or 2.
 template <typename C, bool INV, int E, class S>
-__device__ __forceinline__ void stockham_all(C* buf, int ns, int n, int log2n, const C* tw, int tid) {
+__device__ __forceinline__ void stockham_all(C* buf, int ns, int n, int log2n, const C* __restrict__ rows, int tid) {
     constexpr int LE = E == 8 ? 3 : 2;
     const int per = n / E;
     const int p = tid / per, t = tid - p * per;
     C* pen = buf + p * ns;
     int Ns = 1, rem = log2n;
-    for (; rem >= LE; rem -= LE, Ns <<= LE) stockham_stage<C, INV, E, E, S>(pen, n, Ns, t, tw);
-    if (rem == 2) stockham_stage<C, INV, 4, E, S>(pen, n, Ns, t, tw);
-    else if (rem == 1) stockham_stage<C, INV, 2, E, S>(pen, n, Ns, t, tw);
+    for (; rem >= LE; rem -= LE, Ns <<= LE) {
+        stockham_stage<C, INV, E, E, S>(pen, n, Ns, t, rows);
+        if (Ns > 1) rows += Ns * row_width(E);
+    }
+    if (rem == 2) stockham_stage<C, INV, 4, E, S>(pen, n, Ns, t, rows);
+    else if (rem == 1) stockham_stage<C, INV, 2, E, S>(pen, n, Ns, t, rows);
 }
 
 template <typename T, bool INV, class S>
-__device__ void fft_stockham(typename Cplx<T>::type* buf, int ns, int n, int log2n, const typename Cplx<T>::type* tw,
+__device__ void fft_stockham(typename Cplx<T>::type* buf, int ns, int n, int log2n, const typename Cplx<T>::type* rows,
                              int tid) {
     using C = typename Cplx<T>::type;
     S::sync();
     if (fft_ept<T>(n) == 4)
-        stockham_all<C, INV, 4, S>(buf, ns, n, log2n, tw, tid);
+        stockham_all<C, INV, 4, S>(buf, ns, n, log2n, rows, tid);
     else
-        stockham_all<C, INV, 8, S>(buf, ns, n, log2n, tw, tid);
+        stockham_all<C, INV, 8, S>(buf, ns, n, log2n, rows, tid);
 }
 
-// Shared memory of an FFT block: the n/2 twiddles, then P pencils of n + 1.
+// Entries (complex) of the stage twiddle table of an n-point transform, and
+// the table itself (computed in FP64 and rounded; one launch per stage).
+template <typename T>
+int fft_twiddle_rows(int n) {
+    const int E = fft_ept<T>(n), LE = E == 8 ? 3 : 2;
+    int log2n = 0;
+    while ((1 << log2n) < n) ++log2n;
+    int total = 0, Ns = 1, rem = log2n;
+    for (; rem >= LE; rem -= LE, Ns <<= LE)
+        if (Ns > 1) total += Ns * row_width(E);
+    if (rem > 0 && Ns > 1) total += Ns * row_width(rem == 2 ? 4 : 2);
+    return total;
+}
+
+template <typename C>
+__global__ void k_twiddle_rows(C* __restrict__ rows, int Ns, int R) {
+    const int RW = row_width(R);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ns * RW) return;
+    const int k = i / RW, q = i - k * RW + 1;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (q < R) {
+        double sn, cs;
+        sincospi(-2.0 * double((q * k) % (Ns * R)) / double(Ns * R), &sn, &cs);
+        v.x = decltype(v.x)(cs);
+        v.y = decltype(v.y)(sn);
+    }
+    rows[i] = v;
+}
+
+template <typename T>
+cudaError_t launch_twiddle_rows(void* rows, int n, cudaStream_t s) {
+    using C = typename Cplx<T>::type;
+    const int E = fft_ept<T>(n), LE = E == 8 ? 3 : 2;
+    int log2n = 0;
+    while ((1 << log2n) < n) ++log2n;
+    C* at = static_cast<C*>(rows);
+    int Ns = 1, rem = log2n;
+    auto stage = [&](int R) {
+        const int cnt = Ns * row_width(R);
+        k_twiddle_rows<C><<<unsigned((cnt + 255) / 256), 256, 0, s>>>(at, Ns, R);
+        at += cnt;
+    };
+    for (; rem >= LE; rem -= LE, Ns <<= LE)
+        if (Ns > 1) stage(E);
+    if (rem > 0 && Ns > 1) stage(rem == 2 ? 4 : 2);
+    return cudaGetLastError();
+}
+
+template int fft_twiddle_rows<float>(int);
+template int fft_twiddle_rows<double>(int);
+template cudaError_t launch_twiddle_rows<float>(void*, int, cudaStream_t);
+template cudaError_t launch_twiddle_rows<double>(void*, int, cudaStream_t);
+
+// Shared memory of an FFT block: P pencils of fft_stride(n) slots.
 template <typename T>
 struct FftSmem {
     using C = typename Cplx<T>::type;
-    C* tw;
     C* buf;
-    __device__ __forceinline__ explicit FftSmem(int n) {
+    __device__ __forceinline__ FftSmem() {
         extern __shared__ __align__(16) unsigned char smem_raw[];
-        tw = reinterpret_cast<C*>(smem_raw);
-        buf = tw + n / 2;
+        buf = reinterpret_cast<C*>(smem_raw);
     }
 };
-
-template <typename C>
-__device__ __forceinline__ void load_twiddles(C* dst, const C* __restrict__ src, int n) {
-    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) dst[k] = src[k];
-}
 
 // Elements a thread loads per round; a round's loads are all issued before
 // any of them is stored, so their latencies overlap.
@@ -560,9 +654,8 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_fft_r2c_rows(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
                                                       RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ twg) {
-    const FftSmem<T> sm(n);
-    load_twiddles(sm.tw, twg, n);
-    r2c_unit<T, SyncBlock>(g, out, rp, n, log2n, h, sm.tw, sm.buf, int(blockIdx.x) * fft_pencils(n),
+    const FftSmem<T> sm;
+    r2c_unit<T, SyncBlock>(g, out, rp, n, log2n, h, twg, sm.buf, int(blockIdx.x) * fft_pencils(n),
                            int(threadIdx.x), int(blockDim.x));
 }
 
@@ -570,9 +663,8 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_fft_c2r_rows(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
                                                       RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ twg) {
-    const FftSmem<T> sm(n);
-    load_twiddles(sm.tw, twg, n);
-    c2r_unit<T, SyncBlock>(in, g, rp, n, log2n, h, sm.tw, sm.buf, int(blockIdx.x) * fft_pencils(n),
+    const FftSmem<T> sm;
+    c2r_unit<T, SyncBlock>(in, g, rp, n, log2n, h, twg, sm.buf, int(blockIdx.x) * fft_pencils(n),
                            int(threadIdx.x), int(blockDim.x));
 }
 
@@ -581,9 +673,8 @@ __global__ void __launch_bounds__(512) k_fft_axis(const typename Cplx<T>::type* 
                                                   typename Cplx<T>::type* __restrict__ out, int64_t olo, int64_t ocnt,
                                                   int64_t I, int klo, int kcnt, int n, int log2n, int h,
                                                   const typename Cplx<T>::type* __restrict__ twg) {
-    const FftSmem<T> sm(n);
-    load_twiddles(sm.tw, twg, n);
-    axis_unit<T, INM, OUTM, INV, SyncBlock>(in, out, int(olo), int(ocnt), int(I), klo, kcnt, n, log2n, h, sm.tw, sm.buf,
+    const FftSmem<T> sm;
+    axis_unit<T, INM, OUTM, INV, SyncBlock>(in, out, int(olo), int(ocnt), int(I), klo, kcnt, n, log2n, h, twg, sm.buf,
                                             int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
 
@@ -592,9 +683,8 @@ __global__ void __launch_bounds__(512) k_fft_axis0_convolve(typename Cplx<T>::ty
                                                             int xlo, int xcnt, int n, int log2n, int h,
                                                             const T* __restrict__ mult,
                                                             const typename Cplx<T>::type* __restrict__ twg) {
-    const FftSmem<T> sm(n);
-    load_twiddles(sm.tw, twg, n);
-    convolve_unit<T, SyncBlock>(data, int(I), xlo, xcnt, n, log2n, h, mult, sm.tw, sm.buf,
+    const FftSmem<T> sm;
+    convolve_unit<T, SyncBlock>(data, int(I), xlo, xcnt, n, log2n, h, mult, twg, sm.buf,
                                 int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
 
@@ -664,14 +754,14 @@ __global__ void k_fill_forward(const double* __restrict__ fhat, int d, int h, co
 
 template <typename T>
 static size_t fft_smem_bytes(int n) {
-    return (size_t(n / 2) + size_t(fft_pencils(n)) * size_t(fft_stride(n))) * sizeof(typename Cplx<T>::type);
+    return size_t(fft_pencils(n)) * size_t(fft_stride(n)) * sizeof(typename Cplx<T>::type);
 }
 
 // Largest dynamic shared memory any FFT launch of this precision can use:
-// one pencil of the largest length, 4096, and its twiddles.
+// one pencil of the largest length, 4096.
 template <typename T>
 static size_t fft_smem_max() {
-    return size_t(2048 + fft_stride(4096)) * sizeof(typename Cplx<T>::type);
+    return size_t(fft_stride(4096)) * sizeof(typename Cplx<T>::type);
 }
 
 // Opt a kernel into its largest shared-memory size once per device (the cache

@@ -411,16 +411,6 @@ __global__ void k_build_mult(T* __restrict__ M, int d, int h, const double* __re
     M[idx] = T(c * bk[bi]);
 }
 
-template <typename C>
-__global__ void k_twiddles(C* __restrict__ tw, int n) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n / 2) return;
-    double s, c;
-    sincospi(-2.0 * double(k) / double(n), &s, &c);
-    tw[k].x = decltype(tw[k].x)(c);
-    tw[k].y = decltype(tw[k].y)(s);
-}
-
 // ------------------------------------------------------------ vectors
 __global__ void k_fill(double* __restrict__ p, int64_t n, double v) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -527,11 +517,6 @@ void launch_build_mult(T* M, int d, int h, const double* bk, double inv_norm, co
     k_build_mult<T><<<unsigned((total + 255) / 256), 256, 0, s>>>(M, d, h, bk, inv_norm, psihat);
 }
 
-template <typename T>
-void launch_twiddles(void* tw, int n, cudaStream_t s) {
-    using C = typename Cplx<T>::type;
-    k_twiddles<C><<<unsigned((n / 2 + 255) / 256), 256, 0, s>>>(static_cast<C*>(tw), n);
-}
 
 template void launch_prepare_points<float>(const double*, int64_t, int, const double[3], double, int, const int[3],
                                            const int[3], int, float* const[3], int*, int*, int*, cudaStream_t);
@@ -544,8 +529,6 @@ template void launch_build_mult<float>(float*, int, int, const double*, double, 
                                        cudaStream_t);
 template void launch_build_mult<double>(double*, int, int, const double*, double, const double*, int64_t,
                                         cudaStream_t);
-template void launch_twiddles<float>(void*, int, cudaStream_t);
-template void launch_twiddles<double>(void*, int, cudaStream_t);
 
 // ------------------------------------------------------------ log domain
 // Per-block maxima of v (-inf for an empty block), for the shift of the

@@ -51,8 +51,6 @@ __global__ void k_window_transform(double* out, int h, int n_os, int m, double b
 template <typename T>
 void launch_build_mult(T* M, int d, int h, const double* bk, double inv_norm, const double* psihat, int64_t total,
                        cudaStream_t s);
-template <typename T>
-void launch_twiddles(void* tw, int n, cudaStream_t s);
 
 // spec[k] *= b_k over k in {-h..h}^d (interleaved complex, row-major with
 // index k_t + h), b_k taken from the N^d table over I_N; the kernel is even in
