@@ -43,22 +43,22 @@ enum { FULL = 0, CENTERED = 1 };
 
 constexpr int kFftBlockElems = 512;
 
-__host__ __device__ __forceinline__ int fft_pencils(int n) { return n >= kFftBlockElems ? 1 : kFftBlockElems / n; }
+__host__ __device__ constexpr int fft_pencils(int n) { return n >= kFftBlockElems ? 1 : kFftBlockElems / n; }
 
 // Elements of a pencil per thread: 8 in FP32 (radix-8 stages); 4 in FP64
 // (radix-4 stages), whose arithmetic is slow enough on this GPU that the
 // shorter per-thread chains and twice the threads pay -- except for pencils
 // longer than 2048, which keep 8 so that a block stays within 512 threads.
 template <typename T>
-__host__ __device__ __forceinline__ int fft_ept(int n) { return (sizeof(T) == 8 && n <= 2048) ? 4 : 8; }
+__host__ __device__ constexpr int fft_ept(int n) { return (sizeof(T) == 8 && n <= 2048) ? 4 : 8; }
 
 // Threads of an FFT block (16 to 512).
 template <typename T>
-__host__ __device__ __forceinline__ int fft_threads(int n) { return fft_pencils(n) * n / fft_ept<T>(n); }
+__host__ __device__ constexpr int fft_threads(int n) { return fft_pencils(n) * n / fft_ept<T>(n); }
 
 // Padded position of element e of a pencil; a pencil spans fft_stride(n) slots.
-__host__ __device__ __forceinline__ int pidx(int e) { return e + (e >> 3); }
-__host__ __device__ __forceinline__ int fft_stride(int n) { return n + n / 8; }
+__host__ __device__ constexpr int pidx(int e) { return e + (e >> 3); }
+__host__ __device__ constexpr int fft_stride(int n) { return n + n / 8; }
 
 // Row pairs of the real passes: pair q covers rows r0 = o * ostride + y and
 // r0 + 1 with o = olo + q / npo and y = ylo + 2 (q % npo).
@@ -277,15 +277,36 @@ __device__ __forceinline__ void stockham_all(C* buf, int ns, int n, int log2n, c
     else if (rem == 1) stockham_stage<C, INV, 2, E, S>(pen, n, Ns, t, rows);
 }
 
-template <typename T, bool INV, class S>
+// The same stage sequence for a length known at compile time (N = 2^L2): the
+// stage parameters, pencil strides and shared-memory offsets fold into
+// constants and immediate offsets.
+template <typename C, bool INV, int E, class S, int N, int NS, int REM>
+__device__ __forceinline__ void stages_ct(C* pen, int t, const C* __restrict__ rows) {
+    constexpr int LE = E == 8 ? 3 : 2;
+    if constexpr (REM >= LE) {
+        stockham_stage<C, INV, E, E, S>(pen, N, NS, t, rows);
+        stages_ct<C, INV, E, S, N, NS * E, REM - LE>(pen, t, NS > 1 ? rows + NS * row_width(E) : rows);
+    } else if constexpr (REM == 2) {
+        stockham_stage<C, INV, 4, E, S>(pen, N, NS, t, rows);
+    } else if constexpr (REM == 1) {
+        stockham_stage<C, INV, 2, E, S>(pen, N, NS, t, rows);
+    }
+}
+
+template <typename T, bool INV, class S, int L2>
 __device__ void fft_stockham(typename Cplx<T>::type* buf, int ns, int n, int log2n, const typename Cplx<T>::type* rows,
                              int tid) {
     using C = typename Cplx<T>::type;
     S::sync();
-    if (fft_ept<T>(n) == 4)
+    if constexpr (L2 > 0) {
+        constexpr int N = 1 << L2, E = fft_ept<T>(N), PER = N / E;
+        const int p = tid / PER, t = tid - p * PER;
+        stages_ct<C, INV, E, S, N, 1, L2>(buf + p * fft_stride(N), t, rows);
+    } else if (fft_ept<T>(n) == 4) {
         stockham_all<C, INV, 4, S>(buf, ns, n, log2n, rows, tid);
-    else
+    } else {
         stockham_all<C, INV, 8, S>(buf, ns, n, log2n, rows, tid);
+    }
 }
 
 // Entries (complex) of the stage twiddle table of an n-point transform, and
@@ -370,11 +391,15 @@ constexpr int kFftLoadsPerRound = 8;
 
 // Two real rows of length n -> two half spectra of length h+1 (output rows
 // are the same row indices in A1).  The input rows are zeroed after reading.
-template <typename T, class S>
+template <typename T, class S, int L2>
 __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
                                          const RowPairs& rp, int n, int log2n, int h,
                                          const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf, int q0,
                                          int tid, int nthr) {
+    if constexpr (L2 > 0) {   // a length known at compile time
+        n = 1 << L2;
+        log2n = L2;
+    }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n);
     const int ns = fft_stride(n);
@@ -407,7 +432,7 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
             buf[(e >> log2n) * ns + pidx(e & (n - 1))] = z[j];
         }
     }
-    fft_stockham<T, false, S>(buf, ns, n, log2n, tw, tid);
+    fft_stockham<T, false, S, L2>(buf, ns, n, log2n, tw, tid);
     const int H = h + 1;
     // element e = p H + k of the output, walked without a division per element
     int p = tid / H, k = tid - (tid / H) * H;
@@ -436,11 +461,15 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
 }
 
 // Two half spectra -> two real rows, by Hermitian completion.
-template <typename T, class S>
+template <typename T, class S, int L2>
 __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
                                          const RowPairs& rp, int n, int log2n, int h,
                                          const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf, int q0,
                                          int tid, int nthr) {
+    if constexpr (L2 > 0) {   // a length known at compile time
+        n = 1 << L2;
+        log2n = L2;
+    }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n);
     const int ns = fft_stride(n);
@@ -489,7 +518,7 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
             buf[(e >> log2n) * ns + pidx(pos)] = z;
         }
     }
-    fft_stockham<T, true, S>(buf, ns, n, log2n, tw, tid);
+    fft_stockham<T, true, S, L2>(buf, ns, n, log2n, tw, tid);
     for (int e = tid; e < P * n; e += nthr) {
         const int p = e >> log2n;
         const int l = e & (n - 1);
@@ -507,11 +536,15 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
 // CENTERED stores frequencies -h..h at positions 0..2h.  Only pencils with
 // o in [olo, olo + ocnt) are transformed, and a FULL output is stored only for
 // k in [klo, klo + kcnt).
-template <typename T, int INM, int OUTM, bool INV, class S>
+template <typename T, int INM, int OUTM, bool INV, class S, int L2>
 __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restrict__ in,
                                           typename Cplx<T>::type* __restrict__ out, int olo, int ocnt, int I, int klo,
                                           int kcnt, int n, int log2n, int h, const typename Cplx<T>::type* tw,
                                           typename Cplx<T>::type* buf, int q0, int tid, int nthr) {
+    if constexpr (L2 > 0) {   // a length known at compile time
+        n = 1 << L2;
+        log2n = L2;
+    }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n), lp = ilog2(P);
     const int ns = fft_stride(n);
@@ -556,7 +589,7 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
             buf[pl * ns + pidx(pos)] = v[j];
         }
     }
-    fft_stockham<T, INV, S>(buf, ns, n, log2n, tw, tid);
+    fft_stockham<T, INV, S, L2>(buf, ns, n, log2n, tw, tid);
     if (!qok) return;
     for (int e = tid; e < P * kn; e += nthr) {
         const int k = k0 + (e >> lp);
@@ -569,11 +602,15 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
 // frequencies by M[(k+h)*I + q] and zero the rest, inverse FFT, in place.
 // Only axis-0 positions in [xlo, xlo + xcnt) are loaded (the rest are zero)
 // and stored (the rest are never read).
-template <typename T, class S>
+template <typename T, class S, int L2>
 __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict__ data, int I, int xlo, int xcnt,
                                               int n, int log2n, int h, const T* __restrict__ mult,
                                               const typename Cplx<T>::type* tw, typename Cplx<T>::type* buf,
                                               int q0, int tid, int nthr) {
+    if constexpr (L2 > 0) {   // a length known at compile time
+        n = 1 << L2;
+        log2n = L2;
+    }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n), lp = ilog2(P);
     const int ns = fft_stride(n);
@@ -610,7 +647,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
         const int k = pos <= (n >> 1) ? pos : pos - n;
         mv[j] = (one_round && e < P * n && q < I && k >= -h && k <= h) ? mult[int64_t(k + h) * I + q] : T(0);
     }
-    fft_stockham<T, false, S>(buf, ns, n, log2n, tw, tid);
+    fft_stockham<T, false, S, L2>(buf, ns, n, log2n, tw, tid);
     if (one_round) {
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
@@ -638,7 +675,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
             }
         }
     }
-    fft_stockham<T, true, S>(buf, ns, n, log2n, tw, tid);
+    fft_stockham<T, true, S, L2>(buf, ns, n, log2n, tw, tid);
     for (int e = tid; e < P * xcnt; e += nthr) {
         const int k = xlo + (e >> lp);
         const int pl = e & (P - 1);
@@ -650,41 +687,41 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
 // ------------------------------------------------------------ pass kernels
 // One launch per pass; a block is one unit of fft_threads<T>(n) threads.
 
-template <typename T>
+template <typename T, int L2>
 __global__ void __launch_bounds__(512) k_fft_r2c_rows(T* __restrict__ g, typename Cplx<T>::type* __restrict__ out,
                                                       RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm;
-    r2c_unit<T, SyncBlock>(g, out, rp, n, log2n, h, twg, sm.buf, int(blockIdx.x) * fft_pencils(n),
+    r2c_unit<T, SyncBlock, L2>(g, out, rp, n, log2n, h, twg, sm.buf, int(blockIdx.x) * fft_pencils(n),
                            int(threadIdx.x), int(blockDim.x));
 }
 
-template <typename T>
+template <typename T, int L2>
 __global__ void __launch_bounds__(512) k_fft_c2r_rows(const typename Cplx<T>::type* __restrict__ in, T* __restrict__ g,
                                                       RowPairs rp, int n, int log2n, int h,
                                                       const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm;
-    c2r_unit<T, SyncBlock>(in, g, rp, n, log2n, h, twg, sm.buf, int(blockIdx.x) * fft_pencils(n),
+    c2r_unit<T, SyncBlock, L2>(in, g, rp, n, log2n, h, twg, sm.buf, int(blockIdx.x) * fft_pencils(n),
                            int(threadIdx.x), int(blockDim.x));
 }
 
-template <typename T, int INM, int OUTM, bool INV>
+template <typename T, int INM, int OUTM, bool INV, int L2>
 __global__ void __launch_bounds__(512) k_fft_axis(const typename Cplx<T>::type* __restrict__ in,
                                                   typename Cplx<T>::type* __restrict__ out, int64_t olo, int64_t ocnt,
                                                   int64_t I, int klo, int kcnt, int n, int log2n, int h,
                                                   const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm;
-    axis_unit<T, INM, OUTM, INV, SyncBlock>(in, out, int(olo), int(ocnt), int(I), klo, kcnt, n, log2n, h, twg, sm.buf,
+    axis_unit<T, INM, OUTM, INV, SyncBlock, L2>(in, out, int(olo), int(ocnt), int(I), klo, kcnt, n, log2n, h, twg, sm.buf,
                                             int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
 
-template <typename T>
+template <typename T, int L2>
 __global__ void __launch_bounds__(512) k_fft_axis0_convolve(typename Cplx<T>::type* __restrict__ data, int64_t I,
                                                             int xlo, int xcnt, int n, int log2n, int h,
                                                             const T* __restrict__ mult,
                                                             const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm;
-    convolve_unit<T, SyncBlock>(data, int(I), xlo, xcnt, n, log2n, h, mult, twg, sm.buf,
+    convolve_unit<T, SyncBlock, L2>(data, int(I), xlo, xcnt, n, log2n, h, mult, twg, sm.buf,
                                 int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
 
@@ -807,26 +844,70 @@ static RowPairs row_pairs(const FftPlan& f) {
     return rp;
 }
 
-template <typename T>
-static cudaError_t run_r2c(const FftPlan& f, int64_t* launches, cudaStream_t s) {
+// The pass kernels come in versions for the transform lengths the workloads
+// use (2^6, 2^7, 2^8 and, in FP32, 2^10: the length a compile-time constant)
+// and a version for any length (L2 = 0).
+#define SK_FFT_LENGTHS(T, LOG2N, CALL)                        \
+    switch (LOG2N) {                                          \
+        case 6: { constexpr int L2 = 6; CALL; } break;         \
+        case 7: { constexpr int L2 = 7; CALL; } break;         \
+        case 8: { constexpr int L2 = 8; CALL; } break;         \
+        case 10:                                              \
+            if constexpr (sizeof(T) == 4) {                   \
+                constexpr int L2 = 10;                        \
+                CALL;                                         \
+                break;                                        \
+            }                                                 \
+            [[fallthrough]];                                  \
+        default: { constexpr int L2 = 0; CALL; } break;        \
+    }
+
+template <typename T, int L2>
+static cudaError_t run_r2c_l(const FftPlan& f, int64_t* launches, cudaStream_t s) {
     using C = typename Cplx<T>::type;
-    SK_TRY((ensure_smem<T, k_fft_r2c_rows<T>>()));
+    SK_TRY((ensure_smem<T, k_fft_r2c_rows<T, L2>>()));
     const RowPairs rp = row_pairs(f);
     const int P = fft_pencils(f.n);
-    k_fft_r2c_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_r2c_rows<T, L2><<<unsigned((rp.npairs + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<T*>(f.grid), static_cast<C*>(f.A1), rp, f.n, f.log2n, f.h, static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t run_c2r(const FftPlan& f, int64_t* launches, cudaStream_t s) {
+static cudaError_t run_r2c(const FftPlan& f, int64_t* launches, cudaStream_t s) {
+    SK_FFT_LENGTHS(T, f.log2n, return (run_r2c_l<T, L2>(f, launches, s)))
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int L2>
+static cudaError_t run_c2r_l(const FftPlan& f, int64_t* launches, cudaStream_t s) {
     using C = typename Cplx<T>::type;
-    SK_TRY((ensure_smem<T, k_fft_c2r_rows<T>>()));
+    SK_TRY((ensure_smem<T, k_fft_c2r_rows<T, L2>>()));
     const RowPairs rp = row_pairs(f);
     const int P = fft_pencils(f.n);
-    k_fft_c2r_rows<T><<<unsigned((rp.npairs + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_c2r_rows<T, L2><<<unsigned((rp.npairs + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<const C*>(f.A1), static_cast<T*>(f.grid_out), rp, f.n, f.log2n, f.h,
+        static_cast<const C*>(f.tw));
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t run_c2r(const FftPlan& f, int64_t* launches, cudaStream_t s) {
+    SK_FFT_LENGTHS(T, f.log2n, return (run_c2r_l<T, L2>(f, launches, s)))
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int INM, int OUTM, bool INV, int L2>
+static cudaError_t run_axis_l(const FftPlan& f, const void* in, void* out, int64_t olo, int64_t ocnt, int64_t I,
+                              int klo, int kcnt, int64_t* launches, cudaStream_t s) {
+    using C = typename Cplx<T>::type;
+    SK_TRY((ensure_smem<T, k_fft_axis<T, INM, OUTM, INV, L2>>()));
+    const int P = fft_pencils(f.n);
+    const int64_t Q = ocnt * I;
+    k_fft_axis<T, INM, OUTM, INV, L2><<<unsigned((Q + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
+        static_cast<const C*>(in), static_cast<C*>(out), olo, ocnt, I, klo, kcnt, f.n, f.log2n, f.h,
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
@@ -835,15 +916,9 @@ static cudaError_t run_c2r(const FftPlan& f, int64_t* launches, cudaStream_t s) 
 template <typename T, int INM, int OUTM, bool INV>
 static cudaError_t run_axis(const FftPlan& f, const void* in, void* out, int64_t olo, int64_t ocnt, int64_t I,
                             int klo, int kcnt, int64_t* launches, cudaStream_t s) {
-    using C = typename Cplx<T>::type;
-    SK_TRY((ensure_smem<T, k_fft_axis<T, INM, OUTM, INV>>()));
-    const int P = fft_pencils(f.n);
-    const int64_t Q = ocnt * I;
-    k_fft_axis<T, INM, OUTM, INV><<<unsigned((Q + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
-        static_cast<const C*>(in), static_cast<C*>(out), olo, ocnt, I, klo, kcnt, f.n, f.log2n, f.h,
-        static_cast<const C*>(f.tw));
-    if (launches) ++*launches;
-    return cudaGetLastError();
+    SK_FFT_LENGTHS(T, f.log2n,
+                   return (run_axis_l<T, INM, OUTM, INV, L2>(f, in, out, olo, ocnt, I, klo, kcnt, launches, s)))
+    return cudaErrorInvalidValue;
 }
 
 // Axis-0 positions the spectra hold outside zero: the band, widened to the
@@ -858,18 +933,24 @@ static void axis0_range(const FftPlan& f, int& lo, int& cnt) {
     cnt = hi - lo + 1;
 }
 
-template <typename T>
-static cudaError_t run_axis0_convolve(const FftPlan& f, void* data, int64_t I, int64_t* launches, cudaStream_t s) {
+template <typename T, int L2>
+static cudaError_t run_axis0_convolve_l(const FftPlan& f, void* data, int64_t I, int64_t* launches, cudaStream_t s) {
     using C = typename Cplx<T>::type;
-    SK_TRY((ensure_smem<T, k_fft_axis0_convolve<T>>()));
+    SK_TRY((ensure_smem<T, k_fft_axis0_convolve<T, L2>>()));
     const int P = fft_pencils(f.n);
     int xlo, xcnt;
     axis0_range(f, xlo, xcnt);
-    k_fft_axis0_convolve<T><<<unsigned((I + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
+    k_fft_axis0_convolve<T, L2><<<unsigned((I + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
         static_cast<C*>(data), I, xlo, xcnt, f.n, f.log2n, f.h, static_cast<const T*>(f.mult),
         static_cast<const C*>(f.tw));
     if (launches) ++*launches;
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t run_axis0_convolve(const FftPlan& f, void* data, int64_t I, int64_t* launches, cudaStream_t s) {
+    SK_FFT_LENGTHS(T, f.log2n, return (run_axis0_convolve_l<T, L2>(f, data, I, launches, s)))
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
