@@ -56,9 +56,11 @@ __host__ __device__ constexpr int fft_ept(int n) { return (sizeof(T) == 8 && n <
 template <typename T>
 __host__ __device__ constexpr int fft_threads(int n) { return fft_pencils(n) * n / fft_ept<T>(n); }
 
-// Padded position of element e of a pencil; a pencil spans fft_stride(n) slots.
+// Padded position of element e of a pencil; a pencil spans fft_stride(n)
+// slots.  The 4 extra slots per pencil put the pencils of a block on
+// different shared-memory banks (n + n/8 is a multiple of the 32 banks).
 __host__ __device__ constexpr int pidx(int e) { return e + (e >> 3); }
-__host__ __device__ constexpr int fft_stride(int n) { return n + n / 8; }
+__host__ __device__ constexpr int fft_stride(int n) { return n + n / 8 + 4; }
 
 // Row pairs of the real passes: pair q covers rows r0 = o * ostride + y and
 // r0 + 1 with o = olo + q / npo and y = ylo + 2 (q % npo).
