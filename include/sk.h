@@ -54,6 +54,7 @@ enum { SK_FP32 = 0, SK_FP64 = 1 };          /* precision of spreading / FFT / in
 enum { SK_METHOD_NFFT = 0, SK_METHOD_DIRECT = 1 };
 enum { SK_DOMAIN_SCALING = 0, SK_DOMAIN_LOG = 1 };   /* state of the iteration: Alg. 3 or Alg. 4 */
 enum { SK_KERNELS_SIMT = 0, SK_KERNELS_TENSOR = 1 };   /* interpolation on CUDA cores or tensor cores */
+enum { SK_FFT_PASSES = 0, SK_FFT_PLANES = 1 };         /* 3-D FFT: five pass launches or three with cluster planes */
 enum { SK_FAULT_NONE = 0, SK_FAULT_TC_WAIT = 1 };      /* sk_inject_fault (test hook) */
 enum { SK_SET_X = 0, SK_SET_Y = 1 };        /* which point cloud a stage entry point acts on */
 
@@ -124,6 +125,7 @@ typedef struct {
     int n_subproblems_x, n_subproblems_y;   /* work items of the per-point spreading kernels (1-D; 3-D with m_w > 5) */
     int64_t device_bytes;        /* device memory the plan holds */
     int tensor_cores;            /* 1: interpolation runs on tensor cores (sk_set_kernels) */
+    int fft_planes;              /* 1: the 3-D FFT runs as three launches with cluster planes (sk_set_fft) */
 } sk_info;
 
 /* Text for a status code (static storage, never NULL). */
@@ -193,6 +195,21 @@ int sk_set_domain(sk_plan* plan, int domain);
  * return SK_ERR_TIMEOUT when they read results back.
  */
 int sk_set_kernels(sk_plan* plan, int kernels);
+
+/*
+ * Choose how the FFT part of a 3-D product (Eq. (fastsum): the transform of the
+ * spread grid, the multiply by the kernel's Fourier coefficients, the inverse
+ * transform) is launched.  SK_FFT_PASSES: one launch per axis pass -- r2c along
+ * z, forward y, the axis-0 pass with the multiply, inverse y, c2r along z.
+ * SK_FFT_PLANES (the default where supported: SK_FP32 plans with d = 3 and
+ * n_os = 64, 128 or 256): the two passes on each side of the axis-0 pass run
+ * per x-plane in one launch, a thread-block cluster per plane exchanging the
+ * plane through distributed shared memory -- three launches.  Both compute the
+ * same transforms in the same order of operations per pencil.
+ * Errors: SK_ERR_ARG for a NULL plan or an unknown value; SK_ERR_UNSUPPORTED
+ * for SK_FFT_PLANES on a plan it does not support (nothing changes).
+ */
+int sk_set_fft(sk_plan* plan, int form);
 
 /*
  * Autotuner for the interpolation kernels: times one product K v (three

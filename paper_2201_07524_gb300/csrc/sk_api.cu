@@ -702,6 +702,7 @@ void build_grid(sk_plan* P) {
             f.hi[t] = 0;
         }
     }
+    f.planes = fft_planes_supported(f, sizeof(T) == 4);
 }
 
 template <typename T>
@@ -1493,6 +1494,17 @@ int sk_set_kernels(sk_plan* P, int kernels) {
     return SK_OK;
 }
 
+int sk_set_fft(sk_plan* P, int form) {
+    if (!P || (form != SK_FFT_PASSES && form != SK_FFT_PLANES)) return SK_ERR_ARG;
+    const bool planes = form == SK_FFT_PLANES;
+    if (planes && !fft_planes_supported(P->fft, P->precision == SK_FP32)) return SK_ERR_UNSUPPORTED;
+    if (planes != P->fft.planes) {
+        destroy_graph(P);
+        P->fft.planes = planes;
+    }
+    return SK_OK;
+}
+
 int sk_autotune(sk_plan* P, int* chosen, void* stream) {
     if (!P) return SK_ERR_ARG;
     try {
@@ -1886,6 +1898,7 @@ int sk_plan_info(const sk_plan* P, sk_info* info) {
     info->n_subproblems_y = P->Y.nsub;
     info->device_bytes = P->bytes;
     info->tensor_cores = P->tc ? 1 : 0;
+    info->fft_planes = P->fft.planes ? 1 : 0;
     return SK_OK;
 }
 

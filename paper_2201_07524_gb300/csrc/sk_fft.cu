@@ -35,6 +35,8 @@
 //   3-D: r2c(z) -> fwd(y, keep 2h+1) -> [fwd(x) * M, inv(x)] -> inv(y) -> c2r(z)
 //   2-D: r2c(y) -> [fwd(x) * M, inv(x)] -> c2r(y)
 //   1-D: r2c(x) -> * M -> c2r(x)            (the grid carries a second, zero row)
+#include <algorithm>
+
 #include "sk_internal.cuh"
 
 namespace sk {
@@ -727,6 +729,211 @@ __global__ void __launch_bounds__(512) k_fft_axis0_convolve(typename Cplx<T>::ty
                                 int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
 
+// ------------------------------------------------------------ cluster planes
+// In 3-D the two grid-side passes on each side of the axis-0 pass -- r2c along
+// z then the forward y-transform, and the inverse y-transform then c2r along
+// z -- touch one x-plane at a time, so they are done per plane by a
+// thread-block cluster of CL blocks that hand the plane over through
+// distributed shared memory instead of through global memory and a second
+// launch.  Block r of a plane's cluster owns the row pairs
+// [r pp, (r+1) pp) of the band (z-pencils, two real rows per complex FFT) and
+// the kz-columns [r kp, (r+1) kp) (y-pencils, FULL along y).  Front: each
+// block transforms its row pairs, splits them into half spectra and stores
+// every (y, kz) value into the y-pencil of the block owning kz; after the
+// cluster barrier each block transforms its y-pencils and writes the kept
+// frequencies -h..h (CENTERED) to the spectrum.  Back: the reverse, with the
+// Hermitian packing of two rows into one complex z-pencil done at the
+// exchange.  Positions no block writes (y outside the band; z-frequencies
+// h+1 .. n-h-1) are zeroed by their owner before the first cluster barrier,
+// which also makes sure every block of the cluster is running before any
+// block stores into its shared memory.
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// The two halves of the cluster barrier (every thread of every block of the
+// cluster takes part): arrive releases this thread's earlier shared-memory
+// writes, wait acquires those of every thread that arrived.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// Shared-memory address of `p` (this block's shared memory) in block `rank`
+// of the cluster, and a store of a complex FP32 value there.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, unsigned rank) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// A 3-D plan's band as the cluster kernels see it: planes x0 .. x0 + gridDim.x / CL
+// - 1, row pairs (ylo + 2 j, ylo + 2 j + 1) for j < np, pp row pairs and kp
+// kz-columns per block, h = N/2.
+struct Plane3 {
+    int x0, ylo, np, pp, kp, h;
+};
+
+// Threads per block are PU * (N/8): PU = max(pp, kp) pencils of each kind.
+template <int L2, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
+    k_fft_front3(float* __restrict__ g, float2* __restrict__ A2, Plane3 pl, const float2* __restrict__ tw) {
+    constexpr int N = 1 << L2, NS = fft_stride(N), PER = N / 8;
+    const int H = pl.h + 1, K = 2 * pl.h + 1;
+    const int tid = int(threadIdx.x), nthr = int(blockDim.x), PU = nthr / PER;
+    const int r = int(cluster_ctarank());
+    const int64_t x = pl.x0 + int(blockIdx.x) / CL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* rbuf = reinterpret_cast<float2*>(smem_raw);   // PU z-pencils (this block's row pairs)
+    float2* ybuf = rbuf + PU * NS;                        // PU y-pencils (this block's kz-columns)
+    const int yhi = pl.ylo + 2 * pl.np;
+    for (int e = tid; e < PU * N; e += nthr) {
+        const int p = e >> L2, y = e & (N - 1);
+        if (y < pl.ylo || y >= yhi || p >= pl.kp || r * pl.kp + p >= H) ybuf[p * NS + pidx(y)] = make_float2(0.f, 0.f);
+    }
+    cluster_arrive();
+
+    // this block's row pairs into z-pencils (4 consecutive z per item); the
+    // grid rows are zeroed after reading, for the next spreading
+    constexpr int G4 = N / 4, IPT = G4 / PER;   // items per thread: 2
+    float4 va[IPT], vb[IPT];
+    int64_t at[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const int e = tid + i * nthr;
+        const int p = e / G4, c = e - p * G4;
+        const int j = r * pl.pp + p;
+        at[i] = -1;
+        va[i] = vb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < pl.pp && j < pl.np) {
+            at[i] = (x * N + (pl.ylo + 2 * j)) * N + 4 * c;
+            va[i] = __ldcg(reinterpret_cast<const float4*>(g + at[i]));
+            vb[i] = __ldcg(reinterpret_cast<const float4*>(g + at[i] + N));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const int e = tid + i * nthr;
+        const int p = e / G4, c = e - p * G4;
+        if (at[i] >= 0) {
+            *reinterpret_cast<float4*>(g + at[i]) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(g + at[i] + N) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float2* dst = rbuf + p * NS + pidx(4 * c);   // 4 c .. 4 c + 3 share one pad
+        dst[0] = make_float2(va[i].x, vb[i].x);
+        dst[1] = make_float2(va[i].y, vb[i].y);
+        dst[2] = make_float2(va[i].z, vb[i].z);
+        dst[3] = make_float2(va[i].w, vb[i].w);
+    }
+    fft_stockham<float, false, SyncBlock, L2>(rbuf, NS, N, L2, tw, tid);
+    cluster_wait();
+
+    // half spectra of the two rows of pair j at kz = k, into the owner of column k
+    const int nv = max(0, min(pl.pp, pl.np - r * pl.pp));   // this block's valid pairs
+    for (int e = tid; e < nv * H; e += nthr) {
+        const int p = e / H, k = e - p * H;
+        const float2 zk = rbuf[p * NS + pidx(k)];
+        const float2 zm = rbuf[p * NS + pidx((N - k) & (N - 1))];
+        const float2 a = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
+        const float2 b = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
+        const int owner = k / pl.kp, col = k - owner * pl.kp;
+        const int y0 = pl.ylo + 2 * (r * pl.pp + p);
+        const uint32_t dst = cluster_addr(ybuf + col * NS + pidx(y0), unsigned(owner));
+        st_cluster(dst, a);
+        st_cluster(dst + uint32_t(sizeof(float2)), b);   // y0 even: y0 + 1 is the next slot
+    }
+    cluster_arrive();
+    cluster_wait();
+
+    fft_stockham<float, false, SyncBlock, L2>(ybuf, NS, N, L2, tw, tid);
+    const int kv = max(0, min(pl.kp, H - r * pl.kp));   // this block's valid columns
+    for (int e = tid; e < kv * K; e += nthr) {
+        const int ky = e / kv, p = e - ky * kv;
+        A2[(x * K + ky) * H + r * pl.kp + p] = ybuf[p * NS + pidx((ky - pl.h) & (N - 1))];
+    }
+}
+
+template <int L2, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
+    k_fft_back3(const float2* __restrict__ A2, float* __restrict__ gout, Plane3 pl, const float2* __restrict__ tw) {
+    constexpr int N = 1 << L2, NS = fft_stride(N), PER = N / 8;
+    const int H = pl.h + 1, K = 2 * pl.h + 1;
+    const int tid = int(threadIdx.x), nthr = int(blockDim.x), PU = nthr / PER;
+    const int r = int(cluster_ctarank());
+    const int64_t x = pl.x0 + int(blockIdx.x) / CL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* rbuf = reinterpret_cast<float2*>(smem_raw);   // PU z-pencils (this block's row pairs)
+    float2* ybuf = rbuf + PU * NS;                        // PU y-pencils (this block's kz-columns)
+    for (int e = tid; e < PU * N; e += nthr) {
+        const int p = e >> L2, z = e & (N - 1);
+        if ((z > pl.h && z < N - pl.h) || p >= pl.pp || r * pl.pp + p >= pl.np) rbuf[p * NS + pidx(z)] = make_float2(0.f, 0.f);
+    }
+    cluster_arrive();
+
+    // this block's kz-columns: frequencies -h..h along y, the rest zero
+    const int kv = max(0, min(pl.kp, H - r * pl.kp));
+    for (int e = tid; e < PU * N; e += nthr) {
+        const int p = e >> L2, y = e & (N - 1);
+        if ((y > pl.h && y < N - pl.h) || p >= kv) ybuf[p * NS + pidx(y)] = make_float2(0.f, 0.f);
+    }
+    for (int e0 = 0; e0 < kv * K; e0 += kFftLoadsPerRound * nthr) {
+        float2 v[kFftLoadsPerRound];
+#pragma unroll
+        for (int i = 0; i < kFftLoadsPerRound; ++i) {
+            const int e = e0 + i * nthr + tid;
+            if (e < kv * K) {
+                const int ky = e / kv, p = e - ky * kv;
+                v[i] = __ldcg(A2 + (x * K + ky) * H + r * pl.kp + p);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kFftLoadsPerRound; ++i) {
+            const int e = e0 + i * nthr + tid;
+            if (e < kv * K) {
+                const int ky = e / kv, p = e - ky * kv;
+                ybuf[p * NS + pidx((ky - pl.h) & (N - 1))] = v[i];
+            }
+        }
+    }
+    fft_stockham<float, true, SyncBlock, L2>(ybuf, NS, N, L2, tw, tid);
+    cluster_wait();
+
+    // rows y0, y0 + 1 of column kz packed into the z-pencil of pair j (its owner's)
+    for (int e = tid; e < kv * pl.np; e += nthr) {
+        const int j = e / kv, p = e - j * kv;
+        const int kz = r * pl.kp + p, y0 = pl.ylo + 2 * j;
+        float2 a = ybuf[p * NS + pidx(y0)], b = ybuf[p * NS + pidx(y0) + 1];
+        const int owner = j / pl.pp, slot = j - owner * pl.pp;
+        float2* pen = rbuf + slot * NS;
+        if (kz == 0) {
+            a.y = 0.f;
+            b.y = 0.f;
+        }
+        st_cluster(cluster_addr(pen + pidx(kz), unsigned(owner)), make_float2(a.x - b.y, a.y + b.x));
+        if (kz > 0) st_cluster(cluster_addr(pen + pidx(N - kz), unsigned(owner)), make_float2(a.x + b.y, b.x - a.y));
+    }
+    cluster_arrive();
+    cluster_wait();
+
+    fft_stockham<float, true, SyncBlock, L2>(rbuf, NS, N, L2, tw, tid);
+    constexpr int G4 = N / 4;
+    const int nv = max(0, min(pl.pp, pl.np - r * pl.pp));
+    for (int e = tid; e < nv * G4; e += nthr) {
+        const int p = e / G4, c = e - p * G4;
+        const float2* src = rbuf + p * NS + pidx(4 * c);
+        const float2 s0 = src[0], s1 = src[1], s2 = src[2], s3 = src[3];
+        float* row = gout + (x * N + (pl.ylo + 2 * (r * pl.pp + p))) * N + 4 * c;
+        *reinterpret_cast<float4*>(row) = make_float4(s0.x, s1.x, s2.x, s3.x);
+        *reinterpret_cast<float4*>(row + N) = make_float4(s0.y, s1.y, s2.y, s3.y);
+    }
+}
+
 // 1-D: multiply the half spectrum of row 0 by M[k], k = 0..h.
 template <typename T>
 __global__ void k_mult_half(typename Cplx<T>::type* __restrict__ A1, int h, const T* __restrict__ mult) {
@@ -955,10 +1162,95 @@ static cudaError_t run_axis0_convolve(const FftPlan& f, void* data, int64_t I, i
     return cudaErrorInvalidValue;
 }
 
+// Smallest cluster the plane kernels use (a plane's work split over at least
+// this many blocks, so that the ~60-120 planes of a band fill the GPU).
+constexpr int kPlaneClusterMin = 2;
+
+// Cluster size, band description and block size of the plane kernels for a
+// plan; false where they do not apply (FP32 3-D plans with n_os = 64, 128 or
+// 256, and at most 512 threads per block with clusters of up to 8).
+static bool plane_shape(const FftPlan& f, int& CL, Plane3& pl, int& threads) {
+    if (f.d != 3 || f.log2n < 6 || f.log2n > 8) return false;
+    const int H = f.h + 1, per = f.n / 8;
+    pl.x0 = f.lo[0];
+    pl.ylo = f.lo[1] & ~1;
+    pl.np = ((f.hi[1] | 1) - pl.ylo + 1) / 2;
+    pl.h = f.h;
+    for (CL = kPlaneClusterMin; CL <= 8; CL *= 2) {
+        pl.pp = (pl.np + CL - 1) / CL;
+        pl.kp = (H + CL - 1) / CL;
+        threads = std::max(pl.pp, pl.kp) * per;
+        if (threads <= 512) return true;
+    }
+    return false;
+}
+
+bool fft_planes_supported(const FftPlan& f, bool fp32) {
+    int CL, threads;
+    Plane3 pl;
+    return fp32 && plane_shape(f, CL, pl, threads);
+}
+
+// Opt a plane kernel into the shared memory of its largest block once per
+// device: 512 threads, i.e. 4096 / n pencils of each kind.
+template <auto Kern, int L2>
+static cudaError_t ensure_plane_smem() {
+    constexpr size_t bytes = size_t(2) * (512 / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
+    static unsigned long long configured = 0ull;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured & (1ull << (dev & 63))) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) configured |= (1ull << (dev & 63));
+    return e;
+}
+
+template <int L2, int CL>
+static cudaError_t run_planes_cl(const FftPlan& f, const Plane3& pl, int threads, int64_t* launches, cudaStream_t s) {
+    SK_TRY((ensure_plane_smem<k_fft_front3<L2, CL>, L2>()));
+    SK_TRY((ensure_plane_smem<k_fft_back3<L2, CL>, L2>()));
+    const int64_t H = f.h + 1, K = 2 * f.h + 1;
+    const unsigned blocks = unsigned((f.hi[0] - f.lo[0] + 1) * CL);
+    const size_t smem = size_t(2) * (threads / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
+    const float2* tw = static_cast<const float2*>(f.tw);
+    k_fft_front3<L2, CL><<<blocks, threads, smem, s>>>(static_cast<float*>(f.grid), static_cast<float2*>(f.A2), pl, tw);
+    if (launches) ++*launches;
+    SK_TRY(cudaGetLastError());
+    SK_TRY(run_axis0_convolve<float>(f, f.A2, K * H, launches, s));
+    k_fft_back3<L2, CL><<<blocks, threads, smem, s>>>(static_cast<const float2*>(f.A2), static_cast<float*>(f.grid_out),
+                                                     pl, tw);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+template <int L2>
+static cudaError_t run_planes_l(const FftPlan& f, int64_t* launches, cudaStream_t s) {
+    int CL, threads;
+    Plane3 pl;
+    if (!plane_shape(f, CL, pl, threads)) return cudaErrorInvalidValue;
+    if (CL == 2) return run_planes_cl<L2, 2>(f, pl, threads, launches, s);
+    if (CL == 4) return run_planes_cl<L2, 4>(f, pl, threads, launches, s);
+    return run_planes_cl<L2, 8>(f, pl, threads, launches, s);
+}
+
+// 3-D FP32 product with the plane kernels: front (r2c z, forward y), the
+// axis-0 pass with the multiply, back (inverse y, c2r z): three launches.
+static cudaError_t run_planes(const FftPlan& f, int64_t* launches, cudaStream_t s) {
+    switch (f.log2n) {
+        case 6: return run_planes_l<6>(f, launches, s);
+        case 7: return run_planes_l<7>(f, launches, s);
+        case 8: return run_planes_l<8>(f, launches, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename T>
 cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches) {
     using C = typename Cplx<T>::type;
     const int64_t n = f.n, H = f.h + 1, K = 2 * f.h + 1;
+    if constexpr (sizeof(T) == 4) {
+        if (f.planes) return run_planes(f, launches, s);
+    }
     if (f.d == 1) {
         SK_TRY(run_r2c<T>(f, launches, s));
         k_mult_half<T><<<unsigned((H + 255) / 256), 256, 0, s>>>(static_cast<C*>(f.A1), f.h,

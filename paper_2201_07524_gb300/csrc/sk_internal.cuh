@@ -220,6 +220,7 @@ struct FftPlan {
     void* mult = nullptr;     // T*
     void* tw = nullptr;       // Cplx<T>*, the stage twiddle rows (fft_twiddle_rows<T>(n) entries)
     const double* psihat = nullptr;  // 2h+1 values psihat_n(k/n), k = -h..h (FP64)
+    bool planes = false;      // 3-D FP32: the grid-side passes by thread-block-cluster planes (three launches)
 };
 
 // ----------------------------------------------------------------- launchers
@@ -245,6 +246,7 @@ cudaError_t launch_interp_tc(int d, int W, const InterpArgs& a, const Epilogue& 
 int interp_tc_blocks(int d, int W, int ntasks);
 void bin_shape(int d, int W, int B[3]);
 template <typename T> cudaError_t launch_fft_convolve(const FftPlan& f, cudaStream_t s, int64_t* launches);
+bool fft_planes_supported(const FftPlan& f, bool fp32);
 template <typename T> int fft_twiddle_rows(int n);
 template <typename T> cudaError_t launch_twiddle_rows(void* rows, int n, cudaStream_t s);
 template <typename T> cudaError_t launch_fft_adjoint(const FftPlan& f, double* fhat, cudaStream_t s,

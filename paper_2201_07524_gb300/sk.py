@@ -26,6 +26,7 @@ SK_FP32, SK_FP64 = 0, 1
 SK_METHOD_NFFT, SK_METHOD_DIRECT = 0, 1
 SK_DOMAIN_SCALING, SK_DOMAIN_LOG = 0, 1
 SK_KERNELS_SIMT, SK_KERNELS_TENSOR = 0, 1
+SK_FFT_PASSES, SK_FFT_PLANES = 0, 1
 SK_FAULT_NONE, SK_FAULT_TC_WAIT = 0, 1
 SK_SET_X, SK_SET_Y = 0, 1
 SK_STAGE_SPREAD, SK_STAGE_FFT, SK_STAGE_INTERP, SK_STAGE_OTHER, SK_STAGE_DIRECT, SK_STAGE_NEAR = 0, 1, 2, 3, 4, 5
@@ -51,7 +52,8 @@ class sk_info(ctypes.Structure):
                 ("nearfield", ctypes.c_int), ("eps", ctypes.c_double), ("r", ctypes.c_double),
                 ("eps_scaled", ctypes.c_double), ("center", ctypes.c_double * 3), ("scale", ctypes.c_double),
                 ("eps_B", ctypes.c_double), ("eps_I", ctypes.c_double), ("n_subproblems_x", ctypes.c_int),
-                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("tensor_cores", ctypes.c_int)]
+                ("n_subproblems_y", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("tensor_cores", ctypes.c_int),
+                ("fft_planes", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -67,6 +69,7 @@ _SIGS = {
     "sk_set_method": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_set_domain": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_set_kernels": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sk_set_fft": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_inject_fault": (ctypes.c_int, [_P, ctypes.c_int]),
     "sk_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _S]),
     "sk_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _S]),
@@ -215,6 +218,10 @@ def sk_set_domain(plan, domain):
 
 def sk_set_kernels(plan, kernels):
     _check(_lib.sk_set_kernels(plan.handle, int(kernels)), "sk_set_kernels")
+
+
+def sk_set_fft(plan, form):
+    _check(_lib.sk_set_fft(plan.handle, int(form)), "sk_set_fft")
 
 
 def sk_autotune(plan, stream=None):

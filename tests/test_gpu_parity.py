@@ -368,6 +368,54 @@ def test_kernel_apply_longest_pencils(d, N, precision):
     assert efs(t, osk.kernel_apply(x, y, v, eps, 2.0)) <= TOL_FS[precision]
 
 
+@pytest.mark.parametrize("N,radius,m_w", [(32, 0.2, 4), (64, 0.2, 4), (128, 0.2, 4), (64, 0.2, 8),
+                                           (64, 0.004, 4), (32, 0.24, 4)])
+def test_3d_fft_planes_match_passes_and_exact_sums(N, radius, m_w):
+    # the cluster-plane FFT (three launches) against the five pass launches on
+    # the same plan, and both against the exact sums: n_os = 64, 128, 256; a
+    # band of ~0.5 n_os, a band of a few cells (points in a radius-0.004 ball)
+    # and a wide one (points near the edge of the valid region)
+    x = wl.uniform_ball(2100, 3, radius, 41)
+    y = wl.uniform_ball(1900, 3, radius, 42)
+    eps = 0.02
+    plan = plan_for(x, y, eps=eps, N=N, m_w=m_w, precision=sk.SK_FP32)
+    assert sk.sk_plan_info(plan)["fft_planes"] == 1
+    v = wl.positive_vector(len(y), 43)
+    u = wl.positive_vector(len(x), 44)
+    out = {}
+    for form in (sk.SK_FFT_PLANES, sk.SK_FFT_PASSES):
+        sk.sk_set_fft(plan, form)
+        t, tt = np.zeros(len(x)), np.zeros(len(y))
+        sk.sk_kernel_apply(plan, 0, v, t)
+        sk.sk_kernel_apply(plan, 1, u, tt)
+        out[form] = (t, tt)
+    exact = (osk.kernel_apply(x, y, v, eps, 2.0), osk.kernel_apply_T(x, y, u, eps, 2.0))
+    for k in range(2):
+        a, b = out[sk.SK_FFT_PLANES][k], out[sk.SK_FFT_PASSES][k]
+        assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
+        assert efs(a, exact[k]) <= TOL_FS[sk.SK_FP32]
+        assert efs(b, exact[k]) <= TOL_FS[sk.SK_FP32]
+
+
+def test_fft_form_selection_errors():
+    x = wl.uniform_ball(300, 3, 0.2, 45)
+    y = wl.uniform_ball(200, 3, 0.2, 46)
+    p64 = plan_for(x, y, precision=sk.SK_FP64)
+    assert sk.sk_plan_info(p64)["fft_planes"] == 0
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_set_fft(p64, sk.SK_FFT_PLANES)
+    assert e.value.status == sk.SK_ERR_UNSUPPORTED
+    sk.sk_set_fft(p64, sk.SK_FFT_PASSES)
+    p2 = plan_for(x[:, :2], y[:, :2], precision=sk.SK_FP32)
+    assert sk.sk_plan_info(p2)["fft_planes"] == 0
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_set_fft(p2, sk.SK_FFT_PLANES)
+    assert e.value.status == sk.SK_ERR_UNSUPPORTED
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_set_fft(p64, 7)
+    assert e.value.status == sk.SK_ERR_ARG
+
+
 def test_kernel_apply_host_buffers_and_ragged_tiny_sizes():
     # host (numpy) in/out buffers; sizes below one block and not multiples of anything
     for n, m in [(1, 1), (1, 5), (7, 1), (33, 65)]:
@@ -536,7 +584,13 @@ def test_launch_count_and_stage_timing():
     sk.sk_solve(plan, 4, result=False)
     torch.cuda.synchronize()
     per_iter = (sk.sk_launch_count(plan) - c0) / 4
-    assert per_iter == 2 * (1 + 5 + 1)        # spread, 5 FFT passes, interp per half-step (3-D)
+    assert sk.sk_plan_info(plan)["fft_planes"] == 1
+    assert per_iter == 2 * (1 + 3 + 1)        # spread, 3 FFT launches (cluster planes), interp per half-step
+    sk.sk_set_fft(plan, sk.SK_FFT_PASSES)
+    c0 = sk.sk_launch_count(plan)
+    sk.sk_solve(plan, 2, result=False)
+    torch.cuda.synchronize()
+    assert (sk.sk_launch_count(plan) - c0) / 2 == 2 * (1 + 5 + 1)   # 5 FFT passes
     sk.sk_stage_times(plan, 1)
     sk.sk_solve(plan, 3, result=False)
     times = sk.sk_stage_times(plan, 0)
