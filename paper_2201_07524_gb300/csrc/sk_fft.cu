@@ -313,6 +313,82 @@ __device__ void fft_stockham(typename Cplx<T>::type* buf, int ns, int n, int log
     }
 }
 
+// A stage as above, out of place: it reads `in` and writes `out`, so only the
+// barrier after the writes is needed (the next stage reads `out`).
+template <typename C, bool INV, int R, int E, class S>
+__device__ __forceinline__ void stockham_stage2(const C* in, C* out, int n, int Ns, int t, const C* __restrict__ rows) {
+    constexpr int B = E / R;
+    constexpr int RW = row_width(R);
+    const int stride = n / R, per = n / E;
+    C x[E];
+    C w[B][RW];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int jj = t + b * per;
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[b * R + r] = in[pidx(jj + r * stride)];
+        if (Ns > 1) load_row<C, RW>(rows + (jj & (Ns - 1)) * RW, w[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int jj = t + b * per;
+        const int k = jj & (Ns - 1);
+        if (Ns > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C wq = w[b][q - 1];
+                if (INV) wq.y = -wq.y;
+                x[b * R + q] = cmul(x[b * R + q], wq);
+            }
+        }
+        if (R == 8) dft8<C, INV>(x + b * R);
+        else if (R == 4) dft4<C, INV>(x + b * R);
+        else dft2<C, INV>(x + b * R);
+        const int base = (jj - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[pidx(base + r * Ns)] = x[b * R + r];
+    }
+    S::sync();
+}
+
+template <typename C, bool INV, int E, class S, int N, int NS, int REM>
+__device__ __forceinline__ void stages_ct2(C* in, C* out, int t, const C* __restrict__ rows) {
+    constexpr int LE = E == 8 ? 3 : 2;
+    if constexpr (REM >= LE) {
+        stockham_stage2<C, INV, E, E, S>(in, out, N, NS, t, rows);
+        stages_ct2<C, INV, E, S, N, NS * E, REM - LE>(out, in, t, NS > 1 ? rows + NS * row_width(E) : rows);
+    } else if constexpr (REM == 2) {
+        stockham_stage2<C, INV, 4, E, S>(in, out, N, NS, t, rows);
+    } else if constexpr (REM == 1) {
+        stockham_stage2<C, INV, 2, E, S>(in, out, N, NS, t, rows);
+    }
+}
+
+// Stages of an N = 2^L2 point transform with E elements per thread.
+__host__ __device__ constexpr int fft_stages(int L2, int E) {
+    return E == 8 ? L2 / 3 + (L2 % 3 != 0) : L2 / 2 + (L2 % 2 != 0);
+}
+
+// The unit's transform with two pencil buffers, `a` (input) and `b` (same
+// layout): the stages alternate between them, one barrier each.  Returns the
+// buffer holding the result.  Lengths not known at compile time (L2 = 0) are
+// transformed in place in `a`.
+template <typename T, bool INV, class S, int L2>
+__device__ typename Cplx<T>::type* fft_stockham2(typename Cplx<T>::type* a, typename Cplx<T>::type* b, int ns, int n,
+                                                 int log2n, const typename Cplx<T>::type* rows, int tid) {
+    using C = typename Cplx<T>::type;
+    if constexpr (L2 > 0) {
+        constexpr int N = 1 << L2, E = fft_ept<T>(N), PER = N / E, NSP = fft_stride(N);
+        S::sync();
+        const int p = tid / PER, t = tid - p * PER;
+        stages_ct2<C, INV, E, S, N, 1, L2>(a + p * NSP, b + p * NSP, t, rows);
+        return (fft_stages(L2, E) % 2) ? b : a;
+    } else {
+        fft_stockham<T, INV, S, L2>(a, ns, n, log2n, rows, tid);
+        return a;
+    }
+}
+
 // Entries (complex) of the stage twiddle table of an n-point transform, and
 // the table itself (computed in FP64 and rounded; one launch per stage).
 template <typename T>
@@ -369,7 +445,8 @@ template int fft_twiddle_rows<double>(int);
 template cudaError_t launch_twiddle_rows<float>(void*, int, cudaStream_t);
 template cudaError_t launch_twiddle_rows<double>(void*, int, cudaStream_t);
 
-// Shared memory of an FFT block: P pencils of fft_stride(n) slots.
+// Shared memory of an FFT block: two buffers of P pencils of fft_stride(n)
+// slots each (the input and the other buffer of fft_stockham2).
 template <typename T>
 struct FftSmem {
     using C = typename Cplx<T>::type;
@@ -386,8 +463,9 @@ constexpr int kFftLoadsPerRound = 8;
 
 // The passes below are written for one FFT unit: `nthr` threads (a block of a
 // pass kernel) that transform the P pencils starting at pencil (or row pair)
-// q0, thread `tid` of the unit, staging in `buf` (P pencils of fft_stride(n)
-// slots), with its barrier S::sync().  Data written by the previous pass is
+// q0, thread `tid` of the unit, staging in `buf` (two buffers of P pencils of
+// fft_stride(n) slots, the transform alternating between them), with its
+// barrier S::sync().  Data written by the previous pass is
 // read once, with ld.global.cg (cached in L2 only).  Index arithmetic is
 // 32-bit and free of divisions in the per-element loops (the pencil a thread
 // works on is fixed per unit, the pencil count P is a power of two): a 64-bit
@@ -436,7 +514,7 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
             buf[(e >> log2n) * ns + pidx(e & (n - 1))] = z[j];
         }
     }
-    fft_stockham<T, false, S, L2>(buf, ns, n, log2n, tw, tid);
+    const C* res = fft_stockham2<T, false, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
     const int H = h + 1;
     // element e = p H + k of the output, walked without a division per element
     int p = tid / H, k = tid - (tid / H) * H;
@@ -445,8 +523,8 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
         const int q = q0 + p;
         if (q < rp.npairs) {
             const int64_t r0 = rc.get(rp, q);
-            const C zk = buf[p * ns + pidx(k)];
-            const C zm = buf[p * ns + pidx((n - k) & (n - 1))];
+            const C zk = res[p * ns + pidx(k)];
+            const C zm = res[p * ns + pidx((n - k) & (n - 1))];
             C A, Bv;
             A.x = (zk.x + zm.x) * T(0.5);
             A.y = (zk.y - zm.y) * T(0.5);
@@ -522,14 +600,14 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
             buf[(e >> log2n) * ns + pidx(pos)] = z;
         }
     }
-    fft_stockham<T, true, S, L2>(buf, ns, n, log2n, tw, tid);
+    const C* res = fft_stockham2<T, true, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
     for (int e = tid; e < P * n; e += nthr) {
         const int p = e >> log2n;
         const int l = e & (n - 1);
         const int q = q0 + p;
         if (q >= rp.npairs) continue;
         const int64_t r0 = rc.get(rp, q);
-        const C v = buf[p * ns + pidx(l)];
+        const C v = res[p * ns + pidx(l)];
         g[r0 * n + l] = v.x;
         g[(r0 + 1) * n + l] = v.y;
     }
@@ -593,12 +671,12 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
             buf[pl * ns + pidx(pos)] = v[j];
         }
     }
-    fft_stockham<T, INV, S, L2>(buf, ns, n, log2n, tw, tid);
+    const C* res = fft_stockham2<T, INV, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
     if (!qok) return;
     for (int e = tid; e < P * kn; e += nthr) {
         const int k = k0 + (e >> lp);
         const int pos = OUTM == FULL ? k : ((k - h) & (n - 1));
-        dst[int64_t(k) * I] = buf[pl * ns + pidx(pos)];
+        dst[int64_t(k) * I] = res[pl * ns + pidx(pos)];
     }
 }
 
@@ -651,14 +729,14 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
         const int k = pos <= (n >> 1) ? pos : pos - n;
         mv[j] = (one_round && e < P * n && q < I && k >= -h && k <= h) ? mult[int64_t(k + h) * I + q] : T(0);
     }
-    fft_stockham<T, false, S, L2>(buf, ns, n, log2n, tw, tid);
+    C* res = fft_stockham2<T, false, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
     if (one_round) {
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
             const int e = j * nthr + tid;
             if (e >= P * n) continue;
             const int pos = e >> lp;
-            C& v = buf[(e & (P - 1)) * ns + pidx(pos)];
+            C& v = res[(e & (P - 1)) * ns + pidx(pos)];
             v.x *= mv[j];
             v.y *= mv[j];
         }
@@ -668,7 +746,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
             const int pl = e & (P - 1);
             const int q = q0 + pl;
             const int k = pos <= (n >> 1) ? pos : pos - n;
-            C& v = buf[pl * ns + pidx(pos)];
+            C& v = res[pl * ns + pidx(pos)];
             if (q < I && k >= -h && k <= h) {
                 const T m = mult[int64_t(k + h) * I + q];
                 v.x *= m;
@@ -679,12 +757,12 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
             }
         }
     }
-    fft_stockham<T, true, S, L2>(buf, ns, n, log2n, tw, tid);
+    const C* res2 = fft_stockham2<T, true, S, L2>(res, res == buf ? buf + P * ns : buf, ns, n, log2n, tw, tid);
     for (int e = tid; e < P * xcnt; e += nthr) {
         const int k = xlo + (e >> lp);
         const int pl = e & (P - 1);
         const int q = q0 + pl;
-        if (q < I) data[int64_t(k) * I + q] = buf[pl * ns + pidx(k)];
+        if (q < I) data[int64_t(k) * I + q] = res2[pl * ns + pidx(k)];
     }
 }
 
@@ -791,7 +869,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int64_t x = pl.x0 + int(blockIdx.x) / CL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* rbuf = reinterpret_cast<float2*>(smem_raw);   // PU z-pencils (this block's row pairs)
-    float2* ybuf = rbuf + PU * NS;                        // PU y-pencils (this block's kz-columns)
+    float2* ybuf = rbuf + 2 * PU * NS;                    // PU y-pencils (this block's kz-columns)
     const int yhi = pl.ylo + 2 * pl.np;
     for (int e = tid; e < PU * N; e += nthr) {
         const int p = e >> L2, y = e & (N - 1);
@@ -831,15 +909,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
         dst[2] = make_float2(va[i].z, vb[i].z);
         dst[3] = make_float2(va[i].w, vb[i].w);
     }
-    fft_stockham<float, false, SyncBlock, L2>(rbuf, NS, N, L2, tw, tid);
+    const float2* zr = fft_stockham2<float, false, SyncBlock, L2>(rbuf, rbuf + PU * NS, NS, N, L2, tw, tid);
     cluster_wait();
 
     // half spectra of the two rows of pair j at kz = k, into the owner of column k
     const int nv = max(0, min(pl.pp, pl.np - r * pl.pp));   // this block's valid pairs
     for (int e = tid; e < nv * H; e += nthr) {
         const int p = e / H, k = e - p * H;
-        const float2 zk = rbuf[p * NS + pidx(k)];
-        const float2 zm = rbuf[p * NS + pidx((N - k) & (N - 1))];
+        const float2 zk = zr[p * NS + pidx(k)];
+        const float2 zm = zr[p * NS + pidx((N - k) & (N - 1))];
         const float2 a = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
         const float2 b = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
         const int owner = k / pl.kp, col = k - owner * pl.kp;
@@ -851,11 +929,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     cluster_arrive();
     cluster_wait();
 
-    fft_stockham<float, false, SyncBlock, L2>(ybuf, NS, N, L2, tw, tid);
+    const float2* zy = fft_stockham2<float, false, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid);
     const int kv = max(0, min(pl.kp, H - r * pl.kp));   // this block's valid columns
     for (int e = tid; e < kv * K; e += nthr) {
         const int ky = e / kv, p = e - ky * kv;
-        A2[(x * K + ky) * H + r * pl.kp + p] = ybuf[p * NS + pidx((ky - pl.h) & (N - 1))];
+        A2[(x * K + ky) * H + r * pl.kp + p] = zy[p * NS + pidx((ky - pl.h) & (N - 1))];
     }
 }
 
@@ -869,7 +947,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int64_t x = pl.x0 + int(blockIdx.x) / CL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* rbuf = reinterpret_cast<float2*>(smem_raw);   // PU z-pencils (this block's row pairs)
-    float2* ybuf = rbuf + PU * NS;                        // PU y-pencils (this block's kz-columns)
+    float2* ybuf = rbuf + 2 * PU * NS;                    // PU y-pencils (this block's kz-columns)
     for (int e = tid; e < PU * N; e += nthr) {
         const int p = e >> L2, z = e & (N - 1);
         if ((z > pl.h && z < N - pl.h) || p >= pl.pp || r * pl.pp + p >= pl.np) rbuf[p * NS + pidx(z)] = make_float2(0.f, 0.f);
@@ -901,14 +979,14 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
             }
         }
     }
-    fft_stockham<float, true, SyncBlock, L2>(ybuf, NS, N, L2, tw, tid);
+    const float2* zy = fft_stockham2<float, true, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid);
     cluster_wait();
 
     // rows y0, y0 + 1 of column kz packed into the z-pencil of pair j (its owner's)
     for (int e = tid; e < kv * pl.np; e += nthr) {
         const int j = e / kv, p = e - j * kv;
         const int kz = r * pl.kp + p, y0 = pl.ylo + 2 * j;
-        float2 a = ybuf[p * NS + pidx(y0)], b = ybuf[p * NS + pidx(y0) + 1];
+        float2 a = zy[p * NS + pidx(y0)], b = zy[p * NS + pidx(y0) + 1];
         const int owner = j / pl.pp, slot = j - owner * pl.pp;
         float2* pen = rbuf + slot * NS;
         if (kz == 0) {
@@ -921,12 +999,12 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     cluster_arrive();
     cluster_wait();
 
-    fft_stockham<float, true, SyncBlock, L2>(rbuf, NS, N, L2, tw, tid);
+    const float2* zr = fft_stockham2<float, true, SyncBlock, L2>(rbuf, rbuf + PU * NS, NS, N, L2, tw, tid);
     constexpr int G4 = N / 4;
     const int nv = max(0, min(pl.pp, pl.np - r * pl.pp));
     for (int e = tid; e < nv * G4; e += nthr) {
         const int p = e / G4, c = e - p * G4;
-        const float2* src = rbuf + p * NS + pidx(4 * c);
+        const float2* src = zr + p * NS + pidx(4 * c);
         const float2 s0 = src[0], s1 = src[1], s2 = src[2], s3 = src[3];
         float* row = gout + (x * N + (pl.ylo + 2 * (r * pl.pp + p))) * N + 4 * c;
         *reinterpret_cast<float4*>(row) = make_float4(s0.x, s1.x, s2.x, s3.x);
@@ -1000,14 +1078,14 @@ __global__ void k_fill_forward(const double* __restrict__ fhat, int d, int h, co
 
 template <typename T>
 static size_t fft_smem_bytes(int n) {
-    return size_t(fft_pencils(n)) * size_t(fft_stride(n)) * sizeof(typename Cplx<T>::type);
+    return 2 * size_t(fft_pencils(n)) * size_t(fft_stride(n)) * sizeof(typename Cplx<T>::type);
 }
 
 // Largest dynamic shared memory any FFT launch of this precision can use:
-// one pencil of the largest length, 4096.
+// two buffers of one pencil of the largest length, 4096.
 template <typename T>
 static size_t fft_smem_max() {
-    return size_t(fft_stride(4096)) * sizeof(typename Cplx<T>::type);
+    return 2 * size_t(fft_stride(4096)) * sizeof(typename Cplx<T>::type);
 }
 
 // Opt a kernel into its largest shared-memory size once per device (the cache
@@ -1192,10 +1270,10 @@ bool fft_planes_supported(const FftPlan& f, bool fp32) {
 }
 
 // Opt a plane kernel into the shared memory of its largest block once per
-// device: 512 threads, i.e. 4096 / n pencils of each kind.
+// device: 512 threads, i.e. 4096 / n pencils of each kind, two buffers each.
 template <auto Kern, int L2>
 static cudaError_t ensure_plane_smem() {
-    constexpr size_t bytes = size_t(2) * (512 / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
+    constexpr size_t bytes = size_t(4) * (512 / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
     static unsigned long long configured = 0ull;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1211,7 +1289,7 @@ static cudaError_t run_planes_cl(const FftPlan& f, const Plane3& pl, int threads
     SK_TRY((ensure_plane_smem<k_fft_back3<L2, CL>, L2>()));
     const int64_t H = f.h + 1, K = 2 * f.h + 1;
     const unsigned blocks = unsigned((f.hi[0] - f.lo[0] + 1) * CL);
-    const size_t smem = size_t(2) * (threads / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
+    const size_t smem = size_t(4) * (threads / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
     const float2* tw = static_cast<const float2*>(f.tw);
     k_fft_front3<L2, CL><<<blocks, threads, smem, s>>>(static_cast<float*>(f.grid), static_cast<float2*>(f.A2), pl, tw);
     if (launches) ++*launches;
