@@ -313,21 +313,83 @@ __device__ void fft_stockham(typename Cplx<T>::type* buf, int ns, int n, int log
     }
 }
 
-// A stage as above, out of place: it reads `in` and writes `out`, so only the
-// barrier after the writes is needed (the next stage reads `out`).
-template <typename C, bool INV, int R, int E, class S>
-__device__ __forceinline__ void stockham_stage2(const C* in, C* out, int n, int Ns, int t, const C* __restrict__ rows) {
+// Radix of the stage that finds REM of log2 n left to do (E elements per
+// thread): E while it fits, then 4 or 2.
+__host__ __device__ constexpr int fft_radix(int rem, int E) { return rem >= (E == 8 ? 3 : 2) ? E : (rem == 2 ? 4 : 2); }
+__host__ __device__ constexpr int fft_lg(int R) { return R == 8 ? 3 : (R == 4 ? 2 : 1); }
+
+// Stages of an N = 2^L2 point transform with E elements per thread, and the
+// twiddles one thread applies over all of them: a stage with Ns > 1 gives
+// each of the thread's E / R butterflies R - 1 values.
+__host__ __device__ constexpr int fft_stages(int L2, int E) {
+    int count = 0;
+    for (int rem = L2; rem > 0; rem -= fft_lg(fft_radix(rem, E))) ++count;
+    return count;
+}
+
+__host__ __device__ constexpr int fft_tw_count(int L2, int E) {
+    int count = 0, Ns = 1;
+    for (int rem = L2; rem > 0;) {
+        const int R = fft_radix(rem, E);
+        if (Ns > 1) count += (E / R) * (R - 1);
+        Ns *= R;
+        rem -= fft_lg(R);
+    }
+    return count;
+}
+
+// A thread's twiddles for every stage of an N = 2^L2 point transform, read
+// from the stage table into registers once per unit (before its data loads,
+// so their latency overlaps), so that no stage waits on a table load and the
+// unit's transforms of one direction or the other all reuse them.
+template <typename T, int L2>
+struct FftTw {
+    using C = typename Cplx<T>::type;
+    static constexpr int E = L2 > 0 ? fft_ept<T>(1 << L2) : 8;
+    static constexpr int COUNT = L2 > 0 ? fft_tw_count(L2, E) : 0;
+    static constexpr int SIZE = COUNT > 0 ? COUNT : 1;
+    C w[SIZE];
+
+    template <int N, int NS, int REM, int OFF>
+    __device__ __forceinline__ void load_ct(const C* __restrict__ rows, int t) {
+        if constexpr (REM > 0) {
+            constexpr int R = fft_radix(REM, E), B = E / R, RW = row_width(R), PER = N / E;
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    const int k = (t + b * PER) & (NS - 1);
+#pragma unroll
+                    for (int q = 1; q < R; ++q) w[OFF + b * (R - 1) + q - 1] = __ldg(rows + k * RW + q - 1);
+                }
+                load_ct<N, NS * R, REM - fft_lg(R), OFF + B * (R - 1)>(rows + NS * RW, t);
+            } else {
+                load_ct<N, NS * R, REM - fft_lg(R), OFF>(rows, t);
+            }
+        }
+    }
+
+    // thread `tid` of a unit (its index within its pencil is tid mod N/E)
+    __device__ __forceinline__ void load(const C* __restrict__ rows, int tid) {
+        if constexpr (L2 > 0) {
+            constexpr int N = 1 << L2;
+            load_ct<N, 1, L2, 0>(rows, tid & (N / E - 1));
+        }
+    }
+};
+
+// A stage as stockham_stage, out of place (reads `in`, writes `out`, so only
+// the barrier after the writes is needed) and with the thread's twiddles in
+// registers, from position OFF of `tw`.
+template <typename C, bool INV, int R, int E, class S, int OFF, int TWN>
+__device__ __forceinline__ void stockham_stage2(const C* in, C* out, int n, int Ns, int t, const C (&tw)[TWN]) {
     constexpr int B = E / R;
-    constexpr int RW = row_width(R);
     const int stride = n / R, per = n / E;
     C x[E];
-    C w[B][RW];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int jj = t + b * per;
 #pragma unroll
         for (int r = 0; r < R; ++r) x[b * R + r] = in[pidx(jj + r * stride)];
-        if (Ns > 1) load_row<C, RW>(rows + (jj & (Ns - 1)) * RW, w[b]);
     }
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -336,7 +398,7 @@ __device__ __forceinline__ void stockham_stage2(const C* in, C* out, int n, int 
         if (Ns > 1) {
 #pragma unroll
             for (int q = 1; q < R; ++q) {
-                C wq = w[b][q - 1];
+                C wq = tw[OFF + b * (R - 1) + q - 1];
                 if (INV) wq.y = -wq.y;
                 x[b * R + q] = cmul(x[b * R + q], wq);
             }
@@ -351,37 +413,31 @@ __device__ __forceinline__ void stockham_stage2(const C* in, C* out, int n, int 
     S::sync();
 }
 
-template <typename C, bool INV, int E, class S, int N, int NS, int REM>
-__device__ __forceinline__ void stages_ct2(C* in, C* out, int t, const C* __restrict__ rows) {
-    constexpr int LE = E == 8 ? 3 : 2;
-    if constexpr (REM >= LE) {
-        stockham_stage2<C, INV, E, E, S>(in, out, N, NS, t, rows);
-        stages_ct2<C, INV, E, S, N, NS * E, REM - LE>(out, in, t, NS > 1 ? rows + NS * row_width(E) : rows);
-    } else if constexpr (REM == 2) {
-        stockham_stage2<C, INV, 4, E, S>(in, out, N, NS, t, rows);
-    } else if constexpr (REM == 1) {
-        stockham_stage2<C, INV, 2, E, S>(in, out, N, NS, t, rows);
+template <typename C, bool INV, int E, class S, int N, int NS, int REM, int OFF, int TWN>
+__device__ __forceinline__ void stages_ct2(C* in, C* out, int t, const C (&tw)[TWN]) {
+    if constexpr (REM > 0) {
+        constexpr int R = fft_radix(REM, E);
+        constexpr int NEXT = (NS > 1) ? OFF + (E / R) * (R - 1) : OFF;
+        stockham_stage2<C, INV, R, E, S, OFF, TWN>(in, out, N, NS, t, tw);
+        stages_ct2<C, INV, E, S, N, NS * R, REM - fft_lg(R), NEXT, TWN>(out, in, t, tw);
     }
 }
 
-// Stages of an N = 2^L2 point transform with E elements per thread.
-__host__ __device__ constexpr int fft_stages(int L2, int E) {
-    return E == 8 ? L2 / 3 + (L2 % 3 != 0) : L2 / 2 + (L2 % 2 != 0);
-}
-
 // The unit's transform with two pencil buffers, `a` (input) and `b` (same
-// layout): the stages alternate between them, one barrier each.  Returns the
-// buffer holding the result.  Lengths not known at compile time (L2 = 0) are
-// transformed in place in `a`.
+// layout): the stages alternate between them, one barrier each, with the
+// twiddles `tw` holds.  Returns the buffer holding the result.  Lengths not
+// known at compile time (L2 = 0) are transformed in place in `a`, with the
+// twiddles read from the table `rows`.
 template <typename T, bool INV, class S, int L2>
 __device__ typename Cplx<T>::type* fft_stockham2(typename Cplx<T>::type* a, typename Cplx<T>::type* b, int ns, int n,
-                                                 int log2n, const typename Cplx<T>::type* rows, int tid) {
+                                                 int log2n, const typename Cplx<T>::type* rows, int tid,
+                                                 const FftTw<T, L2>& tw) {
     using C = typename Cplx<T>::type;
     if constexpr (L2 > 0) {
         constexpr int N = 1 << L2, E = fft_ept<T>(N), PER = N / E, NSP = fft_stride(N);
         S::sync();
         const int p = tid / PER, t = tid - p * PER;
-        stages_ct2<C, INV, E, S, N, 1, L2>(a + p * NSP, b + p * NSP, t, rows);
+        stages_ct2<C, INV, E, S, N, 1, L2, 0, FftTw<T, L2>::SIZE>(a + p * NSP, b + p * NSP, t, tw.w);
         return (fft_stages(L2, E) % 2) ? b : a;
     } else {
         fft_stockham<T, INV, S, L2>(a, ns, n, log2n, rows, tid);
@@ -486,6 +542,8 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
     const int P = fft_pencils(n);
     const int ns = fft_stride(n);
     S::sync();   // the unit's previous pencils have been read out of buf
+    FftTw<T, L2> twr;
+    twr.load(tw, tid);
     PairRowCache rc;
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * nthr) {
         C z[kFftLoadsPerRound];
@@ -514,7 +572,7 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
             buf[(e >> log2n) * ns + pidx(e & (n - 1))] = z[j];
         }
     }
-    const C* res = fft_stockham2<T, false, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
+    const C* res = fft_stockham2<T, false, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid, twr);
     const int H = h + 1;
     // element e = p H + k of the output, walked without a division per element
     int p = tid / H, k = tid - (tid / H) * H;
@@ -556,6 +614,8 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
     const int P = fft_pencils(n);
     const int ns = fft_stride(n);
     S::sync();   // the unit's previous pencils have been read out of buf
+    FftTw<T, L2> twr;
+    twr.load(tw, tid);
     const int H = h + 1;
     PairRowCache rc;
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * nthr) {
@@ -600,7 +660,7 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
             buf[(e >> log2n) * ns + pidx(pos)] = z;
         }
     }
-    const C* res = fft_stockham2<T, true, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
+    const C* res = fft_stockham2<T, true, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid, twr);
     for (int e = tid; e < P * n; e += nthr) {
         const int p = e >> log2n;
         const int l = e & (n - 1);
@@ -636,6 +696,8 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
     const int k0 = OUTM == FULL ? klo : 0;
     const int kn = OUTM == FULL ? kcnt : Lout;
     S::sync();   // the unit's previous pencils have been read out of buf
+    FftTw<T, L2> twr;
+    twr.load(tw, tid);
     // the unit's threads are a multiple of P, so a thread always works on
     // pencil pl = tid mod P of the unit: pencil (o, i), o = olo + q / I
     const int pl = tid & (P - 1);
@@ -671,7 +733,7 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
             buf[pl * ns + pidx(pos)] = v[j];
         }
     }
-    const C* res = fft_stockham2<T, INV, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
+    const C* res = fft_stockham2<T, INV, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid, twr);
     if (!qok) return;
     for (int e = tid; e < P * kn; e += nthr) {
         const int k = k0 + (e >> lp);
@@ -697,6 +759,8 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
     const int P = fft_pencils(n), lp = ilog2(P);
     const int ns = fft_stride(n);
     S::sync();   // the unit's previous pencils have been read out of buf
+    FftTw<T, L2> twr;
+    twr.load(tw, tid);
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * nthr) {
         C v[kFftLoadsPerRound];
 #pragma unroll
@@ -729,7 +793,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
         const int k = pos <= (n >> 1) ? pos : pos - n;
         mv[j] = (one_round && e < P * n && q < I && k >= -h && k <= h) ? mult[int64_t(k + h) * I + q] : T(0);
     }
-    C* res = fft_stockham2<T, false, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid);
+    C* res = fft_stockham2<T, false, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid, twr);
     if (one_round) {
 #pragma unroll
         for (int j = 0; j < kFftLoadsPerRound; ++j) {
@@ -757,7 +821,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
             }
         }
     }
-    const C* res2 = fft_stockham2<T, true, S, L2>(res, res == buf ? buf + P * ns : buf, ns, n, log2n, tw, tid);
+    const C* res2 = fft_stockham2<T, true, S, L2>(res, res == buf ? buf + P * ns : buf, ns, n, log2n, tw, tid, twr);
     for (int e = tid; e < P * xcnt; e += nthr) {
         const int k = xlo + (e >> lp);
         const int pl = e & (P - 1);
@@ -867,6 +931,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int tid = int(threadIdx.x), nthr = int(blockDim.x), PU = nthr / PER;
     const int r = int(cluster_ctarank());
     const int64_t x = pl.x0 + int(blockIdx.x) / CL;
+    FftTw<float, L2> twr;   // both transforms of the block share them
+    twr.load(tw, tid);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* rbuf = reinterpret_cast<float2*>(smem_raw);   // PU z-pencils (this block's row pairs)
     float2* ybuf = rbuf + 2 * PU * NS;                    // PU y-pencils (this block's kz-columns)
@@ -909,7 +975,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
         dst[2] = make_float2(va[i].z, vb[i].z);
         dst[3] = make_float2(va[i].w, vb[i].w);
     }
-    const float2* zr = fft_stockham2<float, false, SyncBlock, L2>(rbuf, rbuf + PU * NS, NS, N, L2, tw, tid);
+    const float2* zr = fft_stockham2<float, false, SyncBlock, L2>(rbuf, rbuf + PU * NS, NS, N, L2, tw, tid, twr);
     cluster_wait();
 
     // half spectra of the two rows of pair j at kz = k, into the owner of column k
@@ -929,7 +995,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     cluster_arrive();
     cluster_wait();
 
-    const float2* zy = fft_stockham2<float, false, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid);
+    const float2* zy = fft_stockham2<float, false, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid, twr);
     const int kv = max(0, min(pl.kp, H - r * pl.kp));   // this block's valid columns
     for (int e = tid; e < kv * K; e += nthr) {
         const int ky = e / kv, p = e - ky * kv;
@@ -945,6 +1011,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int tid = int(threadIdx.x), nthr = int(blockDim.x), PU = nthr / PER;
     const int r = int(cluster_ctarank());
     const int64_t x = pl.x0 + int(blockIdx.x) / CL;
+    FftTw<float, L2> twr;   // both transforms of the block share them
+    twr.load(tw, tid);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* rbuf = reinterpret_cast<float2*>(smem_raw);   // PU z-pencils (this block's row pairs)
     float2* ybuf = rbuf + 2 * PU * NS;                    // PU y-pencils (this block's kz-columns)
@@ -979,7 +1047,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
             }
         }
     }
-    const float2* zy = fft_stockham2<float, true, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid);
+    const float2* zy = fft_stockham2<float, true, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid, twr);
     cluster_wait();
 
     // rows y0, y0 + 1 of column kz packed into the z-pencil of pair j (its owner's)
@@ -999,7 +1067,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     cluster_arrive();
     cluster_wait();
 
-    const float2* zr = fft_stockham2<float, true, SyncBlock, L2>(rbuf, rbuf + PU * NS, NS, N, L2, tw, tid);
+    const float2* zr = fft_stockham2<float, true, SyncBlock, L2>(rbuf, rbuf + PU * NS, NS, N, L2, tw, tid, twr);
     constexpr int G4 = N / 4;
     const int nv = max(0, min(pl.pp, pl.np - r * pl.pp));
     for (int e = tid; e < nv * G4; e += nthr) {
