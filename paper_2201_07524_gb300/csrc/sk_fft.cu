@@ -900,6 +900,11 @@ __device__ __forceinline__ unsigned cluster_ctarank() {
 // cluster takes part): arrive releases this thread's earlier shared-memory
 // writes, wait acquires those of every thread that arrived.
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+// Arrive without ordering this thread's earlier memory accesses (for a
+// barrier that only has to show that every block of the cluster is running).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 // Shared-memory address of `p` (this block's shared memory) in block `rank`
@@ -913,6 +918,38 @@ __device__ __forceinline__ uint32_t cluster_addr(const void* p, unsigned rank) {
 
 __device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// The elements e = tid, tid + nthr, ... of a two-level index e = a B + b,
+// walked without a division per step.
+struct Walk2 {
+    int a, b, da, db, B;
+    __device__ __forceinline__ Walk2(int tid, int nthr, int B_) : B(B_) {
+        a = tid / B;
+        b = tid - a * B;
+        da = nthr / B;
+        db = nthr - da * B;
+    }
+    __device__ __forceinline__ void next() {
+        a += da;
+        b += db;
+        if (b >= B) {
+            b -= B;
+            ++a;
+        }
+    }
+};
+
+// Block of the cluster owning index k of items dealt out `per` to a block
+// (k < CL per), and k's position there.
+__device__ __forceinline__ int owner_of(int k, int per, int& local) {
+    int owner = 0;
+    while (k >= per) {
+        k -= per;
+        ++owner;
+    }
+    local = k;
+    return owner;
 }
 
 // A 3-D plan's band as the cluster kernels see it: planes x0 .. x0 + gridDim.x / CL
@@ -941,7 +978,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
         const int p = e >> L2, y = e & (N - 1);
         if (y < pl.ylo || y >= yhi || p >= pl.kp || r * pl.kp + p >= H) ybuf[p * NS + pidx(y)] = make_float2(0.f, 0.f);
     }
-    cluster_arrive();
+    // (the zeroed positions are ones no other block writes)
+    cluster_arrive_relaxed();
 
     // this block's row pairs into z-pencils (4 consecutive z per item); the
     // grid rows are zeroed after reading, for the next spreading
@@ -980,13 +1018,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
 
     // half spectra of the two rows of pair j at kz = k, into the owner of column k
     const int nv = max(0, min(pl.pp, pl.np - r * pl.pp));   // this block's valid pairs
-    for (int e = tid; e < nv * H; e += nthr) {
-        const int p = e / H, k = e - p * H;
+    Walk2 wk(tid, nthr, H);
+    for (int e = tid; e < nv * H; e += nthr, wk.next()) {
+        const int p = wk.a, k = wk.b;
         const float2 zk = zr[p * NS + pidx(k)];
         const float2 zm = zr[p * NS + pidx((N - k) & (N - 1))];
         const float2 a = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
         const float2 b = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
-        const int owner = k / pl.kp, col = k - owner * pl.kp;
+        int col;
+        const int owner = owner_of(k, pl.kp, col);
         const int y0 = pl.ylo + 2 * (r * pl.pp + p);
         const uint32_t dst = cluster_addr(ybuf + col * NS + pidx(y0), unsigned(owner));
         st_cluster(dst, a);
@@ -997,9 +1037,12 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
 
     const float2* zy = fft_stockham2<float, false, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid, twr);
     const int kv = max(0, min(pl.kp, H - r * pl.kp));   // this block's valid columns
-    for (int e = tid; e < kv * K; e += nthr) {
-        const int ky = e / kv, p = e - ky * kv;
-        A2[(x * K + ky) * H + r * pl.kp + p] = zy[p * NS + pidx((ky - pl.h) & (N - 1))];
+    if (kv > 0) {
+        Walk2 wo(tid, nthr, kv);
+        for (int e = tid; e < kv * K; e += nthr, wo.next()) {
+            const int ky = wo.a, p = wo.b;
+            A2[(x * K + ky) * H + r * pl.kp + p] = zy[p * NS + pidx((ky - pl.h) & (N - 1))];
+        }
     }
 }
 
@@ -1020,7 +1063,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
         const int p = e >> L2, z = e & (N - 1);
         if ((z > pl.h && z < N - pl.h) || p >= pl.pp || r * pl.pp + p >= pl.np) rbuf[p * NS + pidx(z)] = make_float2(0.f, 0.f);
     }
-    cluster_arrive();
+    // (the zeroed positions are ones no other block writes)
+    cluster_arrive_relaxed();
 
     // this block's kz-columns: frequencies -h..h along y, the rest zero
     const int kv = max(0, min(pl.kp, H - r * pl.kp));
@@ -1028,34 +1072,38 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
         const int p = e >> L2, y = e & (N - 1);
         if ((y > pl.h && y < N - pl.h) || p >= kv) ybuf[p * NS + pidx(y)] = make_float2(0.f, 0.f);
     }
-    for (int e0 = 0; e0 < kv * K; e0 += kFftLoadsPerRound * nthr) {
-        float2 v[kFftLoadsPerRound];
+    if (kv > 0) {
+        Walk2 wi(tid, nthr, kv);
+        for (int e0 = 0; e0 < kv * K; e0 += kFftLoadsPerRound * nthr) {
+            float2 v[kFftLoadsPerRound];
+            int slot[kFftLoadsPerRound];
 #pragma unroll
-        for (int i = 0; i < kFftLoadsPerRound; ++i) {
-            const int e = e0 + i * nthr + tid;
-            if (e < kv * K) {
-                const int ky = e / kv, p = e - ky * kv;
-                v[i] = __ldcg(A2 + (x * K + ky) * H + r * pl.kp + p);
+            for (int i = 0; i < kFftLoadsPerRound; ++i) {
+                const int e = e0 + i * nthr + tid;
+                slot[i] = -1;
+                if (e < kv * K) {
+                    const int ky = wi.a, p = wi.b;
+                    v[i] = __ldcg(A2 + (x * K + ky) * H + r * pl.kp + p);
+                    slot[i] = p * NS + pidx((ky - pl.h) & (N - 1));
+                }
+                wi.next();
             }
-        }
 #pragma unroll
-        for (int i = 0; i < kFftLoadsPerRound; ++i) {
-            const int e = e0 + i * nthr + tid;
-            if (e < kv * K) {
-                const int ky = e / kv, p = e - ky * kv;
-                ybuf[p * NS + pidx((ky - pl.h) & (N - 1))] = v[i];
-            }
+            for (int i = 0; i < kFftLoadsPerRound; ++i)
+                if (slot[i] >= 0) ybuf[slot[i]] = v[i];
         }
     }
     const float2* zy = fft_stockham2<float, true, SyncBlock, L2>(ybuf, ybuf + PU * NS, NS, N, L2, tw, tid, twr);
     cluster_wait();
 
     // rows y0, y0 + 1 of column kz packed into the z-pencil of pair j (its owner's)
-    for (int e = tid; e < kv * pl.np; e += nthr) {
-        const int j = e / kv, p = e - j * kv;
+    Walk2 ws(tid, nthr, max(kv, 1));
+    for (int e = tid; e < kv * pl.np; e += nthr, ws.next()) {
+        const int j = ws.a, p = ws.b;
         const int kz = r * pl.kp + p, y0 = pl.ylo + 2 * j;
         float2 a = zy[p * NS + pidx(y0)], b = zy[p * NS + pidx(y0) + 1];
-        const int owner = j / pl.pp, slot = j - owner * pl.pp;
+        int slot;
+        const int owner = owner_of(j, pl.pp, slot);
         float2* pen = rbuf + slot * NS;
         if (kz == 0) {
             a.y = 0.f;
