@@ -12,9 +12,10 @@
 //     128-point pencil takes three stages with natural order in and out.
 //     Blocks are small (n/8 threads per pencil), so a launch has many of them
 //     and their load, barrier and store latencies overlap on every SM.
-//     Element e of a pencil sits at e + e/8 (one pad per 8 elements), which
-//     keeps the stride-R stores of the first stages and the parallel walks of
-//     the load phases off each other's shared-memory banks.
+//     Element e of a pencil sits at slot pidx(e), a XOR swizzle of its low
+//     bits, which keeps the stride-n/R reads and stride-Ns writes of every
+//     stage and the parallel walks of the load phases free of shared-memory
+//     bank conflicts.
 //   * The grid is real, so the first pass packs two real rows into one complex
 //     FFT and splits the result into two half spectra (k = 0..h along the
 //     contiguous axis); the last inverse pass does the reverse.
@@ -58,11 +59,24 @@ __host__ __device__ constexpr int fft_ept(int n) { return (sizeof(T) == 8 && n <
 template <typename T>
 __host__ __device__ constexpr int fft_threads(int n) { return fft_pencils(n) * n / fft_ept<T>(n); }
 
-// Padded position of element e of a pencil; a pencil spans fft_stride(n)
-// slots.  The 4 extra slots per pencil put the pencils of a block on
-// different shared-memory banks (n + n/8 is a multiple of the 32 banks).
-__host__ __device__ constexpr int pidx(int e) { return e + (e >> 3); }
-__host__ __device__ constexpr int fft_stride(int n) { return n + n / 8 + 4; }
+// Slot of element e of a pencil of complex values C in shared memory: e with
+// its low bits XOR-ed with higher ones (bits 3-6 into 0-3 for 8-byte values,
+// bits 2-4 into 0-2 for 16-byte ones), a permutation of every aligned block
+// of 16 (8) elements.  Every access of the Stockham stages -- a thread's
+// reads at a stride of n/R, the writes at stride Ns -- then puts the lanes
+// of one shared-memory wavefront (16 lanes of 8 bytes, 8 of 16) on distinct
+// banks, and so do the contiguous walks of the load and store phases.  A
+// pencil spans fft_stride<C>(n) slots: n plus a few, so that the pencils a
+// wavefront spans (n <= 64, and the load phases that walk across pencils)
+// start on different banks.
+template <typename C>
+__host__ __device__ constexpr int pidx(int e) {
+    return sizeof(C) == 8 ? (e ^ ((e >> 3) & 15)) : (e ^ ((e >> 2) & 7));
+}
+template <typename C>
+__host__ __device__ constexpr int fft_stride(int n) {
+    return sizeof(C) == 8 ? (n == 32 ? 36 : (n == 64 ? 72 : n + 4)) : n + 2;
+}
 
 // Row pairs of the real passes: pair q covers rows r0 = o * ostride + y and
 // r0 + 1 with o = olo + q / npo and y = ylo + 2 (q % npo).
@@ -230,7 +244,7 @@ __device__ __forceinline__ void stockham_stage(C* pen, int n, int Ns, int t, con
     for (int b = 0; b < B; ++b) {
         const int jj = t + b * per;
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[b * R + r] = pen[pidx(jj + r * stride)];
+        for (int r = 0; r < R; ++r) x[b * R + r] = pen[pidx<C>(jj + r * stride)];
     }
     // the butterflies' twiddle rows, requested before the barrier
     C w[B][RW];
@@ -256,13 +270,13 @@ __device__ __forceinline__ void stockham_stage(C* pen, int n, int Ns, int t, con
         else dft2<C, INV>(x + b * R);
         const int base = (jj - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) pen[pidx(base + r * Ns)] = x[b * R + r];
+        for (int r = 0; r < R; ++r) pen[pidx<C>(base + r * Ns)] = x[b * R + r];
     }
     S::sync();
 }
 
 // Transform the unit's P pencils in place (natural order in and out; pencil
-// p at buf + p * ns, element e at pidx(e)); the unit has exactly
+// p at buf + p * ns, element e at pidx<C>(e)); the unit has exactly
 // fft_threads<T>(n) threads, `tid` is the thread's index in it.  `rows` is
 // the plan's table of stage twiddle rows.  Radix E = fft_ept stages while
 // they fit, then one of radix 4 or 2.
@@ -305,7 +319,7 @@ __device__ void fft_stockham(typename Cplx<T>::type* buf, int ns, int n, int log
     if constexpr (L2 > 0) {
         constexpr int N = 1 << L2, E = fft_ept<T>(N), PER = N / E;
         const int p = tid / PER, t = tid - p * PER;
-        stages_ct<C, INV, E, S, N, 1, L2>(buf + p * fft_stride(N), t, rows);
+        stages_ct<C, INV, E, S, N, 1, L2>(buf + p * fft_stride<C>(N), t, rows);
     } else if (fft_ept<T>(n) == 4) {
         stockham_all<C, INV, 4, S>(buf, ns, n, log2n, rows, tid);
     } else {
@@ -389,7 +403,7 @@ __device__ __forceinline__ void stockham_stage2(const C* in, C* out, int n, int 
     for (int b = 0; b < B; ++b) {
         const int jj = t + b * per;
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[b * R + r] = in[pidx(jj + r * stride)];
+        for (int r = 0; r < R; ++r) x[b * R + r] = in[pidx<C>(jj + r * stride)];
     }
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -408,7 +422,7 @@ __device__ __forceinline__ void stockham_stage2(const C* in, C* out, int n, int 
         else dft2<C, INV>(x + b * R);
         const int base = (jj - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[pidx(base + r * Ns)] = x[b * R + r];
+        for (int r = 0; r < R; ++r) out[pidx<C>(base + r * Ns)] = x[b * R + r];
     }
     S::sync();
 }
@@ -434,7 +448,7 @@ __device__ typename Cplx<T>::type* fft_stockham2(typename Cplx<T>::type* a, type
                                                  const FftTw<T, L2>& tw) {
     using C = typename Cplx<T>::type;
     if constexpr (L2 > 0) {
-        constexpr int N = 1 << L2, E = fft_ept<T>(N), PER = N / E, NSP = fft_stride(N);
+        constexpr int N = 1 << L2, E = fft_ept<T>(N), PER = N / E, NSP = fft_stride<C>(N);
         S::sync();
         const int p = tid / PER, t = tid - p * PER;
         stages_ct2<C, INV, E, S, N, 1, L2, 0, FftTw<T, L2>::SIZE>(a + p * NSP, b + p * NSP, t, tw.w);
@@ -501,7 +515,7 @@ template int fft_twiddle_rows<double>(int);
 template cudaError_t launch_twiddle_rows<float>(void*, int, cudaStream_t);
 template cudaError_t launch_twiddle_rows<double>(void*, int, cudaStream_t);
 
-// Shared memory of an FFT block: two buffers of P pencils of fft_stride(n)
+// Shared memory of an FFT block: two buffers of P pencils of fft_stride<C>(n)
 // slots each (the input and the other buffer of fft_stockham2).
 template <typename T>
 struct FftSmem {
@@ -520,7 +534,7 @@ constexpr int kFftLoadsPerRound = 8;
 // The passes below are written for one FFT unit: `nthr` threads (a block of a
 // pass kernel) that transform the P pencils starting at pencil (or row pair)
 // q0, thread `tid` of the unit, staging in `buf` (two buffers of P pencils of
-// fft_stride(n) slots, the transform alternating between them), with its
+// fft_stride<C>(n) slots, the transform alternating between them), with its
 // barrier S::sync().  Data written by the previous pass is
 // read once, with ld.global.cg (cached in L2 only).  Index arithmetic is
 // 32-bit and free of divisions in the per-element loops (the pencil a thread
@@ -540,7 +554,7 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
     }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n);
-    const int ns = fft_stride(n);
+    const int ns = fft_stride<C>(n);
     S::sync();   // the unit's previous pencils have been read out of buf
     FftTw<T, L2> twr;
     twr.load(tw, tid);
@@ -569,7 +583,7 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
                 g[at[j]] = T(0);
                 g[at[j] + n] = T(0);
             }
-            buf[(e >> log2n) * ns + pidx(e & (n - 1))] = z[j];
+            buf[(e >> log2n) * ns + pidx<C>(e & (n - 1))] = z[j];
         }
     }
     const C* res = fft_stockham2<T, false, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid, twr);
@@ -581,8 +595,8 @@ __device__ __forceinline__ void r2c_unit(T* __restrict__ g, typename Cplx<T>::ty
         const int q = q0 + p;
         if (q < rp.npairs) {
             const int64_t r0 = rc.get(rp, q);
-            const C zk = res[p * ns + pidx(k)];
-            const C zm = res[p * ns + pidx((n - k) & (n - 1))];
+            const C zk = res[p * ns + pidx<C>(k)];
+            const C zm = res[p * ns + pidx<C>((n - k) & (n - 1))];
             C A, Bv;
             A.x = (zk.x + zm.x) * T(0.5);
             A.y = (zk.y - zm.y) * T(0.5);
@@ -612,7 +626,7 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
     }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n);
-    const int ns = fft_stride(n);
+    const int ns = fft_stride<C>(n);
     S::sync();   // the unit's previous pencils have been read out of buf
     FftTw<T, L2> twr;
     twr.load(tw, tid);
@@ -657,7 +671,7 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
                 z.x = T(0);
                 z.y = T(0);
             }
-            buf[(e >> log2n) * ns + pidx(pos)] = z;
+            buf[(e >> log2n) * ns + pidx<C>(pos)] = z;
         }
     }
     const C* res = fft_stockham2<T, true, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid, twr);
@@ -667,7 +681,7 @@ __device__ __forceinline__ void c2r_unit(const typename Cplx<T>::type* __restric
         const int q = q0 + p;
         if (q >= rp.npairs) continue;
         const int64_t r0 = rc.get(rp, q);
-        const C v = res[p * ns + pidx(l)];
+        const C v = res[p * ns + pidx<C>(l)];
         g[r0 * n + l] = v.x;
         g[(r0 + 1) * n + l] = v.y;
     }
@@ -689,7 +703,7 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
     }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n), lp = ilog2(P);
-    const int ns = fft_stride(n);
+    const int ns = fft_stride<C>(n);
     const int Q = ocnt * I;
     const int Lin = INM == FULL ? n : 2 * h + 1;
     const int Lout = OUTM == FULL ? n : 2 * h + 1;
@@ -730,7 +744,7 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
             const int e = e0 + j * nthr + tid;
             const int k = e >> lp;
             const int pos = INM == FULL ? k : ((k - h) & (n - 1));
-            buf[pl * ns + pidx(pos)] = v[j];
+            buf[pl * ns + pidx<C>(pos)] = v[j];
         }
     }
     const C* res = fft_stockham2<T, INV, S, L2>(buf, buf + P * ns, ns, n, log2n, tw, tid, twr);
@@ -738,7 +752,7 @@ __device__ __forceinline__ void axis_unit(const typename Cplx<T>::type* __restri
     for (int e = tid; e < P * kn; e += nthr) {
         const int k = k0 + (e >> lp);
         const int pos = OUTM == FULL ? k : ((k - h) & (n - 1));
-        dst[int64_t(k) * I] = res[pl * ns + pidx(pos)];
+        dst[int64_t(k) * I] = res[pl * ns + pidx<C>(pos)];
     }
 }
 
@@ -757,7 +771,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
     }
     using C = typename Cplx<T>::type;
     const int P = fft_pencils(n), lp = ilog2(P);
-    const int ns = fft_stride(n);
+    const int ns = fft_stride<C>(n);
     S::sync();   // the unit's previous pencils have been read out of buf
     FftTw<T, L2> twr;
     twr.load(tw, tid);
@@ -777,7 +791,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
             const int e = e0 + j * nthr + tid;
             if (e >= P * n) continue;
             const int k = e >> lp;
-            buf[(e & (P - 1)) * ns + pidx(k)] = v[j];
+            buf[(e & (P - 1)) * ns + pidx<C>(k)] = v[j];
         }
     }
     // when one round covers the unit, the multiplier of each element this
@@ -800,7 +814,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
             const int e = j * nthr + tid;
             if (e >= P * n) continue;
             const int pos = e >> lp;
-            C& v = res[(e & (P - 1)) * ns + pidx(pos)];
+            C& v = res[(e & (P - 1)) * ns + pidx<C>(pos)];
             v.x *= mv[j];
             v.y *= mv[j];
         }
@@ -810,7 +824,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
             const int pl = e & (P - 1);
             const int q = q0 + pl;
             const int k = pos <= (n >> 1) ? pos : pos - n;
-            C& v = res[pl * ns + pidx(pos)];
+            C& v = res[pl * ns + pidx<C>(pos)];
             if (q < I && k >= -h && k <= h) {
                 const T m = mult[int64_t(k + h) * I + q];
                 v.x *= m;
@@ -826,7 +840,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
         const int k = xlo + (e >> lp);
         const int pl = e & (P - 1);
         const int q = q0 + pl;
-        if (q < I) data[int64_t(k) * I + q] = res2[pl * ns + pidx(k)];
+        if (q < I) data[int64_t(k) * I + q] = res2[pl * ns + pidx<C>(k)];
     }
 }
 
@@ -963,7 +977,8 @@ struct Plane3 {
 template <int L2, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     k_fft_front3(float* __restrict__ g, float2* __restrict__ A2, Plane3 pl, const float2* __restrict__ tw) {
-    constexpr int N = 1 << L2, NS = fft_stride(N), PER = N / 8;
+    using C = float2;
+    constexpr int N = 1 << L2, NS = fft_stride<C>(N), PER = N / 8;
     const int H = pl.h + 1, K = 2 * pl.h + 1;
     const int tid = int(threadIdx.x), nthr = int(blockDim.x), PU = nthr / PER;
     const int r = int(cluster_ctarank());
@@ -976,7 +991,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int yhi = pl.ylo + 2 * pl.np;
     for (int e = tid; e < PU * N; e += nthr) {
         const int p = e >> L2, y = e & (N - 1);
-        if (y < pl.ylo || y >= yhi || p >= pl.kp || r * pl.kp + p >= H) ybuf[p * NS + pidx(y)] = make_float2(0.f, 0.f);
+        if (y < pl.ylo || y >= yhi || p >= pl.kp || r * pl.kp + p >= H) ybuf[p * NS + pidx<C>(y)] = make_float2(0.f, 0.f);
     }
     // (the zeroed positions are ones no other block writes)
     cluster_arrive_relaxed();
@@ -1007,11 +1022,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
             *reinterpret_cast<float4*>(g + at[i]) = make_float4(0.f, 0.f, 0.f, 0.f);
             *reinterpret_cast<float4*>(g + at[i] + N) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        float2* dst = rbuf + p * NS + pidx(4 * c);   // 4 c .. 4 c + 3 share one pad
-        dst[0] = make_float2(va[i].x, vb[i].x);
-        dst[1] = make_float2(va[i].y, vb[i].y);
-        dst[2] = make_float2(va[i].z, vb[i].z);
-        dst[3] = make_float2(va[i].w, vb[i].w);
+        float2* pen = rbuf + p * NS;
+        pen[pidx<C>(4 * c)] = make_float2(va[i].x, vb[i].x);
+        pen[pidx<C>(4 * c + 1)] = make_float2(va[i].y, vb[i].y);
+        pen[pidx<C>(4 * c + 2)] = make_float2(va[i].z, vb[i].z);
+        pen[pidx<C>(4 * c + 3)] = make_float2(va[i].w, vb[i].w);
     }
     const float2* zr = fft_stockham2<float, false, SyncBlock, L2>(rbuf, rbuf + PU * NS, NS, N, L2, tw, tid, twr);
     cluster_wait();
@@ -1021,16 +1036,16 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     Walk2 wk(tid, nthr, H);
     for (int e = tid; e < nv * H; e += nthr, wk.next()) {
         const int p = wk.a, k = wk.b;
-        const float2 zk = zr[p * NS + pidx(k)];
-        const float2 zm = zr[p * NS + pidx((N - k) & (N - 1))];
+        const float2 zk = zr[p * NS + pidx<C>(k)];
+        const float2 zm = zr[p * NS + pidx<C>((N - k) & (N - 1))];
         const float2 a = make_float2((zk.x + zm.x) * 0.5f, (zk.y - zm.y) * 0.5f);
         const float2 b = make_float2((zk.y + zm.y) * 0.5f, (zm.x - zk.x) * 0.5f);
         int col;
         const int owner = owner_of(k, pl.kp, col);
         const int y0 = pl.ylo + 2 * (r * pl.pp + p);
-        const uint32_t dst = cluster_addr(ybuf + col * NS + pidx(y0), unsigned(owner));
-        st_cluster(dst, a);
-        st_cluster(dst + uint32_t(sizeof(float2)), b);   // y0 even: y0 + 1 is the next slot
+        const uint32_t dst = cluster_addr(ybuf + col * NS, unsigned(owner));
+        st_cluster(dst + uint32_t(sizeof(float2) * pidx<C>(y0)), a);
+        st_cluster(dst + uint32_t(sizeof(float2) * pidx<C>(y0 + 1)), b);
     }
     cluster_arrive();
     cluster_wait();
@@ -1041,7 +1056,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
         Walk2 wo(tid, nthr, kv);
         for (int e = tid; e < kv * K; e += nthr, wo.next()) {
             const int ky = wo.a, p = wo.b;
-            A2[(x * K + ky) * H + r * pl.kp + p] = zy[p * NS + pidx((ky - pl.h) & (N - 1))];
+            A2[(x * K + ky) * H + r * pl.kp + p] = zy[p * NS + pidx<C>((ky - pl.h) & (N - 1))];
         }
     }
 }
@@ -1049,7 +1064,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
 template <int L2, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     k_fft_back3(const float2* __restrict__ A2, float* __restrict__ gout, Plane3 pl, const float2* __restrict__ tw) {
-    constexpr int N = 1 << L2, NS = fft_stride(N), PER = N / 8;
+    using C = float2;
+    constexpr int N = 1 << L2, NS = fft_stride<C>(N), PER = N / 8;
     const int H = pl.h + 1, K = 2 * pl.h + 1;
     const int tid = int(threadIdx.x), nthr = int(blockDim.x), PU = nthr / PER;
     const int r = int(cluster_ctarank());
@@ -1061,7 +1077,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     float2* ybuf = rbuf + 2 * PU * NS;                    // PU y-pencils (this block's kz-columns)
     for (int e = tid; e < PU * N; e += nthr) {
         const int p = e >> L2, z = e & (N - 1);
-        if ((z > pl.h && z < N - pl.h) || p >= pl.pp || r * pl.pp + p >= pl.np) rbuf[p * NS + pidx(z)] = make_float2(0.f, 0.f);
+        if ((z > pl.h && z < N - pl.h) || p >= pl.pp || r * pl.pp + p >= pl.np) rbuf[p * NS + pidx<C>(z)] = make_float2(0.f, 0.f);
     }
     // (the zeroed positions are ones no other block writes)
     cluster_arrive_relaxed();
@@ -1070,7 +1086,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int kv = max(0, min(pl.kp, H - r * pl.kp));
     for (int e = tid; e < PU * N; e += nthr) {
         const int p = e >> L2, y = e & (N - 1);
-        if ((y > pl.h && y < N - pl.h) || p >= kv) ybuf[p * NS + pidx(y)] = make_float2(0.f, 0.f);
+        if ((y > pl.h && y < N - pl.h) || p >= kv) ybuf[p * NS + pidx<C>(y)] = make_float2(0.f, 0.f);
     }
     if (kv > 0) {
         Walk2 wi(tid, nthr, kv);
@@ -1084,7 +1100,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
                 if (e < kv * K) {
                     const int ky = wi.a, p = wi.b;
                     v[i] = __ldcg(A2 + (x * K + ky) * H + r * pl.kp + p);
-                    slot[i] = p * NS + pidx((ky - pl.h) & (N - 1));
+                    slot[i] = p * NS + pidx<C>((ky - pl.h) & (N - 1));
                 }
                 wi.next();
             }
@@ -1101,7 +1117,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     for (int e = tid; e < kv * pl.np; e += nthr, ws.next()) {
         const int j = ws.a, p = ws.b;
         const int kz = r * pl.kp + p, y0 = pl.ylo + 2 * j;
-        float2 a = zy[p * NS + pidx(y0)], b = zy[p * NS + pidx(y0) + 1];
+        float2 a = zy[p * NS + pidx<C>(y0)], b = zy[p * NS + pidx<C>(y0 + 1)];
         int slot;
         const int owner = owner_of(j, pl.pp, slot);
         float2* pen = rbuf + slot * NS;
@@ -1109,8 +1125,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
             a.y = 0.f;
             b.y = 0.f;
         }
-        st_cluster(cluster_addr(pen + pidx(kz), unsigned(owner)), make_float2(a.x - b.y, a.y + b.x));
-        if (kz > 0) st_cluster(cluster_addr(pen + pidx(N - kz), unsigned(owner)), make_float2(a.x + b.y, b.x - a.y));
+        st_cluster(cluster_addr(pen + pidx<C>(kz), unsigned(owner)), make_float2(a.x - b.y, a.y + b.x));
+        if (kz > 0) st_cluster(cluster_addr(pen + pidx<C>(N - kz), unsigned(owner)), make_float2(a.x + b.y, b.x - a.y));
     }
     cluster_arrive();
     cluster_wait();
@@ -1120,8 +1136,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int nv = max(0, min(pl.pp, pl.np - r * pl.pp));
     for (int e = tid; e < nv * G4; e += nthr) {
         const int p = e / G4, c = e - p * G4;
-        const float2* src = zr + p * NS + pidx(4 * c);
-        const float2 s0 = src[0], s1 = src[1], s2 = src[2], s3 = src[3];
+        const float2* pen = zr + p * NS;
+        const float2 s0 = pen[pidx<C>(4 * c)], s1 = pen[pidx<C>(4 * c + 1)], s2 = pen[pidx<C>(4 * c + 2)],
+                     s3 = pen[pidx<C>(4 * c + 3)];
         float* row = gout + (x * N + (pl.ylo + 2 * (r * pl.pp + p))) * N + 4 * c;
         *reinterpret_cast<float4*>(row) = make_float4(s0.x, s1.x, s2.x, s3.x);
         *reinterpret_cast<float4*>(row + N) = make_float4(s0.y, s1.y, s2.y, s3.y);
@@ -1194,14 +1211,16 @@ __global__ void k_fill_forward(const double* __restrict__ fhat, int d, int h, co
 
 template <typename T>
 static size_t fft_smem_bytes(int n) {
-    return 2 * size_t(fft_pencils(n)) * size_t(fft_stride(n)) * sizeof(typename Cplx<T>::type);
+    using C = typename Cplx<T>::type;
+    return 2 * size_t(fft_pencils(n)) * size_t(fft_stride<C>(n)) * sizeof(C);
 }
 
 // Largest dynamic shared memory any FFT launch of this precision can use:
 // two buffers of one pencil of the largest length, 4096.
 template <typename T>
 static size_t fft_smem_max() {
-    return 2 * size_t(fft_stride(4096)) * sizeof(typename Cplx<T>::type);
+    using C = typename Cplx<T>::type;
+    return 2 * size_t(fft_stride<C>(4096)) * sizeof(C);
 }
 
 // Opt a kernel into its largest shared-memory size once per device (the cache
@@ -1389,7 +1408,7 @@ bool fft_planes_supported(const FftPlan& f, bool fp32) {
 // device: 512 threads, i.e. 4096 / n pencils of each kind, two buffers each.
 template <auto Kern, int L2>
 static cudaError_t ensure_plane_smem() {
-    constexpr size_t bytes = size_t(4) * (512 / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
+    constexpr size_t bytes = size_t(4) * (512 / ((1 << L2) / 8)) * fft_stride<float2>(1 << L2) * sizeof(float2);
     static unsigned long long configured = 0ull;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1405,7 +1424,7 @@ static cudaError_t run_planes_cl(const FftPlan& f, const Plane3& pl, int threads
     SK_TRY((ensure_plane_smem<k_fft_back3<L2, CL>, L2>()));
     const int64_t H = f.h + 1, K = 2 * f.h + 1;
     const unsigned blocks = unsigned((f.hi[0] - f.lo[0] + 1) * CL);
-    const size_t smem = size_t(4) * (threads / ((1 << L2) / 8)) * fft_stride(1 << L2) * sizeof(float2);
+    const size_t smem = size_t(4) * (threads / ((1 << L2) / 8)) * fft_stride<float2>(1 << L2) * sizeof(float2);
     const float2* tw = static_cast<const float2*>(f.tw);
     k_fft_front3<L2, CL><<<blocks, threads, smem, s>>>(static_cast<float*>(f.grid), static_cast<float2*>(f.A2), pl, tw);
     if (launches) ++*launches;
