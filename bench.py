@@ -243,7 +243,7 @@ def kernel_name(stage, w, tensor_cores):
     if w.d == 2:
         if stage == "interp" and tensor_cores:
             return "k_interp2_tc<%d>" % W
-        return "k_%s2_strip<%d, float>" % (stage, W)
+        return ("k_spread2_col<%d, float>" if stage == "spread" else "k_interp2_strip<%d, float>") % W
     return None
 
 

@@ -445,9 +445,10 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
                                                   c.sub_count, c.sub_bin);
     CK(cudaGetLastError());
 
-    // column tasks of the 3-D column kernels
-    if (column_kernels(P->d, P->W)) {
-        const int ncol = P->B[0] * P->B[1];
+    // column tasks of the column spreading kernels (3-D: the B0 x B1 cell
+    // columns of a bin; 2-D: the B0 x-cells of a strip bin)
+    if (column_kernels(P->d, P->W) || P->d == 2) {
+        const int ncol = P->d == 3 ? P->B[0] * P->B[1] : P->B[0];
         k_count_tasks<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, P->nbins, kTaskMaxPts, ncol, nsub);
         CK(cudaGetLastError());
         scan_ints(P, nsub, suboff, P->nbins);
@@ -474,7 +475,9 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
             for (int k = 0; k < 3; ++k) sorted[3 * i + k] = tk[3 * order[i] + k];
         CK(cudaMemcpyAsync(c.tasks, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
         CK(cudaStreamSynchronize(P->ps));
-
+    }
+    if (column_kernels(P->d, P->W)) {
+        const int ncol = P->B[0] * P->B[1];
         // the interpolation's column queue: every non-empty (bin, column)
         // pair, most points first, so the warps that take the last entries
         // take short ones
@@ -784,9 +787,6 @@ void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
     a.key_start = src.key_start;
     a.tasks = src.tasks;
     a.ntasks = src.ntasks;
-    a.stasks = src.stasks;
-    a.nstasks = src.nstasks;
-    a.queue = P->ticket + 4;
     a.n_os = P->n_os;
     for (int t = 0; t < 3; ++t) a.nb[t] = P->nb[t];
     a.beta = P->beta;
@@ -795,7 +795,7 @@ void spread_into_grid(sk_plan* P, const Cloud& src, const double* w) {
     a.wp = P->wp;
     const int st = stage_begin(P, SK_STAGE_SPREAD);
     CK(launch_spread<T>(P->d, P->W, a, P->ps));
-    if ((column_kernels(P->d, P->W) ? src.ntasks : (P->d == 2 ? src.nstasks : src.nsub)) > 0) ++P->launches;
+    if ((column_kernels(P->d, P->W) || P->d == 2 ? src.ntasks : src.nsub) > 0) ++P->launches;
     stage_end(P, st);
 }
 
@@ -1276,7 +1276,7 @@ int sk_init(sk_plan** out, int d, int64_t n, const double* x, const double* a, i
         const int64_t nmax = std::max(n, m);
         P->partial_blocks = std::max<int64_t>(interp_blocks<double>(nmax), kRedBlocks);
         P->partial = static_cast<double*>(dalloc(P, size_t(P->partial_blocks) * 8 * sizeof(double)));
-        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 8));   // [0] reductions, [2..3] interpolation queue, [4..5] spreading queue
+        P->ticket = static_cast<unsigned*>(dalloc(P, sizeof(unsigned) * 8));   // [0] reductions, [2..3] interpolation queue
         P->stats = static_cast<double*>(dalloc(P, sizeof(double) * (3 * NSLOTS + 8)));
         P->status = static_cast<int*>(dalloc(P, sizeof(int) * 4));
         P->shift = static_cast<double*>(dalloc(P, sizeof(double) * 2));

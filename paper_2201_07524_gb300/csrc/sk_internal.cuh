@@ -142,9 +142,6 @@ struct SpreadArgs {
     const int* key_start;  // CSR over sort keys (bin, cell in bin)
     const int* tasks;      // column tasks: (bin, first column, end column)
     int ntasks;
-    const int* stasks;     // 2-D strip tasks: (bin, first point, end point), most points first
-    int nstasks;
-    unsigned* queue;       // 2-D strip queue: [0] next task, [1] warps finished; zero between launches
     int n_os;
     int nb[3];             // bins per dimension
     double beta;           // Kaiser-Bessel shape

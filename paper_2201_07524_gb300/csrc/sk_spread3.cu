@@ -582,18 +582,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (W <= 8 ? 3 : 2) : (W <=
 }
 
 // ------------------------------------------------------------ 2-D strips
-// The 2-D kernels follow the same plan with one axis fewer.  A bin is a strip
-// of BX = 33 - W x-cells by BY y-cells; every point of it touches x-rows
+// The 2-D interpolation on the CUDA cores (FP64 plans, or SK_KERNELS_SIMT)
+// follows the same plan with one axis fewer.  A bin is a strip of
+// BX = 33 - W x-cells by BY y-cells; every point of it touches x-rows
 // x0 - (m-1) ... x0 + BX + m - 2, exactly 32 rows, so lane l owns row
 // x0 - (m-1) + l over the E = BY + W - 1 y-cells of the strip's window, in
 // registers.  Inside a bin the points are sorted by y-cell first, so a batch
 // of 32 comes in non-decreasing y-offset (segments with compile-time
 // register indices, as in 3-D).  For one point, the W lanes whose rows lie in
-// its x-window take wx[lane - dx] and add (or gather) its W y-taps.  Tasks are
-// runs of at most kStripMaxPts points of one bin, taken by warps from a queue
-// (most points first); spreading adds a task's window to the grid with global
-// atomics at its end, interpolation reduces each point's lane partials
-// through shared memory and runs the FP64 epilogue.
+// its x-window take wx[lane - dx] and gather its W y-taps.  Tasks are runs of
+// at most kStripMaxPts points of one bin, taken by warps from a queue (most
+// points first); each point's lane partials are reduced through shared
+// memory and the FP64 epilogue runs with one lane per point.
 template <int W, typename T>
 struct Strip2 {
     static constexpr int BX = 33 - W, BY = kStripBy;
@@ -626,29 +626,6 @@ __device__ __forceinline__ T lane_wx(const T* row, int lane, int dx) {
 }
 
 template <int W, int E, int DY0, typename T>
-__device__ __forceinline__ void strip_spread_segment(T (&acc)[E], const T* wt, const int* dxs, int lane, int mydy,
-                                                     int& first) {
-    using G = Strip2<W, T>;
-    const int cnt = __popc(__ballot_sync(0xffffffffu, mydy == DY0));
-    for (int p = first; p < first + cnt; ++p) {
-        const T* row = wt + p * G::STRIDE;
-        const T ax = lane_wx<W, T>(row, lane, dxs[p]);
-        T wy[W];
-        load_wz<W, T>(row + G::WY, wy);
-#pragma unroll
-        for (int k = 0; k < W; ++k) acc[DY0 + k] = fma(ax, wy[k], acc[DY0 + k]);
-    }
-    first += cnt;
-}
-
-template <int W, int E, typename T, int... DY>
-__device__ __forceinline__ void strip_spread(T (&acc)[E], const T* wt, const int* dxs, int lane, int mydy,
-                                             std::integer_sequence<int, DY...>) {
-    int first = 0;
-    (strip_spread_segment<W, E, DY, T>(acc, wt, dxs, lane, mydy, first), ...);
-}
-
-template <int W, int E, int DY0, typename T>
 __device__ __forceinline__ void strip_interp_segment(const T (&win)[E], const T* wt, const int* dxs, T* rd, int lane,
                                                      int mydy, int& first) {
     using G = Strip2<W, T>;
@@ -673,50 +650,164 @@ __device__ __forceinline__ void strip_interp(const T (&win)[E], const T* wt, con
     (strip_interp_segment<W, E, DY, T>(win, wt, dxs, rd, lane, mydy, first), ...);
 }
 
+// ------------------------------------------------------------ 2-D columns
+// 2-D spreading by columns of a strip bin, the 2-D counterpart of
+// k_spread3_col: a column is one x-cell of the bin (its BY cells along y, each
+// a contiguous range of sorted points), and every point of it touches the
+// same W x-rows of the grid.  A half-warp covers the column's window, lane
+// i < W owning x-row i over the E = BY + W - 1 y-cells in registers; the two
+// half-warps take alternate points of each cell, so one FMA instruction does
+// the W y-taps of two points on 2 W of the 32 lanes (a strip layout, one point
+// on all 32 lanes of which W are in its x-window, was 9 % slower).  A
+// point's y-cell inside the bin is its cell's, so every cell is a segment
+// with compile-time register indices.  Columns go to the block's warps; a
+// finished column is added (both halves summed) into the bin's shared-memory
+// sub-grid with shared-memory atomics, and the block adds the sub-grid to the
+// global grid once.
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_spread2_strip(SpreadArgs a) {
-    using G = Strip2<W, T>;
+struct Col2 {
+    static constexpr int BX = 33 - W, BY = kStripBy;
+    static constexpr int SX = BX + W - 1, SY = BY + W - 1, E = SY;
+    static constexpr int SUB = SX * SY;
+    static constexpr int VEC = 16 / int(sizeof(T));
+    static constexpr int WP = (W + VEC - 1) / VEC * VEC;
+    static constexpr int WX = 0, WY = WP;
+    static constexpr int NV = (2 * WP) / VEC;
+    static constexpr int STRIDE = (NV % 2 == 1 ? NV : NV + 1) * VEC;
+};
+
+// One table row's taps into the lane's row: x-weight `ax` (zero for lanes
+// outside the window or without a row) times the W y-weights, at offset DY.
+template <int W, int E, int DY, typename T>
+__device__ __forceinline__ void col2_row(T (&acc)[E], const T* row, T ax) {
+    using G = Col2<W, T>;
+    T wy[W];
+    load_wz<W, T>(row + G::WY, wy);
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[DY + k] = fma(ax, wy[k], acc[DY + k]);
+}
+
+// The table rows [first, first + cnt) (all of y-cell offset DY): half-warp h
+// takes rows first + h, first + h + 2, ...; the loop bounds are the same for
+// the whole warp.
+template <int W, int E, int DY, typename T>
+__device__ __forceinline__ void col2_segment(T (&acc)[E], const T* wt, int row_i, int h, int mydy, int& first) {
+    using G = Col2<W, T>;
+    const int cnt = __popc(__ballot_sync(0xffffffffu, mydy == DY));
+    const bool lane_ok = row_i < W;
+    for (int q = h; q - h < cnt; q += 2) {
+        const bool ok = q < cnt;
+        const T* row = wt + (first + (ok ? q : 0)) * G::STRIDE;
+        col2_row<W, E, DY, T>(acc, row, (ok && lane_ok) ? row[G::WX + row_i] : T(0));
+    }
+    first += cnt;
+}
+
+template <int W, int E, typename T, int... DY>
+__device__ __forceinline__ void col2_segments(T (&acc)[E], const T* wt, int row_i, int h, int mydy,
+                                              std::integer_sequence<int, DY...>) {
+    int first = 0;
+    (col2_segment<W, E, DY, T>(acc, wt, row_i, h, mydy, first), ...);
+}
+
+// Column c's cells (c < c1): lane ly < BY gets cell ly's first point and count.
+template <int BX, int BY>
+__device__ __forceinline__ void col2_cells(const int* __restrict__ ks, int64_t kbase, int c, int c1, int lane, int& cs,
+                                           int& cn) {
+    cs = 0;
+    cn = 0;
+    if (c < c1 && lane < BY) {
+        const int64_t k = kbase + lane * BX + c;
+        cs = ks[k];
+        cn = ks[k + 1] - cs;
+    }
+}
+
+template <int W, typename T>
+__global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 12 ? 4 : 3) : 2)
+    k_spread2_col(SpreadArgs a) {
+    using G = Col2<W, T>;
     constexpr int E = G::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tab = reinterpret_cast<T*>(smem_raw);
-    int* dxall = reinterpret_cast<int*>(tab + kWarps * 32 * G::STRIDE);
+    T* sub = reinterpret_cast<T*>(smem_raw);
+    T* tab = sub + ((G::SUB + 3) / 4) * 4;
+    __shared__ int col_next;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = lane >> 4, row_i = lane & 15;
     T* wt = tab + warp * 32 * G::STRIDE;
-    int* dxs = dxall + warp * 32;
+
+    const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
+    const int bx = bin / a.nb[1], by = bin - (bin / a.nb[1]) * a.nb[1];
+    for (int c = threadIdx.x; c < G::SUB; c += blockDim.x) sub[c] = T(0);
+    if (threadIdx.x == 0) col_next = col0 + kSpreadWarps;
+    __syncthreads();
+
     const T* c0 = static_cast<const T*>(a.coord[0]);
     const T* c1 = static_cast<const T*>(a.coord[1]);
-    T* grid = static_cast<T*>(a.grid);
-    const int n = a.n_os;
-    for (int t = queue_take(a.queue, lane); t < a.nstasks; t = queue_take(a.queue, lane)) {
-        const int bin = a.stasks[3 * t], start = a.stasks[3 * t + 1], end = a.stasks[3 * t + 2];
-        const int x0 = (bin / a.nb[1]) * G::BX, y0 = (bin % a.nb[1]) * G::BY;
-        T acc[E];
+    const int64_t kbase = int64_t(bin) * (G::BX * G::BY);
+    int col = col0 + warp;
+    while (col < col1) {
+        int cs, cn;
+        col2_cells<G::BX, G::BY>(a.key_start, kbase, col, col1, lane, cs, cn);
+        // the column's points before each cell's end (an inclusive scan)
+        int incl = cn;
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc[e] = T(0);
-        for (int base = start; base < end; base += 32) {
-            const int cnt = min(32, end - base);
-            int mydy = -1;
-            if (lane < cnt) {
-                const int p = base + lane;
-                int fx, fy;
-                fill_row2<W, T>(wt + lane * G::STRIDE, c0[p], c1[p], T(a.w[p]), a.wp, fx, fy);
-                dxs[lane] = fx - x0;
-                mydy = fy - y0;
-            }
-            __syncwarp();
-            strip_spread<W, E, T>(acc, wt, dxs, lane, mydy, std::make_integer_sequence<int, G::BY>{});
-            __syncwarp();
+        for (int o = 1; o < G::BY; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        const int xr = x0 - (W / 2 - 1) + lane;
-        if (xr >= 0 && xr < n) {
+        const int total = __shfl_sync(0xffffffffu, incl, G::BY - 1);
+        if (total > 0) {
+            T acc[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] = T(0);
+            for (int base = 0; base < total; base += 32) {
+                // lane's point: ordinal base + lane of the column, in cell ly
+                const int o = base + lane;
+                int ly = 0;
+#pragma unroll
+                for (int c = 0; c < G::BY - 1; ++c) ly += (o >= __shfl_sync(0xffffffffu, incl, c)) ? 1 : 0;
+                const int start = __shfl_sync(0xffffffffu, cs, ly);
+                const int before = __shfl_sync(0xffffffffu, incl - cn, ly);
+                const int mydy = o < total ? ly : -1;
+                if (o < total) {
+                    const int p = start + (o - before);
+                    T w[W];
+                    int f;
+                    window_poly<W, T>(c0[p], a.wp, T(a.w[p]), f, w);
+                    store_vec<T, W>(wt + lane * G::STRIDE + G::WX, w);
+                    window_poly<W, T>(c1[p], a.wp, T(1), f, w);
+                    store_vec<T, W>(wt + lane * G::STRIDE + G::WY, w);
+                }
+                __syncwarp();
+                col2_segments<W, E, T>(acc, wt, row_i, h, mydy, std::make_integer_sequence<int, G::BY>{});
+                __syncwarp();
+            }
+            // both halves' partial sums of row row_i into the sub-grid
+            T* srow = sub + (col + row_i) * G::SY;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int yr = y0 - (W / 2 - 1) + e;
-                if (yr >= 0 && yr < n && acc[e] != T(0)) atomicAdd(grid + int64_t(xr) * n + yr, acc[e]);
+                const T v = acc[e] + __shfl_xor_sync(0xffffffffu, acc[e], 16);
+                if (h == 0 && row_i < W && v != T(0)) atomicAdd(srow + e, v);
             }
         }
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(&col_next, 1);
+        col = __shfl_sync(0xffffffffu, nxt, 0);
     }
-    queue_leave(a.queue, lane);
+    __syncthreads();
+
+    T* grid = static_cast<T*>(a.grid);
+    const int n = a.n_os;
+    const int ox = bx * G::BX - (W / 2 - 1), oy = by * G::BY - (W / 2 - 1);
+    for (int c = threadIdx.x; c < G::SUB; c += blockDim.x) {
+        const T v = sub[c];
+        if (v == T(0)) continue;
+        const int ly = c % G::SY, lx = c / G::SY;
+        const int gx = ox + lx, gy = oy + ly;
+        if (gx < 0 || gx >= n || gy < 0 || gy >= n) continue;
+        atomicAdd(&grid[int64_t(gx) * n + gy], v);
+    }
 }
 
 template <int W, typename T>
@@ -896,12 +987,6 @@ template int interp3_blocks<float>(int, int);
 template int interp3_blocks<double>(int, int);
 // ------------------------------------------------------------ 2-D strip dispatch
 template <int W, typename T>
-size_t spread2_smem() {
-    using G = Strip2<W, T>;
-    return size_t(kWarps) * 32 * G::STRIDE * sizeof(T) + size_t(kWarps) * 32 * sizeof(int);
-}
-
-template <int W, typename T>
 size_t interp2_smem() {
     using G = Strip2<W, T>;
     return (size_t(kWarps) * 32 * G::STRIDE + size_t(kWarps) * 32 * kRedStride) * sizeof(T) +
@@ -932,17 +1017,19 @@ static int resident_blocks(size_t smem, int tasks) {
 }
 
 template <int W, typename T>
+size_t spread2col_smem() {
+    using G = Col2<W, T>;
+    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kSpreadWarps) * 32 * G::STRIDE) * sizeof(T);
+}
+
+// 2-D spreading: one block per column task (bin, first column, end column).
+template <int W, typename T>
 static cudaError_t spread2_one(const SpreadArgs& a, cudaStream_t s) {
-    const size_t bytes = spread2_smem<W, T>();
-    cudaError_t err = opt_in<k_spread2_strip<W, T>>(bytes);
+    const size_t bytes = spread2col_smem<W, T>();
+    cudaError_t err = opt_in<k_spread2_col<W, T>>(bytes);
     if (err != cudaSuccess) return err;
-    const int blocks = resident_blocks<k_spread2_strip<W, T>>(bytes, a.nstasks);
-    if (blocks == 0) {
-        const cudaError_t last = cudaGetLastError();
-        return last != cudaSuccess ? last : cudaErrorInvalidValue;
-    }
-    if (a.nstasks == 0) return cudaSuccess;
-    k_spread2_strip<W, T><<<blocks, 256, bytes, s>>>(a);
+    if (a.ntasks == 0) return cudaSuccess;
+    k_spread2_col<W, T><<<a.ntasks, kSpreadWarps * 32, bytes, s>>>(a);
     return cudaGetLastError();
 }
 

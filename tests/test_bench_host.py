@@ -83,7 +83,8 @@ def test_roofline_kernel_names_follow_dimension_and_kernel_kind():
     assert bench.kernel_name("interp", wl.HEADLINE_3D, 0) == "k_interp3_col<8, float>"
     assert bench.kernel_name("spread", wl.HEADLINE_3D, 1) == "k_spread3_col<8, float>"
     assert bench.kernel_name("interp", wl.GMM_2D, 1) == "k_interp2_tc<12>"
-    assert bench.kernel_name("spread", wl.GMM_2D, 1) == "k_spread2_strip<12, float>"
+    assert bench.kernel_name("spread", wl.GMM_2D, 1) == "k_spread2_col<12, float>"
+    assert bench.kernel_name("interp", wl.GMM_2D, 0) == "k_interp2_strip<12, float>"
     # every name the bench can look up is one the traffic record may hold
     import json
     import os
