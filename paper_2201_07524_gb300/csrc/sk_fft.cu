@@ -37,6 +37,7 @@
 //   2-D: r2c(y) -> [fwd(x) * M, inv(x)] -> c2r(y)
 //   1-D: r2c(x) -> * M -> c2r(x)            (the grid carries a second, zero row)
 #include <algorithm>
+#include <utility>
 
 #include "sk_internal.cuh"
 
@@ -194,6 +195,14 @@ __device__ __forceinline__ void dft8(C* x) {
         x[r + 4] = csub(e[r], o[r]);
     }
 }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream is finishing;
+// griddep_wait() blocks until the predecessor has completed and its writes
+// are visible (a no-op for a kernel launched the ordinary way), and
+// griddep_launch() lets this kernel's own dependent start launching.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // The barrier of an FFT unit (the block of a pass kernel).
 struct SyncBlock {
@@ -775,6 +784,7 @@ __device__ __forceinline__ void convolve_unit(typename Cplx<T>::type* __restrict
     S::sync();   // the unit's previous pencils have been read out of buf
     FftTw<T, L2> twr;
     twr.load(tw, tid);
+    griddep_wait();   // the previous pass's output
     for (int e0 = 0; e0 < P * n; e0 += kFftLoadsPerRound * nthr) {
         C v[kFftLoadsPerRound];
 #pragma unroll
@@ -881,6 +891,7 @@ __global__ void __launch_bounds__(512) k_fft_axis0_convolve(typename Cplx<T>::ty
                                                             const T* __restrict__ mult,
                                                             const typename Cplx<T>::type* __restrict__ twg) {
     const FftSmem<T> sm;
+    griddep_launch();
     convolve_unit<T, SyncBlock, L2>(data, int(I), xlo, xcnt, n, log2n, h, mult, twg, sm.buf,
                                 int(blockIdx.x) * fft_pencils(n), int(threadIdx.x), int(blockDim.x));
 }
@@ -983,6 +994,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     const int tid = int(threadIdx.x), nthr = int(blockDim.x), PU = nthr / PER;
     const int r = int(cluster_ctarank());
     const int64_t x = pl.x0 + int(blockIdx.x) / CL;
+    griddep_launch();
     FftTw<float, L2> twr;   // both transforms of the block share them
     twr.load(tw, tid);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -999,6 +1011,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
     // this block's row pairs into z-pencils (4 consecutive z per item); the
     // grid rows are zeroed after reading, for the next spreading
     constexpr int G4 = N / 4, IPT = G4 / PER;   // items per thread: 2
+    griddep_wait();   // the spreading's grid
     float4 va[IPT], vb[IPT];
     int64_t at[IPT];
 #pragma unroll
@@ -1084,6 +1097,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512)
 
     // this block's kz-columns: frequencies -h..h along y, the rest zero
     const int kv = max(0, min(pl.kp, H - r * pl.kp));
+    griddep_wait();   // the axis-0 pass's spectrum
     for (int e = tid; e < PU * N; e += nthr) {
         const int p = e >> L2, y = e & (N - 1);
         if ((y > pl.h && y < N - pl.h) || p >= kv) ybuf[p * NS + pidx<C>(y)] = make_float2(0.f, 0.f);
@@ -1238,6 +1252,25 @@ static cudaError_t ensure_smem() {
     return e;
 }
 
+// A launch, with programmatic stream serialization when `pdl` (the kernel may
+// start while its predecessor in the stream finishes; it waits in
+// griddep_wait() before reading what the predecessor wrote).
+template <typename... Exp, typename... Act>
+static cudaError_t launch_pdl(bool pdl, void (*kern)(Exp...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t s, Act&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+}
+
 #define SK_TRY(x)                                   \
     do {                                            \
         cudaError_t e_ = (x);                       \
@@ -1356,15 +1389,16 @@ static void axis0_range(const FftPlan& f, int& lo, int& cnt) {
 }
 
 template <typename T, int L2>
-static cudaError_t run_axis0_convolve_l(const FftPlan& f, void* data, int64_t I, int64_t* launches, cudaStream_t s) {
+static cudaError_t run_axis0_convolve_l(const FftPlan& f, void* data, int64_t I, int64_t* launches, cudaStream_t s,
+                                        bool pdl = false) {
     using C = typename Cplx<T>::type;
     SK_TRY((ensure_smem<T, k_fft_axis0_convolve<T, L2>>()));
     const int P = fft_pencils(f.n);
     int xlo, xcnt;
     axis0_range(f, xlo, xcnt);
-    k_fft_axis0_convolve<T, L2><<<unsigned((I + P - 1) / P), fft_threads<T>(f.n), fft_smem_bytes<T>(f.n), s>>>(
-        static_cast<C*>(data), I, xlo, xcnt, f.n, f.log2n, f.h, static_cast<const T*>(f.mult),
-        static_cast<const C*>(f.tw));
+    SK_TRY(launch_pdl(pdl, k_fft_axis0_convolve<T, L2>, unsigned((I + P - 1) / P), unsigned(fft_threads<T>(f.n)),
+                      fft_smem_bytes<T>(f.n), s, static_cast<C*>(data), I, xlo, xcnt, f.n, f.log2n, f.h,
+                      static_cast<const T*>(f.mult), static_cast<const C*>(f.tw)));
     if (launches) ++*launches;
     return cudaGetLastError();
 }
@@ -1426,12 +1460,12 @@ static cudaError_t run_planes_cl(const FftPlan& f, const Plane3& pl, int threads
     const unsigned blocks = unsigned((f.hi[0] - f.lo[0] + 1) * CL);
     const size_t smem = size_t(4) * (threads / ((1 << L2) / 8)) * fft_stride<float2>(1 << L2) * sizeof(float2);
     const float2* tw = static_cast<const float2*>(f.tw);
-    k_fft_front3<L2, CL><<<blocks, threads, smem, s>>>(static_cast<float*>(f.grid), static_cast<float2*>(f.A2), pl, tw);
+    SK_TRY(launch_pdl(f.pdl, k_fft_front3<L2, CL>, blocks, unsigned(threads), smem, s, static_cast<float*>(f.grid),
+                      static_cast<float2*>(f.A2), pl, tw));
     if (launches) ++*launches;
-    SK_TRY(cudaGetLastError());
-    SK_TRY(run_axis0_convolve<float>(f, f.A2, K * H, launches, s));
-    k_fft_back3<L2, CL><<<blocks, threads, smem, s>>>(static_cast<const float2*>(f.A2), static_cast<float*>(f.grid_out),
-                                                     pl, tw);
+    SK_TRY((run_axis0_convolve_l<float, L2>(f, f.A2, K * H, launches, s, f.pdl)));
+    SK_TRY(launch_pdl(f.pdl, k_fft_back3<L2, CL>, blocks, unsigned(threads), smem, s,
+                      static_cast<const float2*>(f.A2), static_cast<float*>(f.grid_out), pl, tw));
     if (launches) ++*launches;
     return cudaGetLastError();
 }

@@ -218,6 +218,7 @@ struct FftPlan {
     void* tw = nullptr;       // Cplx<T>*, the stage twiddle rows (fft_twiddle_rows<T>(n) entries)
     const double* psihat = nullptr;  // 2h+1 values psihat_n(k/n), k = -h..h (FP64)
     bool planes = false;      // 3-D FP32: the grid-side passes by thread-block-cluster planes (three launches)
+    bool pdl = true;          // the plane path's three launches use programmatic dependent launch
 };
 
 // ----------------------------------------------------------------- launchers
