@@ -389,6 +389,40 @@ struct Tc2 {
     static_assert(2 * KC >= N / 4, "a thread's operand row holds its N results");
 };
 
+// A point's A-operand row in the 2-D kernel: its W y-weights from entry K0,
+// zeros elsewhere, as whole 16-byte chunks (hi and lo parts).  The offset K0
+// is a compile-time constant here: the points of a warp share their y-cell
+// almost always (a bin's points are sorted y-cell first), so the dispatch
+// below costs one branch per warp, and the chunk stores put the warp's lanes
+// on distinct banks, where stores of single values at a per-thread offset
+// collide.
+template <int W, int KC, int K0>
+__device__ __forceinline__ void tc2_row_at(unsigned char* row_hi, unsigned char* row_lo, const float (&wy)[W]) {
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 4 * c + q - K0;
+            v[q] = (k >= 0 && k < W) ? wy[k >= 0 && k < W ? k : 0] : 0.f;
+        }
+        const float4 h = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+        *reinterpret_cast<float4*>(row_hi + c * 128) = h;
+        *reinterpret_cast<float4*>(row_lo + c * 128) = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
+    }
+}
+
+template <int W, int KC, int K0, int KMAX>
+__device__ __forceinline__ void tc2_row(int k0, unsigned char* row_hi, unsigned char* row_lo, const float (&wy)[W]) {
+    if constexpr (K0 < KMAX) {
+        if (k0 != K0) {
+            tc2_row<W, KC, K0 + 1, KMAX>(k0, row_hi, row_lo, wy);
+            return;
+        }
+    }
+    tc2_row_at<W, KC, K0>(row_hi, row_lo, wy);
+}
+
 template <int W>
 __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
     using S = Tc2<W>;
@@ -473,19 +507,8 @@ __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
 #pragma unroll
                 for (int k = 0; k < W; ++k) wx[k] = wy[k] = 0.f;
             }
-#pragma unroll
-            for (int c = 0; c < S::KC; ++c) {
-                *reinterpret_cast<float4*>(row_hi + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
-                *reinterpret_cast<float4*>(row_lo + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const int kk = k0 + k;
-                const int off = (kk >> 2) * S::LBO + (kk & 3) * 4;
-                const float h = tf32_hi(wy[k]);
-                *reinterpret_cast<float*>(row_hi + off) = h;
-                *reinterpret_cast<float*>(row_lo + off) = wy[k] - h;
-            }
+            static_assert(S::LBO == 128, "chunk stride of tc2_row_at");
+            tc2_row<W, S::KC, 0, S::KY - W>(k0, row_hi, row_lo, wy);
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
