@@ -262,19 +262,40 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
 #pragma unroll
                 for (int k = 0; k < W; ++k) wz[k] = 0.f;
             }
-            // the point's operand row: zero, then its W z-weights from entry k0
+            // the point's operand row, its W z-weights from entry k0, as whole
+            // 16-byte chunks: the weights shifted by k0 mod 4 (selects) fill
+            // NU chunks from chunk k0 / 4, the other chunks are zero.  Chunk
+            // stores keep the warp's lanes on distinct banks, where single
+            // values stored at a per-thread offset collide.
+            {
+                constexpr int NU = (W + 3 + 3) / 4;
+                const int sh = k0 & 3, c0 = k0 >> 2;
+                float u[4 * NU];
 #pragma unroll
-            for (int c = 0; c < S::KC; ++c) {
-                *reinterpret_cast<float4*>(row_hi + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
-                *reinterpret_cast<float4*>(row_lo + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+                for (int j = 0; j < 4 * NU; ++j) {
+                    float v = 0.f;
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                const int kk = k0 + k;
-                const int off = (kk >> 2) * S::LBO + (kk & 3) * 4;
-                const float h = tf32_hi(wz[k]);
-                *reinterpret_cast<float*>(row_hi + off) = h;
-                *reinterpret_cast<float*>(row_lo + off) = wz[k] - h;
+                    for (int t = 0; t < 4; ++t)
+                        if (j - t >= 0 && j - t < W) v = sh == t ? wz[j - t >= 0 && j - t < W ? j - t : 0] : v;
+                    u[j] = v;
+                }
+#pragma unroll
+                for (int r = 0; r < NU; ++r) {
+                    if (c0 + r < S::KC) {
+                        const float4 h = make_float4(tf32_hi(u[4 * r]), tf32_hi(u[4 * r + 1]), tf32_hi(u[4 * r + 2]),
+                                                     tf32_hi(u[4 * r + 3]));
+                        *reinterpret_cast<float4*>(row_hi + (c0 + r) * S::LBO) = h;
+                        *reinterpret_cast<float4*>(row_lo + (c0 + r) * S::LBO) =
+                            make_float4(u[4 * r] - h.x, u[4 * r + 1] - h.y, u[4 * r + 2] - h.z, u[4 * r + 3] - h.w);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < S::KC; ++c) {
+                    if (c < c0 || c >= c0 + NU) {
+                        *reinterpret_cast<float4*>(row_hi + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        *reinterpret_cast<float4*>(row_lo + c * S::LBO) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
             }
             fence_async_smem();
             tc_fence_before();
