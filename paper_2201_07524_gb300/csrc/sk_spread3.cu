@@ -23,6 +23,7 @@
 //     each point's 32 lane partials through shared memory, and runs the FP64
 //     epilogue with one lane per point.
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 #include "sk_internal.cuh"
@@ -45,6 +46,14 @@ template <int W, typename T = float> struct Col3 {
     // consecutive lanes on distinct banks
     static constexpr int NV = (3 * WP) / VEC;
     static constexpr int STRIDE = (NV % 2 == 1 ? NV : NV + 1) * VEC;
+    // FP32 spreading adds, after wz | wx | wy, the z-weights shifted by one
+    // slot (0, wz[0], ..., wz[W-1], 0), for points at an odd z-offset (packed
+    // taps, below); its rows are STRIDE_S apart
+    static constexpr int WZS = 3 * WP;
+    static constexpr int NS = (W + 2 + VEC - 1) / VEC * VEC;
+    static constexpr int NVS = (3 * WP + NS) / VEC;
+    static constexpr int STRIDE_S = (NVS % 2 == 1 ? NVS : NVS + 1) * VEC;
+    static constexpr int EP = (BZ + W) / 2;           // z-cell pairs of a column window (E rounded up)
     static constexpr int SUB = SX * SY * SZ;
     // 16-byte-aligned z-chunks covering a column window: the window starts
     // LEAD entries into the first chunk
@@ -212,7 +221,7 @@ __host__ __device__ constexpr int wx_slot(int i) {
 
 // Table row of a point of a sorted batch: wz (times `scale`), wx (permuted
 // when SharedJ), wy.
-template <int W, typename T>
+template <int W, typename T, bool SHIFTED = false>
 __device__ __forceinline__ void fill_row_sorted(T* row, T u0, T u1, T u2, T scale, const WindowPoly& wp) {
     using G = Col3<W, T>;
     int f;
@@ -230,6 +239,12 @@ __device__ __forceinline__ void fill_row_sorted(T* row, T u0, T u1, T u2, T scal
     store_vec<T, W>(row + G::WY, w);
     window_poly<W, T>(u2, wp, scale, f, w);
     store_vec<T, W>(row + G::WZ, w);
+    if constexpr (SHIFTED) {
+        T ws[G::NS];
+#pragma unroll
+        for (int k = 0; k < G::NS; ++k) ws[k] = (k >= 1 && k <= W) ? w[k >= 1 && k <= W ? k - 1 : 0] : T(0);
+        store_vec<T, G::NS>(row + G::WZS, ws);
+    }
 }
 
 // A lane's Q adjacent (permuted) x-weights.
@@ -367,6 +382,73 @@ __device__ __forceinline__ void spread_sorted(T (&acc)[Q][E], const T* wt, int m
     (spread_segment_sorted<W, Q, E, DZ, T>(acc, wt, mydz, first, i0, j0, ri, rj, rv), ...);
 }
 
+// Packed taps (FP32 spreading): the lane's accumulators are pairs of adjacent
+// z-cells (2t, 2t+1), and one packed FMA (FFMA2) adds two z-taps of a row.  A
+// point at an even z-offset DZ0 takes its W z-weights as W/2 pairs into pairs
+// DZ0/2 ...; one at an odd offset takes the shifted copy (0, wz[0], ...,
+// wz[W-1], 0) as W/2 + 1 pairs into pairs (DZ0-1)/2 ...: W/2 or W/2 + 1
+// packed FMAs per row in place of W.
+template <int W, int Q, int EP, int DZ0>
+__device__ __forceinline__ void add_taps_packed(float2 (&acc)[Q][EP], const float (&a)[Q], const float* row) {
+    using G = Col3<W, float>;
+    constexpr bool ODD = DZ0 % 2 == 1;
+    constexpr int NP = ODD ? W / 2 + 1 : W / 2;
+    constexpr int P0 = ODD ? (DZ0 - 1) / 2 : DZ0 / 2;
+    const float* src = row + (ODD ? G::WZS : G::WZ);
+    float2 wz2[NP];
+#pragma unroll
+    for (int t = 0; t < NP; t += 2) {
+        const float4 v = *reinterpret_cast<const float4*>(src + 2 * t);
+        wz2[t] = make_float2(v.x, v.y);
+        if (t + 1 < NP) wz2[t + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const float2 a2 = make_float2(a[q], a[q]);
+#pragma unroll
+        for (int t = 0; t < NP; ++t) acc[q][P0 + t] = __ffma2_rn(a2, wz2[t], acc[q][P0 + t]);
+    }
+}
+
+template <int W, int Q, int EP, int DZ0>
+__device__ __forceinline__ void spread_rows_packed(float2 (&acc)[Q][EP], const float* wt, int p, int pe, int i0,
+                                                   int j0, const int (&ri)[Q], const int (&rj)[Q],
+                                                   const bool (&rv)[Q]) {
+    using G = Col3<W, float>;
+    for (; p + 1 < pe; p += 2) {
+        const float* r0 = wt + p * G::STRIDE_S;
+        const float* r1 = r0 + G::STRIDE_S;
+        float av0[Q], av1[Q];
+        row_weights_sorted<W, Q, float>(r0, i0, j0, ri, rj, rv, av0);
+        row_weights_sorted<W, Q, float>(r1, i0, j0, ri, rj, rv, av1);
+        add_taps_packed<W, Q, EP, DZ0>(acc, av0, r0);
+        add_taps_packed<W, Q, EP, DZ0>(acc, av1, r1);
+    }
+    if (p < pe) {
+        const float* r0 = wt + p * G::STRIDE_S;
+        float av0[Q];
+        row_weights_sorted<W, Q, float>(r0, i0, j0, ri, rj, rv, av0);
+        add_taps_packed<W, Q, EP, DZ0>(acc, av0, r0);
+    }
+}
+
+template <int W, int Q, int EP, int DZ0>
+__device__ __forceinline__ void spread_segment_packed(float2 (&acc)[Q][EP], const float* wt, int mydz, int& first,
+                                                      int i0, int j0, const int (&ri)[Q], const int (&rj)[Q],
+                                                      const bool (&rv)[Q]) {
+    const int cnt = __popc(__ballot_sync(0xffffffffu, mydz == DZ0));
+    spread_rows_packed<W, Q, EP, DZ0>(acc, wt, first, first + cnt, i0, j0, ri, rj, rv);
+    first += cnt;
+}
+
+template <int W, int Q, int EP, int... DZ>
+__device__ __forceinline__ void spread_packed(float2 (&acc)[Q][EP], const float* wt, int mydz, int i0, int j0,
+                                              const int (&ri)[Q], const int (&rj)[Q], const bool (&rv)[Q],
+                                              std::integer_sequence<int, DZ...>) {
+    int first = 0;
+    (spread_segment_packed<W, Q, EP, DZ>(acc, wt, mydz, first, i0, j0, ri, rj, rv), ...);
+}
+
 // Kernel sum of the point in table row `pos`: its 32 lane partials, times
 // wy[j] per lane group when the lanes left it out.
 template <int W, typename T>
@@ -412,7 +494,7 @@ __device__ __forceinline__ T batch_sum(const T* rd, const T* row, int pos) {
 }
 
 template <int W, typename T>
-__global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 4 : 2) : (W <= 6 ? 2 : 1))
+__global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 3 : 2) : (W <= 6 ? 2 : 1))
     k_spread3_col(SpreadArgs a) {
     using G = Col3<W, T>;
     constexpr int Q = G::Q, E = G::E;
@@ -421,7 +503,9 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 
     T* tab = sub + ((G::SUB + 3) / 4) * 4;
     __shared__ int col_next;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* wt = tab + warp * 32 * G::STRIDE;
+    constexpr bool PACK = sizeof(T) == 4;   // packed taps (FP32)
+    constexpr int RS = PACK ? G::STRIDE_S : G::STRIDE;
+    T* wt = tab + warp * 32 * RS;
 
     const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
     const int bz = bin % a.nb[2], by = (bin / a.nb[2]) % a.nb[1], bx = bin / (a.nb[2] * a.nb[1]);
@@ -443,22 +527,34 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 
         const int start = a.key_start[kbase + col * G::BZ];
         const int end = a.key_start[kbase + (col + 1) * G::BZ];
         if (start < end) {
-            T acc[Q][E];
+            // accumulators: T[Q][E], or (packed) float2[Q][EP] over the same z-cells
+            using Acc = typename std::conditional<PACK, float2[Q][G::EP], T[Q][E]>::type;
+            Acc acc;
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
+            for (int q = 0; q < Q; ++q) {
+                if constexpr (PACK) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) acc[q][e] = T(0);
+                    for (int t = 0; t < G::EP; ++t) acc[q][t] = make_float2(0.f, 0.f);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) acc[q][e] = T(0);
+                }
+            }
             Prefetch<T> pf;
             pf.load(c0, c1, c2, a.w, start + lane, lane < end - start);
             for (int base = start; base < end; base += 32) {
                 const int cnt = min(32, end - base);
                 const int mydz = lane < cnt ? int(floor(pf.u2)) - z0 : -1;
                 const int pos = lane;   // a column's points are ordered by z-offset (the sort key)
-                if (lane < cnt) fill_row_sorted<W, T>(wt + pos * G::STRIDE, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp);
+                if (lane < cnt) fill_row_sorted<W, T, PACK>(wt + pos * RS, pf.u0, pf.u1, pf.u2, T(pf.w), a.wp);
                 pf.load(c0, c1, c2, a.w, base + 32 + lane, base + 32 + lane < end);
                 __syncwarp();
-                spread_sorted<W, Q, E, T>(acc, wt, mydz, lane / W, lane % W, ri, rj, rv,
-                                          std::make_integer_sequence<int, G::BZ>{});
+                if constexpr (PACK)
+                    spread_packed<W, Q, G::EP>(acc, wt, mydz, lane / W, lane % W, ri, rj, rv,
+                                               std::make_integer_sequence<int, G::BZ>{});
+                else
+                    spread_sorted<W, Q, E, T>(acc, wt, mydz, lane / W, lane % W, ri, rj, rv,
+                                              std::make_integer_sequence<int, G::BZ>{});
                 __syncwarp();
             }
             const int cx = col / G::BY, cy = col % G::BY;
@@ -466,9 +562,17 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 8 ? 
             for (int q = 0; q < Q; ++q) {
                 if (!rv[q]) continue;
                 T* srow = sub + ((cx + ri[q]) * G::SY + (cy + rj[q])) * G::SZ;
+                if constexpr (PACK) {
 #pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (acc[q][e] != T(0)) atomicAdd(srow + e, acc[q][e]);
+                    for (int t = 0; t < G::EP; ++t) {
+                        if (acc[q][t].x != 0.f) atomicAdd(srow + 2 * t, acc[q][t].x);
+                        if (2 * t + 1 < E && acc[q][t].y != 0.f) atomicAdd(srow + 2 * t + 1, acc[q][t].y);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (acc[q][e] != T(0)) atomicAdd(srow + e, acc[q][e]);
+                }
             }
         }
         int nxt = 0;
@@ -881,7 +985,8 @@ __global__ void __launch_bounds__(256) k_interp2_strip(InterpArgs a, Epilogue e)
 template <int W, typename T>
 size_t spread3_smem() {
     using G = Col3<W, T>;
-    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kSpreadWarps) * 32 * G::STRIDE) * sizeof(T);
+    constexpr int RS = sizeof(T) == 4 ? G::STRIDE_S : G::STRIDE;
+    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kSpreadWarps) * 32 * RS) * sizeof(T);
 }
 
 template <int W, typename T>
