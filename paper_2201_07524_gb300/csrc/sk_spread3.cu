@@ -778,7 +778,57 @@ struct Col2 {
     static constexpr int WX = 0, WY = WP;
     static constexpr int NV = (2 * WP) / VEC;
     static constexpr int STRIDE = (NV % 2 == 1 ? NV : NV + 1) * VEC;
+    // FP32: after wx | wy the y-weights shifted by one slot (0, wy[0], ...,
+    // wy[W-1], 0) for points at an odd y-offset (packed taps); rows STRIDE_S apart
+    static constexpr int WYS = 2 * WP;
+    static constexpr int NS = (W + 2 + VEC - 1) / VEC * VEC;
+    static constexpr int NVS = (2 * WP + NS) / VEC;
+    static constexpr int STRIDE_S = (NVS % 2 == 1 ? NVS : NVS + 1) * VEC;
+    static constexpr int EP = (E + 1) / 2;         // y-cell pairs of the window
 };
+
+// Packed taps (FP32): one table row into the lane's row as pairs of adjacent
+// y-cells, W/2 packed FMAs at an even y-offset DY, W/2 + 1 (the shifted copy)
+// at an odd one.
+template <int W, int EP, int DY>
+__device__ __forceinline__ void col2_row_packed(float2 (&acc)[EP], const float* row, float ax) {
+    using G = Col2<W, float>;
+    constexpr bool ODD = DY % 2 == 1;
+    constexpr int NP = ODD ? W / 2 + 1 : W / 2;
+    constexpr int P0 = ODD ? (DY - 1) / 2 : DY / 2;
+    const float* src = row + (ODD ? G::WYS : G::WY);
+    float2 w2[NP];
+#pragma unroll
+    for (int t = 0; t < NP; t += 2) {
+        const float4 v = *reinterpret_cast<const float4*>(src + 2 * t);
+        w2[t] = make_float2(v.x, v.y);
+        if (t + 1 < NP) w2[t + 1] = make_float2(v.z, v.w);
+    }
+    const float2 a2 = make_float2(ax, ax);
+#pragma unroll
+    for (int t = 0; t < NP; ++t) acc[P0 + t] = __ffma2_rn(a2, w2[t], acc[P0 + t]);
+}
+
+template <int W, int EP, int DY>
+__device__ __forceinline__ void col2_segment_packed(float2 (&acc)[EP], const float* wt, int row_i, int h, int mydy,
+                                                    int& first) {
+    using G = Col2<W, float>;
+    const int cnt = __popc(__ballot_sync(0xffffffffu, mydy == DY));
+    const bool lane_ok = row_i < W;
+    for (int q = h; q - h < cnt; q += 2) {
+        const bool ok = q < cnt;
+        const float* row = wt + (first + (ok ? q : 0)) * G::STRIDE_S;
+        col2_row_packed<W, EP, DY>(acc, row, (ok && lane_ok) ? row[G::WX + row_i] : 0.f);
+    }
+    first += cnt;
+}
+
+template <int W, int EP, int... DY>
+__device__ __forceinline__ void col2_segments_packed(float2 (&acc)[EP], const float* wt, int row_i, int h, int mydy,
+                                                     std::integer_sequence<int, DY...>) {
+    int first = 0;
+    (col2_segment_packed<W, EP, DY>(acc, wt, row_i, h, mydy, first), ...);
+}
 
 // One table row's taps into the lane's row: x-weight `ax` (zero for lanes
 // outside the window or without a row) times the W y-weights, at offset DY.
@@ -838,7 +888,9 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 12 ?
     __shared__ int col_next;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = lane >> 4, row_i = lane & 15;
-    T* wt = tab + warp * 32 * G::STRIDE;
+    constexpr bool PACK = sizeof(T) == 4;   // packed taps (FP32)
+    constexpr int RS = PACK ? G::STRIDE_S : G::STRIDE;
+    T* wt = tab + warp * 32 * RS;
 
     const int bin = a.tasks[3 * blockIdx.x], col0 = a.tasks[3 * blockIdx.x + 1], col1 = a.tasks[3 * blockIdx.x + 2];
     const int bx = bin / a.nb[1], by = bin - (bin / a.nb[1]) * a.nb[1];
@@ -862,9 +914,15 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 12 ?
         }
         const int total = __shfl_sync(0xffffffffu, incl, G::BY - 1);
         if (total > 0) {
-            T acc[E];
+            using Acc = typename std::conditional<PACK, float2[G::EP], T[E]>::type;
+            Acc acc;
+            if constexpr (PACK) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = T(0);
+                for (int t = 0; t < G::EP; ++t) acc[t] = make_float2(0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[e] = T(0);
+            }
             for (int base = 0; base < total; base += 32) {
                 // lane's point: ordinal base + lane of the column, in cell ly
                 const int o = base + lane;
@@ -879,20 +937,41 @@ __global__ void __launch_bounds__(kSpreadWarps * 32, sizeof(T) == 4 ? (W <= 12 ?
                     T w[W];
                     int f;
                     window_poly<W, T>(c0[p], a.wp, T(a.w[p]), f, w);
-                    store_vec<T, W>(wt + lane * G::STRIDE + G::WX, w);
+                    store_vec<T, W>(wt + lane * RS + G::WX, w);
                     window_poly<W, T>(c1[p], a.wp, T(1), f, w);
-                    store_vec<T, W>(wt + lane * G::STRIDE + G::WY, w);
+                    store_vec<T, W>(wt + lane * RS + G::WY, w);
+                    if constexpr (PACK) {
+                        T ws[G::NS];
+#pragma unroll
+                        for (int k = 0; k < G::NS; ++k) ws[k] = (k >= 1 && k <= W) ? w[k >= 1 && k <= W ? k - 1 : 0] : T(0);
+                        store_vec<T, G::NS>(wt + lane * RS + G::WYS, ws);
+                    }
                 }
                 __syncwarp();
-                col2_segments<W, E, T>(acc, wt, row_i, h, mydy, std::make_integer_sequence<int, G::BY>{});
+                if constexpr (PACK)
+                    col2_segments_packed<W, G::EP>(acc, wt, row_i, h, mydy, std::make_integer_sequence<int, G::BY>{});
+                else
+                    col2_segments<W, E, T>(acc, wt, row_i, h, mydy, std::make_integer_sequence<int, G::BY>{});
                 __syncwarp();
             }
             // both halves' partial sums of row row_i into the sub-grid
             T* srow = sub + (col + row_i) * G::SY;
+            if constexpr (PACK) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const T v = acc[e] + __shfl_xor_sync(0xffffffffu, acc[e], 16);
-                if (h == 0 && row_i < W && v != T(0)) atomicAdd(srow + e, v);
+                for (int t = 0; t < G::EP; ++t) {
+                    const float vx = acc[t].x + __shfl_xor_sync(0xffffffffu, acc[t].x, 16);
+                    const float vy = acc[t].y + __shfl_xor_sync(0xffffffffu, acc[t].y, 16);
+                    if (h == 0 && row_i < W) {
+                        if (vx != 0.f) atomicAdd(srow + 2 * t, vx);
+                        if (2 * t + 1 < E && vy != 0.f) atomicAdd(srow + 2 * t + 1, vy);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const T v = acc[e] + __shfl_xor_sync(0xffffffffu, acc[e], 16);
+                    if (h == 0 && row_i < W && v != T(0)) atomicAdd(srow + e, v);
+                }
             }
         }
         int nxt = 0;
@@ -1124,7 +1203,8 @@ static int resident_blocks(size_t smem, int tasks) {
 template <int W, typename T>
 size_t spread2col_smem() {
     using G = Col2<W, T>;
-    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kSpreadWarps) * 32 * G::STRIDE) * sizeof(T);
+    constexpr int RS = sizeof(T) == 4 ? G::STRIDE_S : G::STRIDE;
+    return (size_t((G::SUB + 3) / 4 * 4) + size_t(kSpreadWarps) * 32 * RS) * sizeof(T);
 }
 
 // 2-D spreading: one block per column task (bin, first column, end column).
