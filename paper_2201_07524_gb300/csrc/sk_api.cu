@@ -449,7 +449,8 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
     // columns of a bin; 2-D: the B0 x-cells of a strip bin)
     if (column_kernels(P->d, P->W) || P->d == 2) {
         const int ncol = P->d == 3 ? P->B[0] * P->B[1] : P->B[0];
-        k_count_tasks<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, P->nbins, kTaskMaxPts, ncol, nsub);
+        k_count_tasks<<<nblk(P->nbins), 256, 0, P->ps>>>(c.bin_start, P->nbins,
+                                                         P->d == 3 ? kTaskMaxPts : kTaskMaxPts2, ncol, nsub);
         CK(cudaGetLastError());
         scan_ints(P, nsub, suboff, P->nbins);
         c.ntasks = read_int(P, suboff + P->nbins);

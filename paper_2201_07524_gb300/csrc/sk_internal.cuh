@@ -26,6 +26,7 @@ namespace sk {
 constexpr int kMaxP = 12;            // smoothness limit of the regularized kernel
 constexpr int kSpreadMaxPts = 1024;  // points per spreading subproblem
 constexpr int kTaskMaxPts = 4096;    // points per column task before a bin is split
+constexpr int kTaskMaxPts2 = 2048;   // the same for the 2-D column kernel (finer tasks balance its strip bins)
 
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
