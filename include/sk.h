@@ -46,7 +46,7 @@ enum {
     SK_ERR_NOT_CONVERGED = 6, /* tol > 0 and max_iter reached with ||E|| > tol */
     SK_ERR_TIMEOUT = 7,       /* reserved for bounded device waits */
     SK_ERR_CUDA = 8,          /* a CUDA runtime call failed */
-    SK_ERR_UNSUPPORTED = 9,   /* valid request this build does not implement */
+    SK_ERR_UNSUPPORTED = 9,   /* valid request the library does not implement for this plan */
     SK_ERR_TOO_LARGE = 10     /* size beyond the fixed scratch of sk_direct_residual_noalloc */
 };
 

@@ -1137,7 +1137,7 @@ const char* sk_error_string(int status) {
         case SK_ERR_NOT_CONVERGED: return "not converged within max_iter";
         case SK_ERR_TIMEOUT: return "bounded device wait ran out";
         case SK_ERR_CUDA: return "CUDA runtime error";
-        case SK_ERR_UNSUPPORTED: return "not supported by this build";
+        case SK_ERR_UNSUPPORTED: return "not supported for this plan";
         case SK_ERR_TOO_LARGE: return "size exceeds the fixed scratch of the no-allocation entry point (n <= 2097152)";
         default: return "unknown status";
     }
