@@ -333,7 +333,7 @@ void window_polynomials(int m, double beta, double knorm, WindowPoly& wp) {
 // Reduce a partial table of `nf` fields with the given ops to host doubles.
 void combine_to_host(sk_plan* P, int nblocks, int nf, const int* ops, double* host) {
     double* out = P->stats + 3 * NSLOTS;   // scratch after the slots
-    k_combine<<<1, 32, 0, P->ps>>>(P->partial, nblocks, nf, ops[0], nf > 1 ? ops[1] : 0, nf > 2 ? ops[2] : 0,
+    k_combine<<<1, 32 * nf, 0, P->ps>>>(P->partial, nblocks, nf, ops[0], nf > 1 ? ops[1] : 0, nf > 2 ? ops[2] : 0,
                                    nf > 3 ? ops[3] : 0, nf > 4 ? ops[4] : 0, nf > 5 ? ops[5] : 0,
                                    nf > 6 ? ops[6] : 0, out);
     CK(cudaGetLastError());
@@ -389,18 +389,72 @@ int* upload_runs(sk_plan* P, const std::vector<int>& bs, int run, int& count) {
     return d;
 }
 
+// The column queue of the CUDA-core 3-D interpolation for one cloud: every
+// non-empty (bin, column) pair, most points first, so the warps that take the
+// last entries take short ones.
+void build_column_queue(sk_plan* P, Cloud& c) {
+    const int ncol = P->B[0] * P->B[1];
+    const int64_t npairs = int64_t(P->nbins) * ncol;
+    int* cnt_d = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&cnt_d), size_t(npairs) * sizeof(int), P->ps));
+    k_col_counts<<<unsigned((npairs + 255) / 256), 256, 0, P->ps>>>(c.key_start, P->nbins, P->bvol, ncol, P->B[2],
+                                                                    cnt_d);
+    CK(cudaGetLastError());
+    std::vector<int> cnt(static_cast<size_t>(npairs));
+    CK(cudaMemcpyAsync(cnt.data(), cnt_d, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+    CK(cudaFreeAsync(cnt_d, P->ps));
+    std::vector<int> cols;
+    for (int64_t i = 0; i < npairs; ++i)
+        if (cnt[i] > 0) cols.push_back(int(i));
+    std::stable_sort(cols.begin(), cols.end(), [&](int p, int q) { return cnt[p] > cnt[q]; });
+    c.ncols = int(cols.size());
+    c.cols = static_cast<int*>(dalloc(P, size_t(std::max(c.ncols, 1)) * sizeof(int)));
+    if (c.ncols > 0)
+        CK(cudaMemcpyAsync(c.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
+    CK(cudaStreamSynchronize(P->ps));
+}
+
+// Both clouds' column queues and the reduction partials the CUDA-core 3-D
+// interpolation needs, for a plan that turns to it after sk_init (a no-op when
+// they exist or the plan has no column kernels).  Not during a capture: the
+// callers are sk_set_kernels and sk_autotune.
+template <typename T>
+void ensure_column_queues(sk_plan* P) {
+    if (!column_kernels(P->d, P->W) || P->X.cols) return;
+    build_column_queue(P, P->X);
+    build_column_queue(P, P->Y);
+    const int need = interp3_blocks<T>(P->W, std::max(P->X.ncols, P->Y.ncols));
+    if (need > P->partial_blocks) {
+        P->partial_blocks = need;
+        P->partial = static_cast<double*>(dalloc(P, size_t(need) * 8 * sizeof(double)));
+    }
+}
+
 template <typename T>
 void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, int64_t n) {
     c.n = n;
-    for (int t = 0; t < P->d; ++t) c.coord[t] = dalloc(P, size_t(n) * sizeof(T));
-    c.perm = static_cast<int*>(dalloc(P, size_t(n) * sizeof(int)));
-    c.marg = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
-    c.scal = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
-    c.t = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
-    c.work = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
-    c.stage = static_cast<double*>(dalloc(P, size_t(n) * sizeof(double)));
-    c.key_start = static_cast<int*>(dalloc(P, size_t(P->nkeys + 1) * sizeof(int)));
-    c.bin_start = static_cast<int*>(dalloc(P, size_t(P->nbins + 1) * sizeof(int)));
+    // the cloud's arrays in one allocation (each start 256-byte aligned): one
+    // cudaMalloc instead of a dozen, which is most of a plan build's host time
+    const size_t sizes[11] = {size_t(n) * sizeof(T), size_t(n) * sizeof(T), size_t(n) * sizeof(T),
+                              size_t(n) * sizeof(int), size_t(n) * sizeof(double), size_t(n) * sizeof(double),
+                              size_t(n) * sizeof(double), size_t(n) * sizeof(double), size_t(n) * sizeof(double),
+                              size_t(P->nkeys + 1) * sizeof(int), size_t(P->nbins + 1) * sizeof(int)};
+    size_t off[11], arena = 0;
+    for (int k = 0; k < 11; ++k) {
+        off[k] = arena;
+        arena += (k < 3 && k >= P->d) ? 0 : (sizes[k] + 255) / 256 * 256;
+    }
+    unsigned char* base = static_cast<unsigned char*>(dalloc(P, arena));
+    for (int t = 0; t < P->d; ++t) c.coord[t] = base + off[t];
+    c.perm = reinterpret_cast<int*>(base + off[3]);
+    c.marg = reinterpret_cast<double*>(base + off[4]);
+    c.scal = reinterpret_cast<double*>(base + off[5]);
+    c.t = reinterpret_cast<double*>(base + off[6]);
+    c.work = reinterpret_cast<double*>(base + off[7]);
+    c.stage = reinterpret_cast<double*>(base + off[8]);
+    c.key_start = reinterpret_cast<int*>(base + off[9]);
+    c.bin_start = reinterpret_cast<int*>(base + off[10]);
 
     // temporaries
     T* uo[3] = {nullptr, nullptr, nullptr};
@@ -477,31 +531,9 @@ void build_cloud(sk_plan* P, Cloud& c, const double* xdev, const double* wdev, i
         CK(cudaMemcpyAsync(c.tasks, sorted.data(), sorted.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
         CK(cudaStreamSynchronize(P->ps));
     }
-    if (column_kernels(P->d, P->W)) {
-        const int ncol = P->B[0] * P->B[1];
-        // the interpolation's column queue: every non-empty (bin, column)
-        // pair, most points first, so the warps that take the last entries
-        // take short ones
-        const int64_t npairs = int64_t(P->nbins) * ncol;
-        int* cnt_d = nullptr;
-        CK(cudaMallocAsync(reinterpret_cast<void**>(&cnt_d), size_t(npairs) * sizeof(int), P->ps));
-        k_col_counts<<<unsigned((npairs + 255) / 256), 256, 0, P->ps>>>(c.key_start, P->nbins, P->bvol, ncol,
-                                                                        P->B[2], cnt_d);
-        CK(cudaGetLastError());
-        std::vector<int> cnt(static_cast<size_t>(npairs));
-        CK(cudaMemcpyAsync(cnt.data(), cnt_d, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, P->ps));
-        CK(cudaStreamSynchronize(P->ps));
-        CK(cudaFreeAsync(cnt_d, P->ps));
-        std::vector<int> cols;
-        for (int64_t i = 0; i < npairs; ++i)
-            if (cnt[i] > 0) cols.push_back(int(i));
-        std::stable_sort(cols.begin(), cols.end(), [&](int p, int q) { return cnt[p] > cnt[q]; });
-        c.ncols = int(cols.size());
-        c.cols = static_cast<int*>(dalloc(P, size_t(std::max(c.ncols, 1)) * sizeof(int)));
-        if (c.ncols > 0)
-            CK(cudaMemcpyAsync(c.cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice, P->ps));
-        CK(cudaStreamSynchronize(P->ps));
-    }
+    // the CUDA-core interpolation's column queue, only where that kernel is
+    // the plan's choice from the start (it is built on first use otherwise)
+    if (column_kernels(P->d, P->W) && !P->tc) build_column_queue(P, c);
     // Run tasks: 2-D strips (one warp per task): at most kStripMaxPts points,
     // and small clouds take shorter runs (down to one batch of 32) so that
     // their tasks still reach every SM; tensor-core interpolation (one block
@@ -1488,6 +1520,16 @@ int sk_set_kernels(sk_plan* P, int kernels) {
     if (!P || (kernels != SK_KERNELS_SIMT && kernels != SK_KERNELS_TENSOR)) return SK_ERR_ARG;
     if (kernels == SK_KERNELS_TENSOR && !P->tc_ok) return SK_ERR_UNSUPPORTED;
     const bool tc = kernels == SK_KERNELS_TENSOR;
+    if (!tc) {
+        try {
+            if (P->precision == SK_FP32)
+                ensure_column_queues<float>(P);
+            else
+                ensure_column_queues<double>(P);
+        } catch (const Fail& f) {
+            return fail_code(f);
+        }
+    }
     if (tc != P->tc) {
         destroy_graph(P);
         P->tc = tc;
@@ -1512,6 +1554,10 @@ int sk_autotune(sk_plan* P, int* chosen, void* stream) {
         enter(P, stream);
         int best = P->tc ? SK_KERNELS_TENSOR : SK_KERNELS_SIMT;
         if (P->tc_ok && P->method == SK_METHOD_NFFT) {
+            if (P->precision == SK_FP32)
+                ensure_column_queues<float>(P);
+            else
+                ensure_column_queues<double>(P);
             const bool was = P->tc;
             const int64_t launches = P->launches;
             double ms[2] = {0.0, 0.0};

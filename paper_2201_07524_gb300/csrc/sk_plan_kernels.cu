@@ -109,18 +109,22 @@ __global__ void k_sum_marg_log(const double* __restrict__ marg, const double* __
     if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
 }
 
-// Combine nblocks rows of nf fields; op[f] = 0 sum, 1 min, 2 max.  One block.
+// Combine nblocks rows of nf fields; op[f] = 0 sum, 1 min, 2 max.  One block
+// of 32 nf threads: warp f takes field f, each lane combines rows lane,
+// lane + 32, ... (all its loads in flight at once), then the lanes combine in
+// a fixed butterfly order, so the result does not depend on timing.
 __global__ void k_combine(const double* __restrict__ partial, int nblocks, int nf, int op0, int op1, int op2,
                           int op3, int op4, int op5, int op6, double* __restrict__ out) {
     const int ops[7] = {op0, op1, op2, op3, op4, op5, op6};
-    if (threadIdx.x >= nf) return;
-    const int f = threadIdx.x;
-    double acc = ops[f] == 0 ? 0.0 : (ops[f] == 1 ? INFINITY : -INFINITY);
-    for (int b = 0; b < nblocks; ++b) {
-        const double v = partial[b * nf + f];
-        acc = ops[f] == 0 ? acc + v : (ops[f] == 1 ? fmin(acc, v) : fmax(acc, v));
-    }
-    out[f] = acc;
+    const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (f >= nf) return;
+    const int op = ops[f];
+    auto comb = [op](double a, double b) { return op == 0 ? a + b : (op == 1 ? fmin(a, b) : fmax(a, b)); };
+    double acc = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
+    for (int b = lane; b < nblocks; b += 32) acc = comb(acc, partial[b * nf + f]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = comb(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) out[f] = acc;
 }
 
 // ------------------------------------------------------------ bin sorting
