@@ -415,6 +415,27 @@ __device__ __forceinline__ void epi_point_pre(const Epilogue& e, int64_t i, doub
     }
 }
 
+// The same for a kernel sum computed in FP32 (tv): without a near-field term
+// to add, the update's FP32 seed is tv itself, so the sum is converted to FP64
+// once and never back (bit-identical to epi_point_pre(e, i, double(tv), ...)).
+__device__ __forceinline__ void epi_point_pre32(const Epilogue& e, int64_t i, float tv, double q, double a,
+                                                double& sq, double& bad, double& dot) {
+    if (e.add || e.mode == EPI_APPLY || e.log_domain) {
+        epi_point_pre(e, i, double(tv), q, a, sq, bad, dot);
+        return;
+    }
+    const double t = double(tv);
+    const double r = fma(q, t, -a);
+    sq = fma(r, r, sq);
+    if (e.mode == EPI_UPDATE) {
+        if (!(tv >= 1.17549435e-38f && tv <= 3.0e38f)) bad += 1.0;
+        e.scal[i] = div_newton(a, t, tv);
+    } else {
+        dot = fma(q, t, dot);
+        e.t_store[i] = t;
+    }
+}
+
 // Reduction of the epilogue sums without a block-wide barrier: each warp adds
 // its sums into the block's shared slots; the last warp of the block to
 // arrive writes the block partial and takes part in the grid-wide

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(128) k_interp3_tc(InterpArgs a, Epilogue e) {
             float tv = 0.f;
 #pragma unroll
             for (int i = 0; i < S::X; ++i) tv = fmaf(wxf[i], rs[i], tv);
-            if (ok && !failed) epi_point_pre(e, p, double(tv), ep.q, ep.a, sq, bad, dot);
+            if (ok && !failed) epi_point_pre32(e, p, tv, ep.q, ep.a, sq, bad, dot);
             tc_fence_before();
         }
     }
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(128) k_interp2_tc(InterpArgs a, Epilogue e) {
                 const unsigned char* at = c < S::KC ? row_hi + c * S::LBO : row_lo + (c - S::KC) * S::LBO;
                 tv = fmaf(wx[q], *reinterpret_cast<const float*>(at + (el & 3) * 4), tv);
             }
-            if (ok && !failed) epi_point_pre(e, p, double(tv), ep.q, ep.a, sq, bad, dot);
+            if (ok && !failed) epi_point_pre32(e, p, tv, ep.q, ep.a, sq, bad, dot);
             tc_fence_before();
         }
     }
